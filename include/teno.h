@@ -1,0 +1,148 @@
+/*
+ * teno.h -- C-ABI of the GB300 (sm_103a) TENO5-LAD compressible-Euler library.
+ *
+ * The library computes the semi-discrete right-hand side of the Euler
+ * equations with the fifth-order targeted ENO scheme whose cutoff C_T adapts
+ * locally between 1e-10 and 1e-4 (Peng et al., arXiv 2003.09145, "TENO5-LAD"),
+ * and advances it with SSP-RK3.  All arithmetic is IEEE binary64 on the GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Conservative state U: device memory, float64, structure of arrays
+ *   U[nvar][n_z][n_y][n_x] with x fastest, nvar = ndim + 2, components
+ *   (rho, rho u, [rho v, [rho w]], E), E = p/(gamma-1) + rho |u|^2 / 2
+ *   (eq. 4.7).  Base address 16-byte aligned, no padding, no ghost cells:
+ *   boundaries are applied inside the kernels.
+ * - Every array is owned by the caller.  The library never allocates device
+ *   memory and never synchronises in a compute call: work is enqueued on the
+ *   caller's stream (`stream` is a cudaStream_t; NULL = legacy default stream).
+ *   Scratch space is the caller's workspace `ws` of at least
+ *   teno_workspace_bytes() bytes (256-byte aligned); it also holds the device
+ *   status word read by teno_get_device_status().
+ * - Arguments are validated on the host before anything is launched; an
+ *   invalid call returns TENO_ERR_INVALID_ARG (or TENO_ERR_WORKSPACE /
+ *   TENO_ERR_UNSUPPORTED) and enqueues nothing.  Conditions found on the
+ *   device (non-physical density or pressure, a time-out of a bounded wait)
+ *   are recorded in the workspace's status word.  No call throws.
+ * - Flag bytes (optional output of teno_rhs): one byte per interface, per
+ *   characteristic field and per side; bits 0..2 = delta_0..delta_2 of
+ *   eq. 2.14, bits 3..6 = the magnitude m of eq. 3.1.  Layout: for each
+ *   direction d in order, a block [nvar][2 (0 = f^+, 1 = f^-)][interface grid],
+ *   where the interface grid of direction d has n_d + 1 points along d (entry
+ *   i lies between cells i-1 and i) and n_k along the other axes, x fastest.
+ */
+#ifndef TENO_H
+#define TENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TENO_ABI_VERSION 1
+
+typedef enum {
+  TENO_OK = 0,
+  TENO_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or parameter   */
+  TENO_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  TENO_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed        */
+  TENO_ERR_NONPHYSICAL = 4,   /* device saw rho <= 0, p <= 0 or a non-finite */
+  TENO_ERR_TIMEOUT = 5,       /* a bounded device wait ran out               */
+  TENO_ERR_WORKSPACE = 6,     /* workspace missing, misaligned or too small  */
+  TENO_ERR_UNIMPLEMENTED = 7
+} teno_status;
+
+typedef enum {
+  TENO_BC_PERIODIC = 0,      /* wrap-around                                   */
+  TENO_BC_TRANSMISSIVE = 1   /* zero gradient: the boundary cell is copied    */
+} teno_bc;
+
+/* Grid and scheme parameters (problem statement: eq. 2.1-2.2, eq. 4.7,
+ * eq. 3.1-3.2).  Unused dimensions must have n = 1, dx = 1. */
+typedef struct {
+  int ndim;          /* 1, 2 or 3                                            */
+  int64_t n[3];      /* cells along x, y, z                                  */
+  double dx[3];      /* uniform spacing along x, y, z (> 0)                  */
+  int bc[3];         /* teno_bc per direction (both faces alike)             */
+  double gamma;      /* ratio of specific heats, eq. 4.7 (paper: 1.4)        */
+  double H;          /* discontinuity threshold H of eq. 3.2 (paper: 10)     */
+  int b_l, b_u;      /* magnitude bounds B_l, B_u of eq. 3.1 (paper: 4, 10)  */
+  double eps;        /* epsilon of eq. 2.8 / eq. 3.2 (paper: 1e-6)           */
+} teno_grid;
+
+/* Workspace sizes for each operation (teno_workspace_bytes `op`). */
+enum {
+  TENO_OP_RHS = 0,          /* teno_rhs                                     */
+  TENO_OP_RK3 = 1,          /* teno_rk3_step                                */
+  TENO_OP_RHS_ADJOINT = 2,  /* teno_rhs_adjoint                             */
+  TENO_OP_RK3_ADJOINT = 3   /* teno_rk3_step_adjoint                        */
+};
+
+/* Fills `g` with the paper's parameters (gamma 1.4, H 10, B_l 4, B_u 10,
+ * eps 1e-6; Sec. 2 and Sec. 4) for an ndim grid of n cells of spacing dx with
+ * boundary type bc on every axis. */
+void teno_grid_default(teno_grid* g, int ndim, const int64_t* n,
+                       const double* dx, int bc);
+
+/* Bytes of workspace `op` needs for grid g (0 if g is invalid). */
+size_t teno_workspace_bytes(const teno_grid* g, int op);
+
+/* Number of flag bytes teno_rhs writes for grid g (see the layout above). */
+int64_t teno_flag_count(const teno_grid* g);
+
+/*
+ * teno_rhs -- the semi-discrete operator L(U) of eq. 2.2,
+ *   dU/dt = - sum_d (F^_{d,i+1/2} - F^_{d,i-1/2}) / dx_d,
+ * computed dimension by dimension.  At every interface: global
+ * Lax-Friedrichs splitting (alpha per direction and characteristic field,
+ * the maximum of |lambda| over all cells of U), projection onto the Roe
+ * averaged characteristic fields, TENO5 reconstruction of each split flux
+ * (eq. 2.4-2.15) with the adaptive cutoff C_T = Lad(m) (eq. 3.1-3.4),
+ * back-projection (the convective-term paragraph of Sec. 4).
+ *   U     : [in]  device, nvar * ncell doubles (layout above).
+ *   dUdt  : [out] device, nvar * ncell doubles; must not alias U.
+ *   flags : [out] device, teno_flag_count(g) bytes, or NULL.
+ *   ws    : device workspace of >= teno_workspace_bytes(g, TENO_OP_RHS).
+ */
+teno_status teno_rhs(const teno_grid* g, const double* U, double* dUdt,
+                     uint8_t* flags, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * teno_rk3_step -- one SSP-RK3 step (eq. 4.1-4.3) of U in place:
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 U1 + 1/4 dt L(U1);
+ *   U <- 1/3 U + 2/3 U2 + 2/3 dt L(U2).
+ * dt = dt_fixed if dt_fixed > 0, else the CFL step of eq. dt1 (1D) /
+ * eq. dt2 (2D) / sigma / sum_d(max(|u_d|+c)/dx_d) (3D) with sigma = cfl,
+ * evaluated on the device from U; in both cases dt is clipped to
+ * t_end - t so the step lands on t_end.  When t >= t_end nothing changes.
+ *   U      : [in/out] device state.
+ *   t_dev  : [in/out] device double, the current time (advanced by dt).
+ *   dt_dev : [out] device double receiving the dt used, or NULL.
+ *   ws     : >= teno_workspace_bytes(g, TENO_OP_RK3).
+ */
+teno_status teno_rk3_step(const teno_grid* g, double* U, double cfl,
+                          double dt_fixed, double* t_dev, double t_end,
+                          double* dt_dev, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/*
+ * teno_get_device_status -- waits for `stream`, then returns in *status the
+ * status recorded on the device in workspace `ws` since the last call
+ * (TENO_OK, TENO_ERR_NONPHYSICAL or TENO_ERR_TIMEOUT) and clears it.
+ * The return value reports the host-side outcome of the query itself.
+ */
+teno_status teno_get_device_status(void* ws, void* stream, int* status);
+
+/* Human-readable name of a status code (static storage). */
+const char* teno_status_string(teno_status s);
+
+/* TENO_ABI_VERSION of the loaded library. */
+int teno_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TENO_H */

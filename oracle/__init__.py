@@ -90,6 +90,9 @@ def lib():
             L.or_lf_alpha.restype = ctypes.c_int
             L.or_euler_rhs.argtypes = [ctypes.c_int, _I64, _D, _I32, _PP, _D, _D, _U8, _U8, _D]
             L.or_euler_rhs.restype = ctypes.c_int
+            L.or_euler_rhs_sample.argtypes = [ctypes.c_int, _I64, _D, _I32, _PP, _D, ctypes.c_int64,
+                                              _I64, _D, _U8, _U8, _D]
+            L.or_euler_rhs_sample.restype = ctypes.c_int
             L.or_euler_interface_diag.argtypes = [ctypes.c_int, _I64, _D, _I32, _PP, _D, ctypes.c_int,
                                                   _I64, ctypes.c_int, ctypes.c_int, _D]
             L.or_euler_interface_diag.restype = ctypes.c_int
@@ -243,6 +246,26 @@ def euler_rhs(U: np.ndarray, n, dx, bc, params: Params | None = None,
     if want_alpha:
         out.append(alpha)
     return tuple(out)
+
+
+def euler_rhs_sample(U: np.ndarray, n, dx, bc, cells, params: Params | None = None,
+                     flags_out: np.ndarray | None = None, flags_in: np.ndarray | None = None,
+                     alpha: np.ndarray | None = None) -> np.ndarray:
+    """L(U) at the given linear cell indices; returns [m][nvar].  ``flags_out`` /
+    ``flags_in`` are full-size flag arrays (only the sampled faces are touched)."""
+    p = params or Params()
+    ndim = len(n)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.zeros((cells.size, ndim + 2))
+    pc = p.c()
+    a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
+    st = lib().or_euler_rhs_sample(ndim, _shape3(n), _dx3(dx), _bc3(bc), ctypes.byref(pc),
+                                   _dp(np.ascontiguousarray(U)), cells.size,
+                                   cells.ctypes.data_as(_I64), _dp(out), _u8p(flags_out), _u8p(flags_in),
+                                   None if a is None else _dp(a))
+    if st != 0:
+        raise FloatingPointError("non-physical state in the oracle RHS")
+    return out
 
 
 def euler_interface_diag(U, n, dx, bc, d: int, ifc, field: int, side: int,

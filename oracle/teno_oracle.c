@@ -527,6 +527,66 @@ int or_euler_rhs(int ndim, const int64_t* n, const double* dx, const int* bc,
 }
 
 /*
+ * The right-hand side of eq. 2.2 at m sampled cells only (same arithmetic as
+ * or_euler_rhs; for grids too large to evaluate whole).  cells[k] is a linear
+ * cell index; out is [m][nvar].  flags_in / flags_out use the full flag
+ * layout of or_euler_rhs (only the entries of the sampled cells' faces are
+ * read or written).  alpha_in (nullable, [ndim][nvar]) supplies the LF
+ * speeds; otherwise they are computed from U.
+ */
+int or_euler_rhs_sample(int ndim, const int64_t* n, const double* dx,
+                        const int* bc, const or_params* P, const double* U,
+                        int64_t m, const int64_t* cells, double* out,
+                        unsigned char* flags_out,
+                        const unsigned char* flags_in,
+                        const double* alpha_in) {
+  or_shape s = make_shape(ndim, n);
+  int nvar = s.nvar;
+  double alpha[3][OR_MAXVAR];
+  int status = 0;
+  for (int d = 0; d < ndim; ++d) {
+    if (alpha_in) {
+      for (int r = 0; r < nvar; ++r) alpha[d][r] = alpha_in[d * nvar + r];
+    } else if (or_lf_alpha(ndim, n, d, P->gamma, U, alpha[d]) != 0) {
+      status = -1;
+    }
+  }
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+  for (int64_t k = 0; k < m; ++k) {
+    int64_t lin = cells[k];
+    int64_t idx[3] = {lin % s.n[0], (lin / s.n[0]) % s.n[1], lin / (s.n[0] * s.n[1])};
+    for (int r = 0; r < nvar; ++r) out[k * nvar + r] = 0.0;
+    for (int d = 0; d < ndim; ++d) {
+      int64_t nifc = or_num_interfaces(ndim, n, d);
+      int64_t foff = or_flag_offset(ndim, n, d);
+      int64_t m0 = s.n[0] + (d == 0), m1 = s.n[1] + (d == 1);
+      double Fh[2][OR_MAXVAR];
+      for (int face = 0; face < 2; ++face) {
+        int64_t ifc[3] = {idx[0], idx[1], idx[2]};
+        ifc[d] += face;
+        int64_t ilin = (ifc[2] * m1 + ifc[1]) * m0 + ifc[0];
+        unsigned char fl[2 * OR_MAXVAR], ff[2 * OR_MAXVAR];
+        if (flags_in)
+          for (int r = 0; r < nvar; ++r)
+            for (int side = 0; side < 2; ++side)
+              ff[r * 2 + side] = flags_in[foff + (r * 2 + side) * nifc + ilin];
+        if (interface_flux(&s, d, ifc, bc, P, U, alpha[d], Fh[face], fl,
+                           flags_in ? ff : NULL, -1, -1, NULL) != 0)
+          bad |= 1;
+        if (flags_out)
+          for (int r = 0; r < nvar; ++r)
+            for (int side = 0; side < 2; ++side)
+              flags_out[foff + (r * 2 + side) * nifc + ilin] = fl[r * 2 + side];
+      }
+      for (int r = 0; r < nvar; ++r)
+        out[k * nvar + r] += -(Fh[1][r] - Fh[0][r]) / dx[d];
+    }
+  }
+  return (status || bad) ? -1 : 0;
+}
+
+/*
  * Diagnostic record of one scalar reconstruction inside the Euler RHS: the
  * interface `ifc` of direction d, characteristic field r, side 0 (f^+) or
  * 1 (f^-).  Used to classify selector differences that lie on a rounding

@@ -1,0 +1,177 @@
+"""PyTorch-facing API over the C-ABI.  Tensors are the caller's device memory;
+every arithmetic step runs in the sm_103a kernels behind ``teno_*``.  PyTorch
+supplies allocation and the current CUDA stream only.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+
+WS_ALIGN = 256
+
+
+def _stream_ptr(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check_state(U: torch.Tensor, nvar: int, ncell: int, name: str = "U") -> None:
+    if not U.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if U.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64")
+    if not U.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if U.numel() != nvar * ncell:
+        raise ValueError(f"{name} has {U.numel()} elements, expected {nvar * ncell}")
+
+
+def alloc_workspace(nbytes: int, device) -> torch.Tensor:
+    """Zero-filled workspace whose data pointer is 256-byte aligned."""
+    raw = torch.zeros(int(nbytes) + WS_ALIGN, dtype=torch.uint8, device=device)
+    off = (-raw.data_ptr()) % WS_ALIGN
+    return raw[off:off + int(nbytes)]
+
+
+@dataclass
+class Scheme:
+    """Scheme parameters of eq. 2.8, 3.1-3.2 and the gas (eq. 4.7)."""
+    gamma: float = 1.4
+    H: float = 10.0
+    b_l: int = 4
+    b_u: int = 10
+    eps: float = 1e-6
+
+
+class EulerGrid:
+    """A uniform ndim grid of ``n`` cells (x first) with spacing ``dx`` and
+    boundary types ``bc`` (0 periodic, 1 transmissive)."""
+
+    def __init__(self, n, dx, bc, scheme: Scheme | None = None):
+        self.n = tuple(int(v) for v in n)
+        self.dx = tuple(float(v) for v in dx)
+        self.bc = tuple(bc) if isinstance(bc, (list, tuple)) else (int(bc),) * len(self.n)
+        self.scheme = scheme or Scheme()
+        s = self.scheme
+        self.c = _lib.make_grid(self.n, self.dx, self.bc, s.gamma, s.H, s.b_l, s.b_u, s.eps)
+        self.lib = _lib.load()
+
+    @property
+    def ndim(self) -> int:
+        return len(self.n)
+
+    @property
+    def nvar(self) -> int:
+        return self.ndim + 2
+
+    @property
+    def ncell(self) -> int:
+        c = 1
+        for v in self.n:
+            c *= v
+        return c
+
+    @property
+    def state_shape(self):
+        return (self.nvar,) + tuple(reversed(self.n))
+
+    def workspace_bytes(self, op: int) -> int:
+        nb = self.lib.teno_workspace_bytes(ctypes.byref(self.c), op)
+        if nb == 0:
+            raise ValueError("invalid grid or unsupported operation")
+        return nb
+
+    def flag_count(self) -> int:
+        return int(self.lib.teno_flag_count(ctypes.byref(self.c)))
+
+
+def rhs(grid: EulerGrid, U: torch.Tensor, want_flags: bool = False, ws: torch.Tensor | None = None,
+        out: torch.Tensor | None = None):
+    """dU/dt = L(U) (eq. 2.2) on the current CUDA stream.  Returns dUdt or
+    (dUdt, flags) with the flag layout of ``teno.h``."""
+    _check_state(U, grid.nvar, grid.ncell)
+    dUdt = out if out is not None else torch.empty_like(U)
+    flags = torch.empty(grid.flag_count(), dtype=torch.uint8, device=U.device) if want_flags else None
+    if ws is None:
+        ws = alloc_workspace(grid.workspace_bytes(_lib.OP_RHS), U.device)
+    st = grid.lib.teno_rhs(ctypes.byref(grid.c), _ptr(U), _ptr(dUdt), _ptr(flags), _ptr(ws),
+                           ws.numel(), _stream_ptr())
+    _lib.check(st, "teno_rhs")
+    return (dUdt, flags) if want_flags else dUdt
+
+
+def device_status(ws: torch.Tensor) -> int:
+    """Status recorded on the device in ``ws`` since the last query (clears it)."""
+    lib = _lib.load()
+    out = ctypes.c_int(0)
+    _lib.check(lib.teno_get_device_status(_ptr(ws), _stream_ptr(), ctypes.byref(out)),
+               "teno_get_device_status")
+    return out.value
+
+
+class Solver:
+    """SSP-RK3 time stepper (eq. 4.1-4.3) over one grid; owns its workspace,
+    the device time t and the last dt."""
+
+    def __init__(self, grid: EulerGrid, device="cuda", cfl: float = 0.5):
+        self.grid = grid
+        self.device = torch.device(device)
+        self.cfl = float(cfl)
+        self.ws = alloc_workspace(grid.workspace_bytes(_lib.OP_RK3), self.device)
+        self.t = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.dt = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.graph = None
+        self._graph_key = None
+
+    def reset_time(self, t0: float = 0.0) -> None:
+        self.t.fill_(t0)
+
+    def step(self, U: torch.Tensor, t_end: float = float("inf"), dt_fixed: float = 0.0) -> None:
+        """One step in place on U: dt = dt_fixed or the CFL step, clipped to t_end."""
+        g = self.grid
+        _check_state(U, g.nvar, g.ncell)
+        st = g.lib.teno_rk3_step(ctypes.byref(g.c), _ptr(U), self.cfl, float(dt_fixed), _ptr(self.t),
+                                 float(t_end), _ptr(self.dt), _ptr(self.ws), self.ws.numel(), _stream_ptr())
+        _lib.check(st, "teno_rk3_step")
+
+    def capture(self, U: torch.Tensor, steps: int, t_end: float = float("inf"), dt_fixed: float = 0.0):
+        """Capture ``steps`` RK3 steps on U into a CUDA graph (replayed by ``replay``)."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            self.step(U, t_end, dt_fixed)  # warm-up outside capture
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(steps):
+                self.step(U, t_end, dt_fixed)
+        self.graph = g
+        self._graph_key = (U.data_ptr(), steps, t_end, dt_fixed)
+        return g
+
+    def run(self, U: torch.Tensor, t_end: float, max_steps: int = 1 << 62, dt_fixed: float = 0.0,
+            chunk: int = 0) -> int:
+        """Advance U to t_end (or max_steps); returns the number of steps taken.
+        With chunk > 0 steps are issued ``chunk`` at a time between host checks
+        of t (steps after t_end are no-ops)."""
+        k = 0
+        chunk = chunk or 64
+        while k < max_steps:
+            n = min(chunk, max_steps - k)
+            for _ in range(n):
+                self.step(U, t_end, dt_fixed)
+            k += n
+            if float(self.t.item()) >= t_end:
+                break
+        return k
+
+    def status(self) -> int:
+        return device_status(self.ws)

@@ -1,0 +1,274 @@
+// teno_capi.cu -- the C-ABI of include/teno.h: argument validation, workspace
+// layout and the launch sequences of teno_rhs and teno_rk3_step.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "teno.h"
+#include "teno_device.cuh"
+#include "teno_launch.h"
+
+namespace {
+
+using teno::Grid;
+using teno::Scheme;
+
+constexpr size_t kAlign = 256;
+constexpr size_t kHeader = 256;  // status word, dt, alpha bit patterns
+
+size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool grid_ok(const teno_grid* g) {
+  if (!g) return false;
+  if (g->ndim < 1 || g->ndim > 3) return false;
+  for (int k = 0; k < 3; ++k) {
+    if (g->n[k] < 1) return false;
+    if (k >= g->ndim && g->n[k] != 1) return false;
+    if (k < g->ndim) {
+      if (!(g->dx[k] > 0.0) || !std::isfinite(g->dx[k])) return false;
+      if (g->bc[k] != TENO_BC_PERIODIC && g->bc[k] != TENO_BC_TRANSMISSIVE) return false;
+    }
+  }
+  if (!(g->gamma > 1.0) || !std::isfinite(g->gamma)) return false;
+  if (!(g->H > 0.0) || !std::isfinite(g->H)) return false;
+  if (!(g->eps > 0.0) || !std::isfinite(g->eps)) return false;
+  if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
+  // total cell count must stay addressable with 64-bit indices
+  const double cells = double(g->n[0]) * double(g->n[1]) * double(g->n[2]);
+  if (cells * (g->ndim + 3) > 9.0e18 / 8.0) return false;
+  return true;
+}
+
+int64_t ncell_of(const teno_grid* g) { return g->n[0] * g->n[1] * g->n[2]; }
+
+int64_t nifc_of(const teno_grid* g, int d) {
+  int64_t m = 1;
+  for (int k = 0; k < 3; ++k) m *= g->n[k] + (k == d ? 1 : 0);
+  return m;
+}
+
+struct Layout {
+  size_t status = 0, dt = 8, alpha = 64;
+  size_t aux = 0, fhat = 0, R = 0, U1 = 0, U2 = 0, total = 0;
+};
+
+Layout layout_of(const teno_grid* g, int op) {
+  Layout L;
+  const int nvar = g->ndim + 2;
+  const size_t ncell = size_t(ncell_of(g));
+  int64_t maxifc = 0;
+  for (int d = 0; d < g->ndim; ++d) maxifc = nifc_of(g, d) > maxifc ? nifc_of(g, d) : maxifc;
+  size_t off = kHeader;
+  L.aux = off;
+  off += round_up(sizeof(double) * (g->ndim + 3) * ncell);
+  L.fhat = off;
+  off += round_up(sizeof(double) * nvar * size_t(maxifc));
+  if (op == TENO_OP_RK3) {
+    L.R = off;
+    off += round_up(sizeof(double) * nvar * ncell);
+    L.U1 = off;
+    off += round_up(sizeof(double) * nvar * ncell);
+    L.U2 = off;
+    off += round_up(sizeof(double) * nvar * ncell);
+  }
+  L.total = off;
+  return L;
+}
+
+Grid make_grid(const teno_grid* g) {
+  Grid G;
+  for (int k = 0; k < 3; ++k) {
+    G.n[k] = g->n[k];
+    G.bc[k] = k < g->ndim ? g->bc[k] : 0;
+    G.dx[k] = k < g->ndim ? g->dx[k] : 1.0;
+    G.inv_dx[k] = 1.0 / G.dx[k];
+  }
+  G.ncell = ncell_of(g);
+  return G;
+}
+
+Scheme make_scheme(const teno_grid* g) {
+  Scheme S;
+  std::memset(&S, 0, sizeof(S));
+  S.gamma = g->gamma;
+  S.gm1 = g->gamma - 1.0;
+  S.eps = g->eps;
+  S.b_l = g->b_l;
+  S.b_u = g->b_u;
+  const int K = g->b_u - g->b_l;
+  S.nthr = K;
+  // floor(theta K) >= j  <=>  max chi~ <= H (K/j - 1)   (eq. 3.1-3.2)
+  for (int j = 1; j < K; ++j) S.thr[j - 1] = g->H * (double(K) / double(j) - 1.0);
+  // theta == 1 in binary64  <=>  max chi~ / H <= 2^-53
+  S.thr[K - 1] = g->H * 0x1p-53;
+  return S;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// True if p is a device (or managed) allocation the current device can use.
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  static int cache[64] = {0};
+  if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  if (dev >= 0 && dev < 64) cache[dev] = n;
+  return n;
+}
+
+#define TENO_CUDA(call)                                  \
+  do {                                                   \
+    if ((call) != cudaSuccess) return TENO_ERR_CUDA;     \
+  } while (0)
+
+// One right-hand-side evaluation of state `U`.  mode_last selects what the
+// last direction's difference kernel does (0: write/accumulate dUdt into R;
+// 2/3/4: SSP-RK3 stage into Uout).
+teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
+                         const double* U, double* R, uint8_t* flags,
+                         int mode_last, const double* Un, const double* Uk,
+                         double* Uout, cudaStream_t st, bool with_dt,
+                         double cfl, double dt_fixed, double* t_dev,
+                         double t_end, double* dt_out) {
+  const Grid G = make_grid(g);
+  const Scheme S = make_scheme(g);
+  const int nsm = sm_count();
+  int* status = reinterpret_cast<int*>(ws + L.status);
+  double* dt_ws = reinterpret_cast<double*>(ws + L.dt);
+  auto* alpha = reinterpret_cast<unsigned long long*>(ws + L.alpha);
+  double* aux = reinterpret_cast<double*>(ws + L.aux);
+  double* Fhat = reinterpret_cast<double*>(ws + L.fhat);
+  TENO_CUDA(cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st));
+  TENO_CUDA(teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st));
+  if (with_dt)
+    TENO_CUDA(teno::launch_dt(g->ndim, alpha, G, cfl, dt_fixed, t_dev, t_end, dt_ws, dt_out, st));
+  int64_t foff = 0;
+  for (int d = 0; d < g->ndim; ++d) {
+    uint8_t* fl = flags ? flags + foff : nullptr;
+    TENO_CUDA(teno::launch_flux(g->ndim, d, U, aux, alpha, Fhat, fl, status, G, S, nsm, st));
+    foff += int64_t(g->ndim + 2) * 2 * nifc_of(g, d);
+    const bool last = (d == g->ndim - 1);
+    const int mode = last ? (mode_last == 0 ? (d == 0 ? 0 : 1) : mode_last) : (d == 0 ? 0 : 1);
+    const int acc = d > 0 ? 1 : 0;
+    TENO_CUDA(teno::launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt_ws, G, mode, acc, nsm, st));
+  }
+  return TENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void teno_grid_default(teno_grid* g, int ndim, const int64_t* n, const double* dx, int bc) {
+  if (!g) return;
+  std::memset(g, 0, sizeof(*g));
+  g->ndim = ndim;
+  for (int k = 0; k < 3; ++k) {
+    g->n[k] = (k < ndim && n) ? n[k] : 1;
+    g->dx[k] = (k < ndim && dx) ? dx[k] : 1.0;
+    g->bc[k] = bc;
+  }
+  g->gamma = 1.4;
+  g->H = 10.0;
+  g->b_l = 4;
+  g->b_u = 10;
+  g->eps = 1e-6;
+}
+
+size_t teno_workspace_bytes(const teno_grid* g, int op) {
+  if (!grid_ok(g)) return 0;
+  if (op != TENO_OP_RHS && op != TENO_OP_RK3) return 0;
+  return layout_of(g, op).total;
+}
+
+int64_t teno_flag_count(const teno_grid* g) {
+  if (!grid_ok(g)) return 0;
+  int64_t c = 0;
+  for (int d = 0; d < g->ndim; ++d) c += int64_t(g->ndim + 2) * 2 * nifc_of(g, d);
+  return c;
+}
+
+teno_status teno_rhs(const teno_grid* g, const double* U, double* dUdt, uint8_t* flags,
+                     void* ws, size_t ws_bytes, void* stream) {
+  if (!grid_ok(g) || !U || !dUdt || U == dUdt) return TENO_ERR_INVALID_ARG;
+  if (!aligned(U, 16) || !aligned(dUdt, 16)) return TENO_ERR_INVALID_ARG;
+  if (!is_device_ptr(U) || !is_device_ptr(dUdt) || (flags && !is_device_ptr(flags)))
+    return TENO_ERR_INVALID_ARG;
+  const Layout L = layout_of(g, TENO_OP_RHS);
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < L.total || !is_device_ptr(ws)) return TENO_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return rhs_sequence(g, L, static_cast<char*>(ws), U, dUdt, flags, 0, nullptr, nullptr, nullptr,
+                      st, false, 0.0, 0.0, nullptr, 0.0, nullptr);
+}
+
+teno_status teno_rk3_step(const teno_grid* g, double* U, double cfl, double dt_fixed,
+                          double* t_dev, double t_end, double* dt_dev, void* ws,
+                          size_t ws_bytes, void* stream) {
+  if (!grid_ok(g) || !U || !t_dev) return TENO_ERR_INVALID_ARG;
+  if (!aligned(U, 16) || !aligned(t_dev, 8) || (dt_dev && !aligned(dt_dev, 8))) return TENO_ERR_INVALID_ARG;
+  if (!(dt_fixed > 0.0) && !(cfl > 0.0 && std::isfinite(cfl))) return TENO_ERR_INVALID_ARG;
+  if (!std::isfinite(dt_fixed) || std::isnan(t_end)) return TENO_ERR_INVALID_ARG;
+  if (!is_device_ptr(U) || !is_device_ptr(t_dev) || (dt_dev && !is_device_ptr(dt_dev)))
+    return TENO_ERR_INVALID_ARG;
+  const Layout L = layout_of(g, TENO_OP_RK3);
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < L.total || !is_device_ptr(ws)) return TENO_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  double* R = reinterpret_cast<double*>(w + L.R);
+  double* U1 = reinterpret_cast<double*>(w + L.U1);
+  double* U2 = reinterpret_cast<double*>(w + L.U2);
+  teno_status s;
+  // eq. 4.1: U1 = U + dt L(U); dt from U^n (eq. dt1 / dt2)
+  s = rhs_sequence(g, L, w, U, R, nullptr, 2, U, nullptr, U1, st, true, cfl, dt_fixed, t_dev,
+                   t_end, dt_dev);
+  if (s != TENO_OK) return s;
+  // eq. 4.2: U2 = 3/4 U + 1/4 U1 + 1/4 dt L(U1)
+  s = rhs_sequence(g, L, w, U1, R, nullptr, 3, U, U1, U2, st, false, 0, 0, nullptr, 0, nullptr);
+  if (s != TENO_OK) return s;
+  // eq. 4.3: U <- 1/3 U + 2/3 U2 + 2/3 dt L(U2)
+  return rhs_sequence(g, L, w, U2, R, nullptr, 4, U, U2, U, st, false, 0, 0, nullptr, 0, nullptr);
+}
+
+teno_status teno_get_device_status(void* ws, void* stream, int* status) {
+  if (!ws || !status || !aligned(ws, kAlign)) return TENO_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  TENO_CUDA(cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TENO_CUDA(cudaStreamSynchronize(st));
+  TENO_CUDA(cudaMemsetAsync(ws, 0, sizeof(int), st));
+  TENO_CUDA(cudaStreamSynchronize(st));
+  if (h & teno::kStatusTimeout) *status = TENO_ERR_TIMEOUT;
+  else if (h & teno::kStatusNonphysical) *status = TENO_ERR_NONPHYSICAL;
+  else *status = TENO_OK;
+  return TENO_OK;
+}
+
+const char* teno_status_string(teno_status s) {
+  switch (s) {
+    case TENO_OK: return "TENO_OK";
+    case TENO_ERR_INVALID_ARG: return "TENO_ERR_INVALID_ARG";
+    case TENO_ERR_UNSUPPORTED: return "TENO_ERR_UNSUPPORTED";
+    case TENO_ERR_CUDA: return "TENO_ERR_CUDA";
+    case TENO_ERR_NONPHYSICAL: return "TENO_ERR_NONPHYSICAL";
+    case TENO_ERR_TIMEOUT: return "TENO_ERR_TIMEOUT";
+    case TENO_ERR_WORKSPACE: return "TENO_ERR_WORKSPACE";
+    case TENO_ERR_UNIMPLEMENTED: return "TENO_ERR_UNIMPLEMENTED";
+  }
+  return "TENO_UNKNOWN_STATUS";
+}
+
+int teno_abi_version(void) { return TENO_ABI_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+// teno_launch.h -- host-side launchers of the kernels in teno_kernels.cu
+// (internal to the library; the public interface is include/teno.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "teno_device.cuh"
+
+namespace teno {
+
+cudaError_t launch_cell(int ndim, const double* U, double* aux,
+                        unsigned long long* alpha, int* status, int64_t ncell,
+                        double gamma, int nsm, cudaStream_t st);
+
+cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux,
+                        const unsigned long long* alpha, double* Fhat,
+                        uint8_t* flags, int* status, const Grid& G,
+                        const Scheme& S, int nsm, cudaStream_t st);
+
+cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
+                        const double* Un, const double* Uk, double* Uout,
+                        const double* dt, const Grid& G, int mode, int acc,
+                        int nsm, cudaStream_t st);
+
+cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
+                      double cfl, double dt_fixed, double* t_dev, double t_end,
+                      double* dt_ws, double* dt_out, cudaStream_t st);
+
+}  // namespace teno

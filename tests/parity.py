@@ -1,0 +1,110 @@
+"""Comparison of the CUDA path with the oracle (test infrastructure).
+
+Rounding-order differences can flip a selector that sits on a rounding
+boundary.  Such flips are counted, not failed, when (i) delta_k differs and the
+oracle's chi_k lies within 1e-10 relative of its C_T, or (ii) m differs and the
+oracle's 6 theta lies within 1e-12 of an integer (delta flips that only follow
+from that m flip are allowed as well).  The right-hand side is then compared
+with the oracle evaluated with the GPU's selections forced.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+RHS_RTOL = 1e-12     # relative max-norm, one RHS evaluation
+STEP_RTOL = 1e-10    # relative L1 after a fixed number of steps
+
+
+@dataclass
+class FlagReport:
+    total: int = 0
+    mismatched: int = 0
+    allowed_delta: int = 0
+    allowed_m: int = 0
+    unexplained: list = field(default_factory=list)
+
+
+def decode_flag_index(ndim, n, flat, oracle):
+    """flat flag index -> (direction, field, side, interface coordinates)."""
+    nvar = ndim + 2
+    for d in range(ndim):
+        off = oracle.flag_offset(ndim, n, d)
+        nifc = oracle.num_interfaces(ndim, n, d)
+        if off <= flat < off + nvar * 2 * nifc:
+            r = flat - off
+            fs, ilin = divmod(r, nifc)
+            s, side = divmod(fs, 2)
+            nn = list(n) + [1] * (3 - ndim)
+            m0 = nn[0] + (d == 0)
+            m1 = nn[1] + (d == 1)
+            ifc = (ilin % m0, (ilin // m0) % m1, ilin // (m0 * m1))
+            return d, s, side, ifc
+    raise IndexError(flat)
+
+
+def classify_flags(U, n, dx, bc, gpu_flags, oracle_flags, oracle, params=None,
+                   max_examined=2000) -> FlagReport:
+    rep = FlagReport(total=int(gpu_flags.size))
+    diff = np.nonzero(gpu_flags != oracle_flags)[0]
+    rep.mismatched = int(diff.size)
+    for flat in diff[:max_examined]:
+        d, s, side, ifc = decode_flag_index(len(n), n, int(flat), oracle)
+        dg = oracle.euler_interface_diag(U, n, dx, bc, d, ifc, s, side, params)
+        g, o = int(gpu_flags[flat]), int(oracle_flags[flat])
+        if (g >> 3) != (o >> 3):
+            six_theta = 6.0 * dg["theta"]
+            if abs(six_theta - round(six_theta)) <= 1e-12 * max(1.0, six_theta):
+                rep.allowed_m += 1
+                continue
+            rep.unexplained.append((d, s, side, ifc, g, o, dg))
+            continue
+        ok = True
+        for k in range(3):
+            if ((g >> k) & 1) != ((o >> k) & 1):
+                if abs(dg[f"chi{k}"] - dg["CT"]) > 1e-10 * dg["CT"]:
+                    ok = False
+        if ok:
+            rep.allowed_delta += 1
+        else:
+            rep.unexplained.append((d, s, side, ifc, g, o, dg))
+    if diff.size > max_examined:
+        rep.unexplained.append(("too many mismatches", int(diff.size)))
+    return rep
+
+
+def rel_max_err(a: np.ndarray, b: np.ndarray) -> float:
+    """max over fields of max|a - b| / max|b| (b's overall scale if a field is 0)."""
+    nvar = a.shape[0]
+    a = a.reshape(nvar, -1)
+    b = b.reshape(nvar, -1)
+    overall = float(np.max(np.abs(b))) or 1.0
+    worst = 0.0
+    for v in range(nvar):
+        scale = float(np.max(np.abs(b[v]))) or overall
+        worst = max(worst, float(np.max(np.abs(a[v] - b[v]))) / scale)
+    return worst
+
+
+def rel_l1_err(a: np.ndarray, b: np.ndarray) -> float:
+    nvar = a.shape[0]
+    a = a.reshape(nvar, -1)
+    b = b.reshape(nvar, -1)
+    worst = 0.0
+    for v in range(nvar):
+        scale = float(np.sum(np.abs(b[v]))) or 1.0
+        worst = max(worst, float(np.sum(np.abs(a[v] - b[v]))) / scale)
+    return worst
+
+
+def compare_rhs(U, n, dx, bc, gpu_rhs, gpu_flags, oracle, params=None):
+    """Full-grid comparison.  Returns (relative max error vs the forced-flag
+    oracle, FlagReport)."""
+    R_or, fl_or = oracle.euler_rhs(U, n, dx, bc, params, want_flags=True)
+    rep = classify_flags(U, n, dx, bc, gpu_flags, fl_or, oracle, params)
+    if rep.mismatched:
+        R_ref = oracle.euler_rhs(U, n, dx, bc, params, flags_in=gpu_flags)
+    else:
+        R_ref = R_or
+    return rel_max_err(gpu_rhs.reshape(R_ref.shape), R_ref), rep

@@ -1,0 +1,133 @@
+"""GPU parity of teno_rhs (through the C-ABI) with the FP64 oracle.
+
+Tolerance: 1e-12 relative max-norm per field on one RHS evaluation; selection
+flags identical except counted rounding-boundary flips (tests/parity.py)."""
+import numpy as np
+import pytest
+
+from paper_2003_09145_gb300 import inputs
+from parity import RHS_RTOL, classify_flags, compare_rhs, rel_max_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_09145_gb300 import api as A
+    return A
+
+
+def _gpu_rhs(api, P, want_flags=True):
+    grid = api.EulerGrid(P.n, P.dx, P.bc, api.Scheme(gamma=P.gamma))
+    U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
+    out = api.rhs(grid, U, want_flags=want_flags)
+    torch.cuda.synchronize()
+    if want_flags:
+        return out[0].cpu().numpy(), out[1].cpu().numpy()
+    return out.cpu().numpy(), None
+
+
+def _check(api, oracle, P, max_flips=0):
+    R, fl = _gpu_rhs(api, P)
+    err, rep = compare_rhs(P.U0, P.n, P.dx, P.bc, R, fl, oracle, oracle.Params(gamma=P.gamma))
+    assert not rep.unexplained, rep.unexplained[:3]
+    assert rep.mismatched <= max(max_flips, rep.total * 1e-4), rep
+    assert err <= RHS_RTOL, err
+    return err, rep
+
+
+def test_sod_200(api, oracle):
+    _check(api, oracle, inputs.shock_tube(200))
+
+
+def test_shu_osher_4096(api, oracle):
+    _check(api, oracle, inputs.shu_osher(4096))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 33, 129, 1000])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_1d_ragged_sizes(api, oracle, n, bc):
+    U = inputs.random_discontinuous_state(1, (n,), seed=n)
+    P = inputs.Problem("rand1d", U, (n,), (1.0 / n,), (bc,), 0.0)
+    _check(api, oracle, P)
+
+
+@pytest.mark.parametrize("n", [(17, 9), (64, 64), (5, 130)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_2d_random(api, oracle, n, bc):
+    U = inputs.random_discontinuous_state(2, n, seed=sum(n))
+    P = inputs.Problem("rand2d", U, n, (0.01, 0.013), (bc, bc), 0.0)
+    _check(api, oracle, P)
+
+
+def test_2d_four_quadrant_128(api, oracle):
+    _check(api, oracle, inputs.riemann_2d(n=128))
+
+
+@pytest.mark.parametrize("n", [(8, 8, 8), (13, 6, 9), (24, 24, 24)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_3d_random(api, oracle, n, bc):
+    U = inputs.random_discontinuous_state(3, n, seed=sum(n) + bc)
+    P = inputs.Problem("rand3d", U, n, (0.1, 0.07, 0.05), (bc,) * 3, 0.0)
+    _check(api, oracle, P)
+
+
+def test_3d_turbulence_32(api, oracle):
+    _check(api, oracle, inputs.solenoidal_turbulence(n=32))
+
+
+def test_smooth_periodic_3d(api, oracle):
+    U = inputs.random_smooth_state(3, (16, 12, 10), seed=3)
+    P = inputs.Problem("smooth3d", U, (16, 12, 10), (0.1, 0.1, 0.1), (0, 0, 0), 0.0)
+    _check(api, oracle, P)
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_constant_state_exact_zero(api, ndim):
+    n = (9, 7, 5)[:ndim]
+    prim = [1.3] + [0.4, -0.7, 0.2][:ndim] + [2.1]
+    rho = np.full(tuple(reversed(n)), prim[0])
+    U = inputs.prim_to_cons(rho, [np.full_like(rho, v) for v in prim[1:-1]], np.full_like(rho, prim[-1]))
+    for bc in (0, 1):
+        P = inputs.Problem("const", U, n, (0.1,) * ndim, (bc,) * ndim, 0.0)
+        R, fl = _gpu_rhs(api, P)
+        assert np.all(R == 0.0)
+        assert np.all(fl & 7 == 7)
+
+
+def _sampled(api, oracle, P, m, seed):
+    """Full-size launch; the oracle evaluates m sampled cells one by one."""
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
+    R, fl = api.rhs(grid, U, want_flags=True)
+    torch.cuda.synchronize()
+    R = R.cpu().numpy().reshape(P.U0.shape[0], -1)
+    fl = fl.cpu().numpy()
+    rng = np.random.default_rng(seed)
+    cells = np.unique(np.concatenate([rng.integers(0, P.ncell, size=m), [0, P.ncell - 1]]))
+    fo = np.zeros_like(fl)
+    S = oracle.euler_rhs_sample(P.U0, P.n, P.dx, P.bc, cells, flags_out=fo)
+    touched = np.nonzero(fo)[0]
+    ref = fl.copy()
+    ref[touched] = fo[touched]          # oracle's own selections on the sampled faces
+    rep = classify_flags(P.U0, P.n, P.dx, P.bc, fl, ref, oracle)
+    assert not rep.unexplained, rep.unexplained[:3]
+    Sf = oracle.euler_rhs_sample(P.U0, P.n, P.dx, P.bc, cells, flags_in=fl)
+    G = R[:, cells].T
+    scale = np.max(np.abs(R), axis=1)
+    err = np.max(np.abs(G - Sf) / np.where(scale > 0, scale, 1.0))
+    assert err <= RHS_RTOL, err
+    return rep
+
+
+@pytest.mark.slow
+def test_four_quadrant_2048_sampled(api, oracle):
+    _sampled(api, oracle, inputs.riemann_2d(n=2048), 4000, 1)
+
+
+@pytest.mark.slow
+def test_turbulence_256_sampled(api, oracle):
+    _sampled(api, oracle, inputs.solenoidal_turbulence(n=256), 2000, 2)

@@ -1,0 +1,100 @@
+"""GPU parity of teno_rk3_step (SSP-RK3, eq. 4.1-4.3, CFL step eq. dt1/dt2) with the
+oracle after a fixed number of steps: 1e-10 relative L1 per field, identical
+step sizes."""
+import numpy as np
+import pytest
+
+from paper_2003_09145_gb300 import inputs
+from parity import STEP_RTOL, rel_l1_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2003_09145_gb300 import api as A
+    return A
+
+
+def _gpu_run(api, P, steps, t_end=None, dt_fixed=0.0):
+    grid = api.EulerGrid(P.n, P.dx, P.bc, api.Scheme(gamma=P.gamma))
+    solver = api.Solver(grid, cfl=P.cfl)
+    U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
+    dts = []
+    te = P.t_end if t_end is None else t_end
+    for _ in range(steps):
+        solver.step(U, te, dt_fixed)
+        dts.append(solver.dt.item())
+    assert solver.status() == 0
+    return U.cpu().numpy(), solver.t.item(), dts
+
+
+def _oracle_run(oracle, P, steps, t_end=None, dt_fixed=0.0):
+    U = np.array(P.U0)
+    t = 0.0
+    dts = []
+    te = P.t_end if t_end is None else t_end
+    for _ in range(steps):
+        U, t2, k = oracle.euler_run(U, P.n, P.dx, P.bc, te, sigma=P.cfl, dt_fixed=dt_fixed,
+                                    max_steps=1, t0=t, params=oracle.Params(gamma=P.gamma))
+        dts.append(t2 - t if k else 0.0)
+        t = t2
+    return U, t, dts
+
+
+@pytest.mark.parametrize("case,steps", [
+    ("sod", 400),          # runs to t = 0.2 and past (steps beyond t_end are no-ops)
+    ("shu_osher", 100),
+    ("riemann2d", 20),
+    ("turb3d", 6),
+])
+def test_fixed_steps(api, oracle, case, steps):
+    P = {"sod": lambda: inputs.shock_tube(200),
+         "shu_osher": lambda: inputs.shu_osher(4096),
+         "riemann2d": lambda: inputs.riemann_2d(n=128, t_end=10.0),
+         "turb3d": lambda: inputs.solenoidal_turbulence(n=24, t_end=10.0)}[case]()
+    Ug, tg, dg = _gpu_run(api, P, steps)
+    Uo, to, do = _oracle_run(oracle, P, steps)
+    err = rel_l1_err(Ug, Uo)
+    assert err <= STEP_RTOL, err
+    # the step sizes come from the same correctly rounded wave speeds
+    np.testing.assert_allclose(dg, do, rtol=1e-12, atol=0)
+    assert tg == pytest.approx(to, rel=1e-13)
+    if case == "sod":
+        assert tg == P.t_end
+
+
+def test_first_dt_bitwise(api, oracle):
+    for P in (inputs.shock_tube(200), inputs.riemann_2d(n=64), inputs.solenoidal_turbulence(n=16)):
+        _, _, dg = _gpu_run(api, P, 1, t_end=100.0)
+        dt_or = oracle.euler_dt(P.U0, P.n, P.dx, P.cfl, P.gamma)
+        assert dg[0] == dt_or
+
+
+def test_clip_and_no_op_after_t_end(api):
+    P = inputs.shock_tube(64)
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    solver = api.Solver(grid, cfl=0.5)
+    U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
+    t_end = 1e-4
+    solver.step(U, t_end)
+    assert solver.t.item() == t_end
+    before = U.clone()
+    solver.step(U, t_end)
+    assert solver.dt.item() == 0.0
+    assert torch.equal(before, U)
+
+
+def test_nonphysical_state_is_reported(api):
+    P = inputs.shock_tube(64)
+    U0 = np.array(P.U0)
+    U0[2, 10] = -1.0          # negative total energy -> negative pressure
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    solver = api.Solver(grid)
+    U = torch.from_numpy(U0).cuda()
+    solver.step(U, 1.0, dt_fixed=1e-5)
+    assert solver.status() == 4      # TENO_ERR_NONPHYSICAL
+    assert solver.status() == 0      # cleared by the query
