@@ -1,0 +1,335 @@
+"""Benchmark: SSP-RK3 steps of the TENO5-LAD Euler solver on the 3D periodic
+turbulence box (256^3 cells, FP64), reported in Gcell-updates/s (one cell
+advanced one full RK3 step = three right-hand-side evaluations).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 (torchrun) runs N independent replicas,
+one per GPU, with no data exchange ("replicas only"); the timed region is
+bracketed by a barrier and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RHS Gcell-updates/s & roofline fraction; batched/adjoint vs plain at 1e-10"
+UNIT = "Gcell-updates/s"
+WORKLOAD = ("3D periodic compressible Euler, random-phase solenoidal velocity E(k)~k^4 exp(-2(k/4)^2), "
+            "Mt 0.6, 256^3 cells, TENO5-LAD + global LF + characteristic projection, SSP-RK3 CFL 0.5")
+N_CELLS_1D = 256
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
+# Algorithmic work of one interface flux at nvar = 5 (FMA = 2 flops, a division
+# or square root = 1): Roe eigensystem 60, characteristic projection 456, LF
+# split 60, ten TENO5-LAD reconstructions 874, back-projection 50, plus the 45
+# divisions / roots: 1495 flops.
+ALG_FLOPS_PER_IFACE_3D = 1495
+STATE_BYTES_PER_CELL = 5 * 8
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    backend = "nccl"
+    dist.init_process_group(backend=backend)
+    return dist, rank, ws
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2003_09145_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch():
+    """DRAM bytes per flux-kernel launch from the committed ncu summary, if it was
+    taken on the current kernel sources; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "flux_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != _source_hash():
+        return None
+    return rec.get("bytes_per_launch_full_size")
+
+
+def cpu_baseline(sample_n: int = 96, steps: int = 2) -> dict:
+    """The oracle (plain FP64 C, OpenMP on all host cores) on a bounded sample of
+    the same workload: `steps` RK3 steps of the same turbulence generator on a
+    sample_n^3 box."""
+    import oracle
+    from paper_2003_09145_gb300 import inputs
+    P = inputs.solenoidal_turbulence(n=sample_n)
+    U = P.U0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dt = oracle.euler_dt(U, P.n, P.dx, 0.5)
+        U = oracle.euler_rk3_step(U, P.n, P.dx, P.bc, dt)
+    el = time.perf_counter() - t0
+    cells = sample_n ** 3 * steps
+    return {"value": cells / el / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 steps on a {sample_n}^3 box of the same turbulence generator "
+                      f"({el:.1f} s wall)"}
+
+
+def run_reference(args, rank: int) -> None:
+    """The oracle as the reference arm: each step one RK3 step of a bounded
+    sample (64^3 box) of the workload, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2003_09145_gb300 import inputs
+    n = 64
+    P = inputs.solenoidal_turbulence(n=n)
+    U = P.U0
+    for _ in range(args.warmup):
+        U = oracle.euler_rk3_step(U, P.n, P.dx, P.bc, oracle.euler_dt(U, P.n, P.dx, 0.5))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = oracle.euler_rk3_step(U, P.n, P.dx, P.bc, oracle.euler_dt(U, P.n, P.dx, 0.5))
+    el = time.perf_counter() - t0
+    value = n ** 3 * args.steps / el / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}^3 box per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} RK3 steps on a {n}^3 box"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def fp64_probe(api, device) -> float:
+    """Measured FP64 FMA throughput (flop/s) of this GPU."""
+    import torch
+    lib = api._lib.load()
+    blocks, iters = SM_COUNT * 16, 4096
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=device)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        api._lib.check(lib.teno_probe_fp64(ctypes.c_void_p(out.data_ptr()), blocks, iters, st), "probe")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api._lib.check(lib.teno_probe_fp64(ctypes.c_void_p(out.data_ptr()), blocks, iters, st), "probe")
+    e1.record()
+    torch.cuda.synchronize()
+    return blocks * 256 * 8 * iters * 2 / (e0.elapsed_time(e1) * 1e-3)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_CELLS_1D, help="cells per axis (default 256)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    dist, rank, world = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_2003_09145_gb300 import api, inputs
+    from paper_2003_09145_gb300 import _lib
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    lib = _lib.load()
+
+    n = args.n
+    P = inputs.solenoidal_turbulence(n=n)
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    solver = api.Solver(grid, device=device, cfl=0.5)
+    U0 = torch.from_numpy(P.U0).to(device)
+    U = U0.clone()
+    t_end = float("inf")
+
+    for _ in range(args.warmup):
+        solver.step(U, t_end)
+    torch.cuda.synchronize()
+    assert solver.status() == 0, "non-physical state during warm-up"
+
+    # ---- device-resident timed region --------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    _lib.check(lib.teno_timer_begin(), "teno_timer_begin")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        solver.step(U, t_end)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    kms = (ctypes.c_double * 4)()
+    kcount = (ctypes.c_int64 * 4)()
+    _lib.check(lib.teno_timer_end(kms, kcount), "teno_timer_end")
+    clk = clocks.stop()
+    assert solver.status() == 0, "non-physical state in the timed region"
+    if dist:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = grid.ncell
+    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (interface fluxes) ----------------
+    kinds = dict(zip(_lib.KERNEL_KINDS, zip(list(kms), list(kcount))))
+    flux_ms, flux_n = kinds["flux"]
+    nifc = (n + 1) * n * n
+    flux_avg_s = flux_ms / flux_n * 1e-3
+    achieved = ALG_FLOPS_PER_IFACE_3D * nifc / flux_avg_s / 1e12
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    probe = fp64_probe(api, device) / 1e12
+    traffic = _traffic_per_launch()
+    total_kernel_ms = sum(kms)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "flux_kernel<3,d> (interface fluxes)",
+                "kernel_share": flux_ms / total_kernel_ms if total_kernel_ms else None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP64_FLOP_PER_CLK_PER_SM} FP64 flop/clk x "
+                               f"{sm_max:.0f} MHz (max SM clock)",
+                "fp64_probe_tflops": probe,
+                "alg_flops_per_interface": ALG_FLOPS_PER_IFACE_3D}
+
+    # ---- end to end through the public API with host buffers ---------------
+    U_host = P.U0.copy()
+    pin = torch.from_numpy(U_host).pin_memory()
+    out_host = torch.empty_like(pin).pin_memory()
+    Ud = torch.empty_like(U0)
+    solver.reset_time(0.0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.steps):
+        Ud.copy_(pin, non_blocking=True)
+        solver.step(Ud, t_end)
+        out_host.copy_(Ud, non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    ems = f0.elapsed_time(f1)
+    if dist:
+        t = torch.tensor([ems], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    nbytes = U0.numel() * 8
+    e2e = {"value": world * cells * args.steps / (ems * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells": cells, "grid": [n, n, n],
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (state %.0f MB)" % (nbytes / 1e6)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(sum(kcount)),
+                "kernel_ms": {k: v[0] for k, v in kinds.items()},
+                "clocks": clk, "impl": "ours"}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

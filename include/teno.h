@@ -135,6 +135,38 @@ teno_status teno_rk3_step(const teno_grid* g, double* U, double cfl,
  */
 teno_status teno_get_device_status(void* ws, void* stream, int* status);
 
+/* Kernel kinds reported by the launch timer. */
+enum {
+  TENO_KERNEL_CELL = 0,  /* primitive variables + LF wave-speed reduction   */
+  TENO_KERNEL_FLUX = 1,  /* interface fluxes of one direction               */
+  TENO_KERNEL_DIFF = 2,  /* conservative difference / fused RK3 stage       */
+  TENO_KERNEL_DT = 3,    /* CFL time step                                   */
+  TENO_KERNEL_KINDS = 4
+};
+
+/*
+ * teno_timer_begin / teno_timer_end -- measurement aid (no counterpart in the
+ * paper).  Between the two calls every kernel the library launches is
+ * bracketed by CUDA events on its stream (at most 8192 launches; later ones
+ * are not timed and teno_timer_end then returns TENO_ERR_WORKSPACE).
+ * teno_timer_end waits for those events and writes, per kernel kind, the
+ * summed device time in ms[TENO_KERNEL_KINDS] and the launch count in
+ * launches[TENO_KERNEL_KINDS] (host arrays).  Not thread-safe; do not use
+ * while capturing a CUDA graph.
+ */
+teno_status teno_timer_begin(void);
+teno_status teno_timer_end(double* ms, int64_t* launches);
+
+/*
+ * teno_probe_fp64 -- measurement aid (no counterpart in the paper): launches
+ * `blocks` blocks of 256 threads, each running 8 independent FP64 fused
+ * multiply-add chains of `iters` steps (2 * 8 * iters flops per thread), and
+ * writes one double per thread to out_dev (device, blocks * 256 doubles).
+ * Timing it with events gives the FP64 pipe's throughput on this GPU.
+ */
+teno_status teno_probe_fp64(double* out_dev, int64_t blocks, int64_t iters,
+                            void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* teno_status_string(teno_status s);
 

@@ -20,6 +20,7 @@ STATUS_NAMES = {
 }
 OP_RHS, OP_RK3, OP_RHS_ADJOINT, OP_RK3_ADJOINT = 0, 1, 2, 3
 BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+KERNEL_KINDS = ("cell", "flux", "diff", "dt")
 
 
 class TenoGrid(ctypes.Structure):
@@ -55,6 +56,9 @@ SIGNATURES = [
     ("teno_rk3_step", ctypes.c_int, [_GP, _VP, ctypes.c_double, ctypes.c_double, _VP,
                                      ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
     ("teno_get_device_status", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int)]),
+    ("teno_timer_begin", ctypes.c_int, []),
+    ("teno_timer_end", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    ("teno_probe_fp64", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP]),
     ("teno_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("teno_abi_version", ctypes.c_int, []),
 ]

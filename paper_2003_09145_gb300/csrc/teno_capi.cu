@@ -128,6 +128,37 @@ int sm_count() {
   return n;
 }
 
+// ---------------------------------------------------------------------------
+// Optional per-kernel timing: when enabled, every launch of the library is
+// bracketed by a pair of CUDA events on its stream; teno_timer_end() sums the
+// elapsed times per kernel kind.  Off by default (no events are recorded).
+// ---------------------------------------------------------------------------
+constexpr int kTimerPairs = 8192;
+struct KernelTimer {
+  bool on = false;
+  bool created = false;
+  int used = 0;
+  int64_t dropped = 0;
+  cudaEvent_t ev[2 * kTimerPairs];
+  int kind[kTimerPairs];
+};
+KernelTimer g_timer;
+
+struct TimerScope {
+  cudaStream_t st;
+  int slot = -1;
+  TimerScope(cudaStream_t s, int kind) : st(s) {
+    if (!g_timer.on) return;
+    if (g_timer.used >= kTimerPairs) { ++g_timer.dropped; return; }
+    slot = g_timer.used++;
+    g_timer.kind[slot] = kind;
+    cudaEventRecord(g_timer.ev[2 * slot], st);
+  }
+  ~TimerScope() {
+    if (slot >= 0) cudaEventRecord(g_timer.ev[2 * slot + 1], st);
+  }
+};
+
 #define TENO_CUDA(call)                                  \
   do {                                                   \
     if ((call) != cudaSuccess) return TENO_ERR_CUDA;     \
@@ -151,18 +182,29 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
   double* aux = reinterpret_cast<double*>(ws + L.aux);
   double* Fhat = reinterpret_cast<double*>(ws + L.fhat);
   TENO_CUDA(cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st));
-  TENO_CUDA(teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st));
-  if (with_dt)
+  {
+    TimerScope ts(st, TENO_KERNEL_CELL);
+    TENO_CUDA(teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st));
+  }
+  if (with_dt) {
+    TimerScope ts(st, TENO_KERNEL_DT);
     TENO_CUDA(teno::launch_dt(g->ndim, alpha, G, cfl, dt_fixed, t_dev, t_end, dt_ws, dt_out, st));
+  }
   int64_t foff = 0;
   for (int d = 0; d < g->ndim; ++d) {
     uint8_t* fl = flags ? flags + foff : nullptr;
-    TENO_CUDA(teno::launch_flux(g->ndim, d, U, aux, alpha, Fhat, fl, status, G, S, nsm, st));
+    {
+      TimerScope ts(st, TENO_KERNEL_FLUX);
+      TENO_CUDA(teno::launch_flux(g->ndim, d, U, aux, alpha, Fhat, fl, status, G, S, nsm, st));
+    }
     foff += int64_t(g->ndim + 2) * 2 * nifc_of(g, d);
     const bool last = (d == g->ndim - 1);
     const int mode = last ? (mode_last == 0 ? (d == 0 ? 0 : 1) : mode_last) : (d == 0 ? 0 : 1);
     const int acc = d > 0 ? 1 : 0;
-    TENO_CUDA(teno::launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt_ws, G, mode, acc, nsm, st));
+    {
+      TimerScope ts(st, TENO_KERNEL_DIFF);
+      TENO_CUDA(teno::launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt_ws, G, mode, acc, nsm, st));
+    }
   }
   return TENO_OK;
 }
@@ -253,6 +295,36 @@ teno_status teno_get_device_status(void* ws, void* stream, int* status) {
   else if (h & teno::kStatusNonphysical) *status = TENO_ERR_NONPHYSICAL;
   else *status = TENO_OK;
   return TENO_OK;
+}
+
+teno_status teno_timer_begin(void) {
+  if (!g_timer.created) {
+    for (int i = 0; i < 2 * kTimerPairs; ++i)
+      if (cudaEventCreate(&g_timer.ev[i]) != cudaSuccess) return TENO_ERR_CUDA;
+    g_timer.created = true;
+  }
+  g_timer.used = 0;
+  g_timer.dropped = 0;
+  g_timer.on = true;
+  return TENO_OK;
+}
+
+teno_status teno_timer_end(double* ms, int64_t* launches) {
+  if (!ms || !launches) return TENO_ERR_INVALID_ARG;
+  g_timer.on = false;
+  for (int k = 0; k < TENO_KERNEL_KINDS; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (int i = 0; i < g_timer.used; ++i) {
+    if (cudaEventSynchronize(g_timer.ev[2 * i + 1]) != cudaSuccess) return TENO_ERR_CUDA;
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, g_timer.ev[2 * i], g_timer.ev[2 * i + 1]) != cudaSuccess)
+      return TENO_ERR_CUDA;
+    ms[g_timer.kind[i]] += t;
+    launches[g_timer.kind[i]] += 1;
+  }
+  return g_timer.dropped ? TENO_ERR_WORKSPACE : TENO_OK;
 }
 
 const char* teno_status_string(teno_status s) {
