@@ -89,20 +89,7 @@ Grid make_grid(const teno_grid* g) {
 }
 
 Scheme make_scheme(const teno_grid* g) {
-  Scheme S;
-  std::memset(&S, 0, sizeof(S));
-  S.gamma = g->gamma;
-  S.gm1 = g->gamma - 1.0;
-  S.eps = g->eps;
-  S.b_l = g->b_l;
-  S.b_u = g->b_u;
-  const int K = g->b_u - g->b_l;
-  S.nthr = K;
-  // floor(theta K) >= j  <=>  max chi~ <= H (K/j - 1)   (eq. 3.1-3.2)
-  for (int j = 1; j < K; ++j) S.thr[j - 1] = g->H * (double(K) / double(j) - 1.0);
-  // theta == 1 in binary64  <=>  max chi~ / H <= 2^-53
-  S.thr[K - 1] = g->H * 0x1p-53;
-  return S;
+  return teno::make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }

@@ -43,11 +43,14 @@ struct Scheme {
   double eps;     // epsilon of eq. 2.8 / 3.2
   int b_l, b_u;   // magnitude bounds of eq. 3.1
   int nthr;       // B_u - B_l
+  int top;        // largest power of two <= nthr (binary-search start)
+  unsigned keep_all;  // bit m set: every chi_k >= C_T is guaranteed at this m
   // m = B_l + #{ j in 1..B_u-B_l : tau <= thr[j-1] * min_k(beta_k + eps) }.
   // With theta = 1/(1 + max_k chi~_k / H) and max_k chi~_k = tau / min_k(beta_k
   // + eps) (eq. 3.2), floor(theta (B_u - B_l)) >= j  <=>  max chi~ <=
   // H ((B_u - B_l)/j - 1); the last threshold (theta == 1 exactly) is the
   // binary64 condition 1 + max chi~ / H == 1, i.e. max chi~ <= H 2^-53.
+  // Entries past B_u - B_l are 0 (the count is clamped to B_u - B_l).
   double thr[kMaxLadder];
 };
 
@@ -81,61 +84,89 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 
 // ---------------------------------------------------------------------------
 // TENO5-LAD scalar reconstruction of the interface value from five values
-// v0..v4 = (f_{i-2}, ..., f_{i+2}).  Returns f^ (eq. 2.7); *flag receives
+// v0..v4 = (f_{i-2}, ..., f_{i+2}).  Returns f^ (eq. 2.7); `flag` receives
 // delta bits 0..2 and m in bits 3..6.
+//
+// Arithmetic (all exact rewrites of the paper's formulas, evaluated in FP64):
+//  * with first differences e_k = v_{k+1} - v_k, the indicator terms of
+//    eq. 2.9-2.11 are a_0 = e1 - e0, c_0 = 3 e1 - e0, a_1 = e2 - e1,
+//    c_1 = -(e1 + e2), a_2 = e3 - e2, c_2 = e3 - 3 e2, and the candidate
+//    fluxes of eq. 2.4-2.6 are v2 + (5 e1/6 - e0/3), v2 + (e1/6 + e2/3),
+//    v2 + (2 e2/3 - e3/6);
+//  * m of eq. 3.1 counts the thresholds tau <= thr_j * min_k(beta_k + eps)
+//    (see Scheme), found by binary search over the decreasing thresholds;
+//  * the cutoff chi_k >= C_T of eq. 2.13-2.14 is decided without division:
+//    with D_k = beta_k + eps and N_k = D_k + tau, gamma_k (D0 D1 D2)^6 =
+//    (N_k prod_{j!=k} D_j)^6 =: P_k^6, so chi_k >= C_T <=> P_k^6 >= C_T sum P^6;
+//  * when max chi~ is small enough that chi_k >= 1/(3 (1 + max chi~)^6) > C_T
+//    holds for every k (Scheme::keep_all), all stencils are kept without
+//    evaluating gamma.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
                                             double v3, double v4,
                                             const Scheme& S, unsigned& flag) {
+  const double e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
   // eq. 2.9-2.11
   const double k13_12 = 13.0 / 12.0;
-  double a0 = v0 - 2.0 * v1 + v2, c0 = v0 - 4.0 * v1 + 3.0 * v2;
-  double a1 = v1 - 2.0 * v2 + v3, c1 = v1 - v3;
-  double a2 = v2 - 2.0 * v3 + v4, c2 = 3.0 * v2 - 4.0 * v3 + v4;
-  double beta0 = k13_12 * a0 * a0 + 0.25 * c0 * c0;
-  double beta1 = k13_12 * a1 * a1 + 0.25 * c1 * c1;
-  double beta2 = k13_12 * a2 * a2 + 0.25 * c2 * c2;
+  const double a0 = e1 - e0, a1 = e2 - e1, a2 = e3 - e2;
+  const double h0 = 0.5 * fma(3.0, e1, -e0);
+  const double h1 = 0.5 * (e1 + e2);
+  const double h2 = 0.5 * fma(-3.0, e2, e3);
+  const double beta0 = fma(k13_12 * a0, a0, h0 * h0);
+  const double beta1 = fma(k13_12 * a1, a1, h1 * h1);
+  const double beta2 = fma(k13_12 * a2, a2, h2 * h2);
   // eq. 2.12
-  double tau = fabs(beta2 - beta0);
-  double d0 = beta0 + S.eps, d1 = beta1 + S.eps, d2 = beta2 + S.eps;
-  // eq. 3.1-3.2 without division: compare tau with thr_j * min_k(beta_k+eps)
-  unsigned long long bmin = min(dbits(d0), min(dbits(d1), dbits(d2)));
-  double dmin = __longlong_as_double(static_cast<long long>(bmin));
-  unsigned long long btau = dbits(tau);
-  int m = S.b_l;
+  const double tau = fabs(beta2 - beta0);
+  const double d0 = beta0 + S.eps, d1 = beta1 + S.eps, d2 = beta2 + S.eps;
+  // eq. 3.1-3.2: m = B_l + #{j : tau <= thr_j * min_k D_k}
+  const unsigned long long bmin = min(dbits(d0), min(dbits(d1), dbits(d2)));
+  const double dmin = __longlong_as_double(static_cast<long long>(bmin));
+  const unsigned long long btau = dbits(tau);
+  int cnt = 0;
 #pragma unroll
-  for (int j = 0; j < kMaxLadder; ++j) {
-    if (j < S.nthr) m += (btau <= dbits(S.thr[j] * dmin)) ? 1 : 0;
+  for (int step = 8; step >= 1; step >>= 1) {
+    if (step <= S.top) {
+      const int idx = cnt + step - 1;
+      if (btau <= dbits(S.thr[idx] * dmin)) cnt += step;
+    }
   }
-  // eq. 3.4
-  double ct = c_lad[m];
-  // eq. 2.8 with C = 1, q = 6
-  double x0 = 1.0 + tau / d0, x1 = 1.0 + tau / d1, x2 = 1.0 + tau / d2;
-  double g0 = x0 * x0 * x0; g0 *= g0;
-  double g1 = x1 * x1 * x1; g1 *= g1;
-  double g2 = x2 * x2 * x2; g2 *= g2;
-  // eq. 2.13-2.14 as gamma_k >= C_T * sum(gamma)  (chi_k >= C_T)
-  unsigned long long lim = dbits(ct * (g0 + g1 + g2));
-  unsigned sel = (dbits(g0) >= lim ? 1u : 0u) | (dbits(g1) >= lim ? 2u : 0u) |
-                 (dbits(g2) >= lim ? 4u : 0u);
+  cnt = min(cnt, S.nthr);
+  const int m = S.b_l + cnt;
+  unsigned sel = 7u;
+  if (!((S.keep_all >> m) & 1u)) {
+    // eq. 3.4, eq. 2.8, eq. 2.13-2.14 (division-free form, see above)
+    const double ct = c_lad[m];
+    const double n0 = d0 + tau, n1 = d1 + tau, n2 = d2 + tau;
+    const double p0 = n0 * (d1 * d2), p1 = n1 * (d0 * d2), p2 = n2 * (d0 * d1);
+    double q0 = p0 * p0, q1 = p1 * p1, q2 = p2 * p2;
+    q0 = q0 * q0 * q0;
+    q1 = q1 * q1 * q1;
+    q2 = q2 * q2 * q2;
+    const double sum = q0 + q1 + q2;
+    if (sum > 0.0 && sum <= 1.7976931348623157e308) {
+      const unsigned long long lim = dbits(ct * sum);
+      sel = (dbits(q0) >= lim ? 1u : 0u) | (dbits(q1) >= lim ? 2u : 0u) |
+            (dbits(q2) >= lim ? 4u : 0u);
+    } else {
+      // outside the range of the products: gamma_k = (1 + tau/D_k)^6 directly
+      const double x0 = 1.0 + tau / d0, x1 = 1.0 + tau / d1, x2 = 1.0 + tau / d2;
+      double g0 = x0 * x0 * x0, g1 = x1 * x1 * x1, g2 = x2 * x2 * x2;
+      g0 *= g0;
+      g1 *= g1;
+      g2 *= g2;
+      const double gs = g0 + g1 + g2;
+      const unsigned long long lim = dbits(ct * gs);
+      sel = (dbits(g0) >= lim ? 1u : 0u) | (dbits(g1) >= lim ? 2u : 0u) |
+            (dbits(g2) >= lim ? 4u : 0u);
+      if (!(gs <= 1.7976931348623157e308)) sel = 7u;  // every chi_k undefined: keep all
+    }
+  }
   flag = sel | (static_cast<unsigned>(m) << 3);
-  // eq. 2.4-2.6
-  double f0 = (1.0 / 3.0) * v0 - (7.0 / 6.0) * v1 + (11.0 / 6.0) * v2;
-  double f1 = -(1.0 / 6.0) * v1 + (5.0 / 6.0) * v2 + (1.0 / 3.0) * v3;
-  double f2 = (1.0 / 3.0) * v2 + (5.0 / 6.0) * v3 - (1.0 / 6.0) * v4;
-  // eq. 2.15, eq. 2.7
-  return c_omega[sel][0] * f0 + c_omega[sel][1] * f1 + c_omega[sel][2] * f2;
-}
-
-// Same reconstruction with the selection forced (bits 0..2 of `forced`).
-__device__ __forceinline__ double teno5_forced(double v0, double v1, double v2,
-                                               double v3, double v4,
-                                               const Scheme& S, unsigned forced) {
-  double f0 = (1.0 / 3.0) * v0 - (7.0 / 6.0) * v1 + (11.0 / 6.0) * v2;
-  double f1 = -(1.0 / 6.0) * v1 + (5.0 / 6.0) * v2 + (1.0 / 3.0) * v3;
-  double f2 = (1.0 / 3.0) * v2 + (5.0 / 6.0) * v3 - (1.0 / 6.0) * v4;
-  unsigned sel = forced & 7u;
-  return c_omega[sel][0] * f0 + c_omega[sel][1] * f1 + c_omega[sel][2] * f2;
+  // eq. 2.4-2.6 relative to v2, eq. 2.15, eq. 2.7
+  const double r0 = fma(5.0 / 6.0, e1, (-1.0 / 3.0) * e0);
+  const double r1 = fma(1.0 / 6.0, e1, (1.0 / 3.0) * e2);
+  const double r2 = fma(2.0 / 3.0, e2, (-1.0 / 6.0) * e3);
+  return fma(c_omega[sel][0], r0, fma(c_omega[sel][1], r1, fma(c_omega[sel][2], r2, v2)));
 }
 
 }  // namespace teno

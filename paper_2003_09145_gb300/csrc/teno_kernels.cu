@@ -13,6 +13,7 @@
 //   diff_kernel<D> : per cell, -(F^_{i+1/2} - F^_{i-1/2}) / dx_D, written,
 //                    accumulated, or fused into the SSP-RK3 stage (eq. 4.1-4.3).
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "teno_device.cuh"
@@ -165,33 +166,26 @@ __global__ void __launch_bounds__(128) flux_kernel(
                                     : i1 * G.n[0] + i0;
 
     // six-point stencil i-2..i+3 with i = id - 1
-    double Ux[6][NVAR], Fx[6][NVAR];
+    double Ux[6][NVAR], un[6], pn[6];
     double sr2, sr3, sh2, sh3, uu2[NDIM], uu3[NDIM];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const int64_t c = base + ghost(id - 3 + j, nd, bcd) * stride_d;
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Ux[j][v] = U[v * ncell + c];
-      double un[NDIM];
+      un[j] = aux[DIR * ncell + c];
+      pn[j] = aux[NDIM * ncell + c];
+      if (j == 2 || j == 3) {
+        double* uu = (j == 2) ? uu2 : uu3;
 #pragma unroll
-      for (int k = 0; k < NDIM; ++k) un[k] = aux[k * ncell + c];
-      const double p = aux[NDIM * ncell + c];
-      // eq. 4.7: F = (rho u_d, rho u_k u_d + p delta_kd, u_d (E + p))
-      Fx[j][0] = Ux[j][0] * un[DIR];
-#pragma unroll
-      for (int k = 0; k < NDIM; ++k) Fx[j][1 + k] = Ux[j][1 + k] * un[DIR] + (k == DIR ? p : 0.0);
-      Fx[j][NVAR - 1] = un[DIR] * (Ux[j][NVAR - 1] + p);
-      if (j == 2) {
-        sr2 = aux[(NDIM + 1) * ncell + c];
-        sh2 = aux[(NDIM + 2) * ncell + c];
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) uu2[k] = un[k];
-      }
-      if (j == 3) {
-        sr3 = aux[(NDIM + 1) * ncell + c];
-        sh3 = aux[(NDIM + 2) * ncell + c];
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) uu3[k] = un[k];
+        for (int k = 0; k < NDIM; ++k) uu[k] = (k == DIR) ? un[j] : aux[k * ncell + c];
+        if (j == 2) {
+          sr2 = aux[(NDIM + 1) * ncell + c];
+          sh2 = aux[(NDIM + 2) * ncell + c];
+        } else {
+          sr3 = aux[(NDIM + 1) * ncell + c];
+          sh3 = aux[(NDIM + 2) * ncell + c];
+        }
       }
     }
     // Roe average of cells i and i+1
@@ -200,30 +194,45 @@ __global__ void __launch_bounds__(128) flux_kernel(
     double q2 = 0.0;
 #pragma unroll
     for (int k = 0; k < NDIM; ++k) {
-      u[k] = (sr2 * uu2[k] + sr3 * uu3[k]) * inv;
+      u[k] = fma(sr2, uu2[k], sr3 * uu3[k]) * inv;
       q2 = fma(u[k], u[k], q2);
     }
     const double H = (sh2 + sh3) * inv;
-    const double c2 = S.gm1 * (H - 0.5 * q2);
+    const double c2 = S.gm1 * fma(-0.5, q2, H);
     if (!(c2 > 0.0)) atomicOr(status, kStatusNonphysical);
-    const double cs = sqrt(c2);
-    const double ic = 1.0 / cs;
+    const double ic = rsqrt(c2);
+    const double cs = c2 * ic;
     const double b1 = S.gm1 * ic * ic;
     const double b2 = 0.5 * b1 * q2;
     const double hb1 = 0.5 * b1, hb2 = 0.5 * b2, hic = 0.5 * ic;
 
-    // projection and LF split: v+ = (g + alpha w)/2, v- = (g - alpha w)/2
+    // Characteristic values w = L U and the split fluxes v+- = (g +- alpha w)/2
+    // with g = L F.  Since F(U) = u_d U + p (0, e_d, u_d) (eq. 4.7),
+    // g = u_d w + p z with z = (hb1 du - hic, -2 hb1 du, 0.., hb1 du + hic),
+    // du = u_d - u~_d, so v+- = (u_d/2 +- alpha/2) w + (p/2) z.
     double fchar[NVAR];
     double vp[6][NVAR], vm[6][NVAR];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      double w[NVAR], g[NVAR];
+      double w[NVAR];
       project<NDIM, DIR>(Ux[j], u, hb1, hb2, hic, w);
-      project<NDIM, DIR>(Fx[j], u, hb1, hb2, hic, g);
+      const double hu = 0.5 * un[j];
+      const double hp = 0.5 * pn[j];
+      const double zeta = hb1 * (un[j] - u[DIR]);
+      const double t0 = hp * (zeta - hic);
+      const double tE = hp * (zeta + hic);
+      const double t1 = -2.0 * (hp * zeta);
+      vp[j][0] = fma(hu + alpha[0], w[0], t0);
+      vm[j][0] = fma(hu - alpha[0], w[0], t0);
+      vp[j][NVAR - 1] = fma(hu + alpha[NVAR - 1], w[NVAR - 1], tE);
+      vm[j][NVAR - 1] = fma(hu - alpha[NVAR - 1], w[NVAR - 1], tE);
+      const double sp = hu + alpha[1], sm = hu - alpha[1];
+      vp[j][1] = fma(sp, w[1], t1);
+      vm[j][1] = fma(sm, w[1], t1);
 #pragma unroll
-      for (int s = 0; s < NVAR; ++s) {
-        vp[j][s] = fma(alpha[s], w[s], 0.5 * g[s]);
-        vm[j][s] = fma(-alpha[s], w[s], 0.5 * g[s]);
+      for (int f = 2; f < NVAR - 1; ++f) {
+        vp[j][f] = sp * w[f];
+        vm[j][f] = sm * w[f];
       }
     }
     unsigned fl[NVAR][2];
@@ -359,6 +368,41 @@ __global__ void dt_kernel(const unsigned long long* __restrict__ alpha_bits,
   *dt_ws = dt;
   if (dt_out) *dt_out = dt;
   *t_dev = t + dt;
+}
+
+// ---------------------------------------------------------------------------
+// Scheme constants (host side)
+// ---------------------------------------------------------------------------
+Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u) {
+  static const double kPow10Neg[16] = {1e-0, 1e-1, 1e-2,  1e-3,  1e-4,  1e-5,  1e-6,  1e-7,
+                                       1e-8, 1e-9, 1e-10, 1e-11, 1e-12, 1e-13, 1e-14, 1e-15};
+  Scheme S;
+  std::memset(&S, 0, sizeof(S));
+  S.gamma = gamma;
+  S.gm1 = gamma - 1.0;
+  S.eps = eps;
+  S.b_l = b_l;
+  S.b_u = b_u;
+  const int K = b_u - b_l;
+  S.nthr = K;
+  S.top = 1;
+  while (S.top * 2 <= K) S.top *= 2;
+  // floor(theta K) >= j  <=>  max chi~ <= H (K/j - 1)   (eq. 3.1-3.2)
+  for (int j = 1; j < K; ++j) S.thr[j - 1] = H * (double(K) / double(j) - 1.0);
+  // theta == 1 in binary64  <=>  max chi~ / H <= 2^-53
+  S.thr[K - 1] = H * 0x1p-53;
+  // All stencils are kept whenever 3 (1 + max chi~)^6 C_T < 1 (then
+  // chi_k >= gamma_min / (3 gamma_max) >= 1 / (3 (1 + max chi~)^6) > C_T); at
+  // a given m, max chi~ <= thr[m - B_l - 1].  A relative margin of 1e-9 covers
+  // the rounding of the threshold products.
+  S.keep_all = 0;
+  for (int c = 1; c <= K; ++c) {
+    const int m = b_l + c;
+    const double x = 1.0 + S.thr[c - 1];
+    const double x6 = x * x * x * x * x * x;
+    if (3.0 * x6 * kPow10Neg[m] <= 1.0 - 1e-9) S.keep_all |= 1u << m;
+  }
+  return S;
 }
 
 // ---------------------------------------------------------------------------

@@ -9,6 +9,9 @@
 
 namespace teno {
 
+// Scheme constants for the given gas and LAD parameters (eq. 3.1-3.2, 2.8).
+Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u);
+
 cudaError_t launch_cell(int ndim, const double* U, double* aux,
                         unsigned long long* alpha, int* status, int64_t ncell,
                         double gamma, int nsm, cudaStream_t st);
