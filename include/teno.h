@@ -135,6 +135,36 @@ teno_status teno_rk3_step(const teno_grid* g, double* U, double cfl,
  */
 teno_status teno_get_device_status(void* ws, void* stream, int* status);
 
+/*
+ * teno_rhs_noalloc -- teno_rhs for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment aid.
+ *
+ * Who needs it: code that may not call cudaMalloc -- a plugin running inside
+ * another framework's memory pool or allocator, a host application that
+ * forbids device allocation on its threads, or a deployment with a fixed,
+ * pre-planned memory footprint.  Such callers can pass their own input and
+ * output arrays but cannot supply the workspace teno_rhs needs.  This entry
+ * point computes the same L(U) with the same kernels and allocates nothing:
+ * its scratch is one file-scope device array of TENO_NOALLOC_SCRATCH_BYTES,
+ * which every GPU that loads the library holds until the process exits.
+ *   U    : [in]  device, nvar * ncell doubles (layout above).
+ *   dUdt : [out] device, nvar * ncell doubles; must not alias U.
+ * Size limit: a call needs 256 + 8 (ndim + 3) ncell + 8 (ndim + 2) max_d
+ * (#interfaces_d) bytes (each term rounded up to 256); larger grids are
+ * rejected with TENO_ERR_WORKSPACE before anything is launched.  In 1D that is
+ * up to about 149,000 cells; in 3D about 45^3.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before capturing
+ * a stream into a CUDA graph.
+ * All calls share the one array and each call starts by clearing the parts
+ * that must start at zero, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and give wrong results: serialise them.
+ * Selection flags and device-side status are not reported by this variant.
+ */
+#define TENO_NOALLOC_SCRATCH_BYTES (8u << 20)
+teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, double* dUdt,
+                             void* stream);
+
 /* Kernel kinds reported by the launch timer. */
 enum {
   TENO_KERNEL_CELL = 0,  /* primitive variables + LF wave-speed reduction   */
