@@ -32,11 +32,19 @@ WORKLOAD = ("3D periodic compressible Euler, random-phase solenoidal velocity E(
 N_CELLS_1D = 256
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
-# Algorithmic work of one interface flux at nvar = 5 (FMA = 2 flops, a division
-# or square root = 1): Roe eigensystem 60, characteristic projection 456, LF
-# split 60, ten TENO5-LAD reconstructions 874, back-projection 50, plus the 45
-# divisions / roots: 1495 flops.
-ALG_FLOPS_PER_IFACE_3D = 1495
+# Algorithmic work of one interface flux at nvar = 5 (3D), counting the
+# formulas the kernel evaluates (add/mul = 1 flop, FMA = 2, divide / rsqrt = 1):
+# Roe average and eigen-coefficients 34, projection of six points 6 x 20,
+# split fluxes 6 x 32, characteristic sum 5, back-projection 21, and per
+# scalar reconstruction (10 per interface) 49 for indicators, tau, m,
+# candidates and weights, plus 21 for the cutoff test when it is evaluated
+# (it is skipped when every stencil is provably kept).
+ALG_FIXED_3D = 34 + 6 * 20 + 6 * 32 + 5 + 21
+ALG_PER_RECON = 49
+ALG_CUTOFF = 21
+# The survey's nominal count of a straightforward evaluation (reported for
+# reference): 1450 flops + 45 divisions per interface.
+SURVEY_FLOPS_PER_IFACE_3D = 1495
 STATE_BYTES_PER_CELL = 5 * 8
 
 
@@ -177,6 +185,19 @@ def run_reference(args, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def _keep_all_mask(scheme) -> int:
+    """Magnitudes m at which chi_k >= C_T holds for every k by the bound
+    chi_k >= 1/(3 (1 + max chi~)^6) (the kernel skips the cutoff test there)."""
+    K = scheme.b_u - scheme.b_l
+    thr = [scheme.H * (K / j - 1.0) for j in range(1, K)] + [scheme.H * 2.0 ** -53]
+    mask = 0
+    for c in range(1, K + 1):
+        m = scheme.b_l + c
+        if 3.0 * (1.0 + thr[c - 1]) ** 6 * float(f"1e-{m}") <= 1.0 - 1e-9:
+            mask |= 1 << m
+    return mask
+
+
 def fp64_probe(api, device) -> float:
     """Measured FP64 FMA throughput (flop/s) of this GPU."""
     import torch
@@ -194,6 +215,50 @@ def fp64_probe(api, device) -> float:
     return blocks * 256 * 8 * iters * 2 / (e0.elapsed_time(e1) * 1e-3)
 
 
+def bench_batched(api, device, steps: int) -> dict:
+    """The batched form on the 4096-tube workload (N log-uniform in [64, 4096],
+    seed 20200320), every tube active: one persistent launch per RK stage,
+    `steps` steps captured in one CUDA graph; beside it the same tubes advanced
+    one by one through teno_rk3_step (one step each)."""
+    import numpy as np
+    import torch
+    from paper_2003_09145_gb300 import autotune, inputs
+    B = inputs.tube_batch(nprob=4096)
+    solver = api.BatchSolver(B.n, B.dx, np.full(B.nprob, np.inf), device=device)
+    U = torch.from_numpy(B.U0).to(device)
+    tuning = autotune.tune_batched(solver, U, steps=2, use_cache=False)
+    solver.capture(U, steps)
+    solver.graph.replay()                       # warm-up replay
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    solver.graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # the same tubes one by one (single-problem path, one step each)
+    singles = []
+    for p in range(B.nprob):
+        g = api.EulerGrid((int(B.n[p]),), (float(B.dx[p]),), (1,))
+        singles.append((api.Solver(g, device=device),
+                        torch.from_numpy(np.ascontiguousarray(B.U0[:, B.offsets[p]:B.offsets[p + 1]])).to(device)))
+    for s_, u_ in singles[:8]:
+        s_.step(u_)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for s_, u_ in singles:
+        s_.step(u_)
+    f1.record()
+    torch.cuda.synchronize()
+    ms_single = f0.elapsed_time(f1)
+    return {"value": B.ncell / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "workload": "4096 independent shock tubes, N log-uniform in [64,4096] (sum N = %d), FP64" % B.ncell,
+            "tuning": {"block": tuning[0], "ctas_per_sm": tuning[1]}, "graph_steps": steps,
+            "one_by_one": {"value": B.ncell / (ms_single * 1e-3) / 1e9, "unit": UNIT,
+                           "ms_per_step": ms_single}}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +267,7 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_CELLS_1D, help="cells per axis (default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint forms")
     args = ap.parse_args()
 
     dist, rank, world = _dist()
@@ -233,6 +299,14 @@ def main() -> None:
         solver.step(U, t_end)
     torch.cuda.synchronize()
     assert solver.status() == 0, "non-physical state during warm-up"
+
+    # share of scalar reconstructions that evaluate the cutoff test (flag m at
+    # which keeping every stencil is not guaranteed), on the timed start state
+    _, fl = api.rhs(grid, U, want_flags=True)
+    m = (fl >> 3).to(torch.int64)
+    keep_all = _keep_all_mask(grid.scheme)
+    cut_frac = float((((keep_all >> m) & 1) == 0).double().mean().item())
+    del fl, m
 
     # ---- device-resident timed region --------------------------------------
     clocks = ClockSampler(local)
@@ -268,7 +342,8 @@ def main() -> None:
     flux_ms, flux_n = kinds["flux"]
     nifc = (n + 1) * n * n
     flux_avg_s = flux_ms / flux_n * 1e-3
-    achieved = ALG_FLOPS_PER_IFACE_3D * nifc / flux_avg_s / 1e12
+    alg_per_ifc = ALG_FIXED_3D + 10 * ALG_PER_RECON + 10 * ALG_CUTOFF * cut_frac
+    achieved = alg_per_ifc * nifc / flux_avg_s / 1e12
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
@@ -282,7 +357,9 @@ def main() -> None:
                 "peak_source": f"derived: {SM_COUNT} SMs x {FP64_FLOP_PER_CLK_PER_SM} FP64 flop/clk x "
                                f"{sm_max:.0f} MHz (max SM clock)",
                 "fp64_probe_tflops": probe,
-                "alg_flops_per_interface": ALG_FLOPS_PER_IFACE_3D}
+                "alg_flops_per_interface": alg_per_ifc,
+                "cutoff_evaluated_fraction": cut_frac,
+                "survey_count_tflops": SURVEY_FLOPS_PER_IFACE_3D * nifc / flux_avg_s / 1e12}
 
     # ---- end to end through the public API with host buffers ---------------
     U_host = P.U0.copy()
@@ -310,6 +387,10 @@ def main() -> None:
     e2e = {"value": world * cells * args.steps / (ems * 1e-3) / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    forms = {}
+    if not args.no_forms:
+        forms["batched"] = bench_batched(api, device, max(args.steps, 4))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -321,7 +402,7 @@ def main() -> None:
                 "config": {"workload": WORKLOAD, "cells": cells, "grid": [n, n, n],
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (state %.0f MB)" % (nbytes / 1e6)},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
                 "gpu_launches": int(sum(kcount)),
                 "kernel_ms": {k: v[0] for k, v in kinds.items()},
                 "clocks": clk, "impl": "ours"}

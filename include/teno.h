@@ -127,6 +127,64 @@ teno_status teno_rk3_step(const teno_grid* g, double* U, double cfl,
                           double* dt_dev, void* ws, size_t ws_bytes,
                           void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched mode: many independent 1D problems advanced together.             */
+/* ------------------------------------------------------------------------ */
+
+/* A batch of nprob 1D Euler problems packed back to back: problem p owns the
+ * cells offsets[p] .. offsets[p+1]-1 of the SoA state U[3][ncell]
+ * (rho, rho u, E), has its own spacing dx[p], time t[p] and final time
+ * t_end[p], and its own global Lax-Friedrichs speeds.  Boundary type and
+ * scheme parameters are shared. */
+typedef struct {
+  int64_t nprob;     /* number of problems (>= 1)                            */
+  int64_t ncell;     /* total cells, offsets[nprob]                          */
+  int bc;            /* teno_bc of every problem's two ends                   */
+  double gamma;      /* eq. 4.7                                               */
+  double H;          /* eq. 3.2                                               */
+  int b_l, b_u;      /* eq. 3.1                                               */
+  double eps;        /* eq. 2.8                                               */
+} teno_batch;
+
+/* Launch shape of the batched kernel (NULL = 128 threads, 4 CTAs per SM).
+ * block: 64, 128 or 256 threads; ctas_per_sm: persistent CTAs per SM. */
+typedef struct {
+  int block;
+  int ctas_per_sm;
+} teno_batch_tuning;
+
+/* Workspace bytes of a batch (0 if b is invalid). */
+size_t teno_batch_workspace_bytes(const teno_batch* b);
+
+/*
+ * teno_batch_prepare -- checks the host copy of the offsets (offsets[0] = 0,
+ * offsets[nprob] = ncell, every problem at least one cell), stores the
+ * processing order (largest problems first) in the workspace and clears its
+ * status word.  Call once per workspace and batch layout before stepping; it
+ * waits for `stream`.
+ */
+teno_status teno_batch_prepare(const teno_batch* b, const int64_t* offsets_host,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * teno_rk3_step_batched -- one SSP-RK3 step (eq. 4.1-4.3) of every problem,
+ * three persistent launches (one per stage).  Per problem: dt = dt_fixed if
+ * dt_fixed > 0, else eq. dt1 with sigma = cfl from its own state, clipped to
+ * t_end[p] - t[p]; problems with t[p] >= t_end[p] are left unchanged.  The
+ * arithmetic per problem is exactly that of teno_rk3_step on the problem
+ * alone.
+ *   offsets : device int64[nprob + 1];  dx : device double[nprob]
+ *   U       : [in/out] device double[3 * ncell]
+ *   t_dev   : [in/out] device double[nprob];  t_end_dev : device double[nprob]
+ *   ws      : >= teno_batch_workspace_bytes(b), prepared by teno_batch_prepare.
+ */
+teno_status teno_rk3_step_batched(const teno_batch* b, const int64_t* offsets,
+                                  const double* dx, double* U, double* t_dev,
+                                  const double* t_end_dev, double cfl,
+                                  double dt_fixed,
+                                  const teno_batch_tuning* tuning, void* ws,
+                                  size_t ws_bytes, void* stream);
+
 /*
  * teno_get_device_status -- waits for `stream`, then returns in *status the
  * status recorded on the device in workspace `ws` since the last call

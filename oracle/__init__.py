@@ -101,7 +101,7 @@ def lib():
             L.or_euler_rk3_step.argtypes = [ctypes.c_int, _I64, _D, _I32, _PP, _D, ctypes.c_double]
             L.or_euler_rk3_step.restype = ctypes.c_int
             L.or_euler_run.argtypes = [ctypes.c_int, _I64, _D, _I32, _PP, _D, _D, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64]
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int, _I64]
             L.or_euler_run.restype = ctypes.c_int64
             L.or_scalar_rhs.argtypes = [ctypes.c_int64, ctypes.c_double, _PP, ctypes.c_int, _D, _D]
             L.or_scalar_rhs.restype = None
@@ -300,19 +300,30 @@ def euler_rk3_step(U: np.ndarray, n, dx, bc, dt: float, params: Params | None = 
 
 def euler_run(U: np.ndarray, n, dx, bc, t_end: float, sigma: float = 0.5,
               dt_fixed: float = 0.0, max_steps: int = 1 << 40, t0: float = 0.0,
-              params: Params | None = None):
+              params: Params | None = None, strict: bool = True):
     """Advance by CFL-limited SSP-RK3 steps to ``t_end`` (or ``max_steps``).
 
-    Returns ``(U_new, t, steps)``."""
+    Returns ``(U_new, t, steps)``.  ``strict``: raise at the first step whose
+    stages meet a non-physical state; otherwise continue (see ``euler_run_ex``)."""
+    V, t, k, _ = euler_run_ex(U, n, dx, bc, t_end, sigma, dt_fixed, max_steps, t0, params, strict)
+    return V, t, k
+
+
+def euler_run_ex(U, n, dx, bc, t_end, sigma=0.5, dt_fixed=0.0, max_steps=1 << 40, t0=0.0,
+                 params=None, strict=False):
+    """As euler_run, also returning the number of steps that met a non-physical
+    intermediate state: ``(U_new, t, steps, bad_steps)``."""
     p = params or Params()
     V = np.array(U, dtype=np.float64, copy=True, order="C")
     t = ctypes.c_double(t0)
+    nbad = ctypes.c_int64(0)
     pc = p.c()
     k = lib().or_euler_run(len(n), _shape3(n), _dx3(dx), _bc3(bc), ctypes.byref(pc), _dp(V),
-                           ctypes.byref(t), t_end, sigma, dt_fixed, int(max_steps))
+                           ctypes.byref(t), t_end, sigma, dt_fixed, int(max_steps), 1 if strict else 0,
+                           ctypes.byref(nbad))
     if k < 0:
         raise FloatingPointError("non-physical state in the oracle run")
-    return V, t.value, k
+    return V, t.value, k, nbad.value
 
 
 def scalar_rhs(u: np.ndarray, dx: float, mode: str = "lad", params: Params | None = None):

@@ -665,19 +665,25 @@ int or_euler_rk3_step(int ndim, const int64_t* n, const double* dx,
 /*
  * Advance with CFL steps until t_end or max_steps: each step takes
  * dt = min(dt_CFL(U^n), t_end - t) (dt_fixed > 0 replaces dt_CFL).
- * *t is updated; returns the number of steps taken, or -1 on a
- * non-physical state.
+ * *t is updated; returns the number of steps taken.  With strict != 0 the run
+ * stops and returns -1 at the first step in which a stage meets a
+ * non-physical state; otherwise it continues and counts such steps in
+ * *n_bad (nullable).
  */
 int64_t or_euler_run(int ndim, const int64_t* n, const double* dx,
                      const int* bc, const or_params* P, double* U, double* t,
                      double t_end, double sigma, double dt_fixed,
-                     int64_t max_steps) {
+                     int64_t max_steps, int strict, int64_t* n_bad) {
   int64_t k = 0;
+  if (n_bad) *n_bad = 0;
   while (k < max_steps && *t < t_end) {
     double dt = dt_fixed > 0.0 ? dt_fixed
                                : or_euler_dt(ndim, n, dx, P->gamma, sigma, U);
     if (t_end - *t < dt) dt = t_end - *t;
-    if (or_euler_rk3_step(ndim, n, dx, bc, P, U, dt) != 0) return -1;
+    if (or_euler_rk3_step(ndim, n, dx, bc, P, U, dt) != 0) {
+      if (strict) return -1;
+      if (n_bad) ++*n_bad;
+    }
     *t = *t + dt;
     ++k;
   }

@@ -38,6 +38,25 @@ class TenoGrid(ctypes.Structure):
     ]
 
 
+class TenoBatch(ctypes.Structure):
+    """Mirror of ``teno_batch``."""
+    _fields_ = [
+        ("nprob", ctypes.c_int64),
+        ("ncell", ctypes.c_int64),
+        ("bc", ctypes.c_int),
+        ("gamma", ctypes.c_double),
+        ("H", ctypes.c_double),
+        ("b_l", ctypes.c_int),
+        ("b_u", ctypes.c_int),
+        ("eps", ctypes.c_double),
+    ]
+
+
+class TenoBatchTuning(ctypes.Structure):
+    """Mirror of ``teno_batch_tuning``."""
+    _fields_ = [("block", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
 class TenoError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -56,6 +75,12 @@ SIGNATURES = [
     ("teno_rk3_step", ctypes.c_int, [_GP, _VP, ctypes.c_double, ctypes.c_double, _VP,
                                      ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
     ("teno_get_device_status", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int)]),
+    ("teno_batch_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(TenoBatch)]),
+    ("teno_batch_prepare", ctypes.c_int, [ctypes.POINTER(TenoBatch), ctypes.POINTER(ctypes.c_int64), _VP,
+                                          ctypes.c_size_t, _VP]),
+    ("teno_rk3_step_batched", ctypes.c_int, [ctypes.POINTER(TenoBatch), _VP, _VP, _VP, _VP, _VP,
+                                             ctypes.c_double, ctypes.c_double,
+                                             ctypes.POINTER(TenoBatchTuning), _VP, ctypes.c_size_t, _VP]),
     ("teno_rhs_noalloc", ctypes.c_int, [_GP, _VP, _VP, _VP]),
     ("teno_timer_begin", ctypes.c_int, []),
     ("teno_timer_end", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),

@@ -175,3 +175,77 @@ class Solver:
 
     def status(self) -> int:
         return device_status(self.ws)
+
+
+class BatchSolver:
+    """Many independent 1D Euler problems of uneven length (one SoA state
+    U[3][sum N]) advanced together by ``teno_rk3_step_batched``: one persistent
+    launch per SSP-RK3 stage, each problem with its own dx, time, final time
+    and Lax-Friedrichs speeds."""
+
+    def __init__(self, n, dx, t_end, bc: int = 1, scheme: Scheme | None = None, device="cuda",
+                 cfl: float = 0.5, tuning=None):
+        import numpy as np
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        n = np.asarray(n, dtype=np.int64)
+        self.nprob = int(n.size)
+        self.offsets_host = np.zeros(self.nprob + 1, dtype=np.int64)
+        self.offsets_host[1:] = np.cumsum(n)
+        self.ncell = int(self.offsets_host[-1])
+        s = scheme or Scheme()
+        self.c = _lib.TenoBatch(self.nprob, self.ncell, int(bc), s.gamma, s.H, s.b_l, s.b_u, s.eps)
+        self.offsets = torch.from_numpy(self.offsets_host).to(self.device)
+        self.dx = torch.as_tensor(np.asarray(dx, dtype=np.float64)).to(self.device)
+        self.t = torch.zeros(self.nprob, dtype=torch.float64, device=self.device)
+        self.t_end = torch.as_tensor(np.asarray(t_end, dtype=np.float64)).to(self.device)
+        self.cfl = float(cfl)
+        nb = self.lib.teno_batch_workspace_bytes(ctypes.byref(self.c))
+        if nb == 0:
+            raise ValueError("invalid batch")
+        self.ws = alloc_workspace(nb, self.device)
+        self.set_tuning(tuning)
+        offs = (ctypes.c_int64 * (self.nprob + 1))(*self.offsets_host.tolist())
+        _lib.check(self.lib.teno_batch_prepare(ctypes.byref(self.c), offs, _ptr(self.ws), self.ws.numel(),
+                                               _stream_ptr()), "teno_batch_prepare")
+        self.graph = None
+
+    def set_tuning(self, tuning) -> None:
+        """tuning: None or (block, ctas_per_sm)."""
+        self.tuning = None if tuning is None else _lib.TenoBatchTuning(int(tuning[0]), int(tuning[1]))
+
+    def step(self, U: torch.Tensor, dt_fixed: float = 0.0) -> None:
+        _check_state(U, 3, self.ncell)
+        tp = ctypes.byref(self.tuning) if self.tuning is not None else None
+        st = self.lib.teno_rk3_step_batched(ctypes.byref(self.c), _ptr(self.offsets), _ptr(self.dx), _ptr(U),
+                                            _ptr(self.t), _ptr(self.t_end), self.cfl, float(dt_fixed), tp,
+                                            _ptr(self.ws), self.ws.numel(), _stream_ptr())
+        _lib.check(st, "teno_rk3_step_batched")
+
+    def capture(self, U: torch.Tensor, steps: int, dt_fixed: float = 0.0):
+        """Capture ``steps`` batched steps into a CUDA graph (``self.graph``)."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        torch.cuda.current_stream(self.device).synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(steps):
+                self.step(U, dt_fixed)
+        self.graph = g
+        return g
+
+    def run(self, U: torch.Tensor, max_steps: int = 1 << 62, graph_steps: int = 32) -> int:
+        """Advance every problem to its t_end; graph replays of ``graph_steps``
+        steps between host checks of min(t_end - t).  Returns steps issued."""
+        if self.graph is None:
+            self.capture(U, graph_steps)
+        k = 0
+        while k < max_steps:
+            self.graph.replay()
+            k += graph_steps
+            if bool(torch.all(self.t >= self.t_end).item()):
+                break
+        return k
+
+    def status(self) -> int:
+        return device_status(self.ws)

@@ -29,6 +29,24 @@ static __constant__ double c_omega[8][3] = {
     {0.0, 0.6 / (0.6 + 0.3), 0.3 / (0.6 + 0.3)},
     {0.1 / (0.1 + 0.6 + 0.3), 0.6 / (0.1 + 0.6 + 0.3), 0.3 / (0.1 + 0.6 + 0.3)}};
 
+// The TENO flux of eq. 2.7 written on first differences e_k = v_{k+1} - v_k:
+// f^ = v2 + sum_k w_k e_k with, for weights omega = c_omega[sel],
+// w = (-omega_0/3, 5 omega_0/6 + omega_1/6, omega_1/3 + 2 omega_2/3, -omega_2/6)
+// (candidates of eq. 2.4-2.6 relative to v2: (5 e1/6 - e0/3), (e1/6 + e2/3),
+// (2 e2/3 - e3/6)).  With every stencil kept this is eq. 2.3.
+#define TENO_COEF_ROW(o0, o1, o2) \
+  {-(o0) / 3.0, 5.0 * (o0) / 6.0 + (o1) / 6.0, (o1) / 3.0 + 2.0 * (o2) / 3.0, -(o2) / 6.0}
+static __constant__ double c_coef[8][4] = {
+    TENO_COEF_ROW(0.0, 0.0, 0.0),
+    TENO_COEF_ROW(0.1 / 0.1, 0.0, 0.0),
+    TENO_COEF_ROW(0.0, 0.6 / 0.6, 0.0),
+    TENO_COEF_ROW(0.1 / (0.1 + 0.6), 0.6 / (0.1 + 0.6), 0.0),
+    TENO_COEF_ROW(0.0, 0.0, 0.3 / 0.3),
+    TENO_COEF_ROW(0.1 / (0.1 + 0.3), 0.0, 0.3 / (0.1 + 0.3)),
+    TENO_COEF_ROW(0.0, 0.6 / (0.6 + 0.3), 0.3 / (0.6 + 0.3)),
+    TENO_COEF_ROW(0.1 / (0.1 + 0.6 + 0.3), 0.6 / (0.1 + 0.6 + 0.3), 0.3 / (0.1 + 0.6 + 0.3))};
+#undef TENO_COEF_ROW
+
 constexpr int kMaxDim = 3;
 constexpr int kMaxVar = 5;
 constexpr int kMaxLadder = 16;
@@ -41,10 +59,12 @@ struct Scheme {
   double gamma;   // ratio of specific heats (eq. 4.7)
   double gm1;     // gamma - 1
   double eps;     // epsilon of eq. 2.8 / 3.2
+  double eps4;    // 4 eps (the indicators are carried scaled by 4)
   int b_l, b_u;   // magnitude bounds of eq. 3.1
   int nthr;       // B_u - B_l
   int top;        // largest power of two <= nthr (binary-search start)
   unsigned keep_all;  // bit m set: every chi_k >= C_T is guaranteed at this m
+  int keep_idx;   // keep_all = {m >= B_l + keep_idx + 1}: tau <= thr[keep_idx] dmin (-1: none)
   // m = B_l + #{ j in 1..B_u-B_l : tau <= thr[j-1] * min_k(beta_k + eps) }.
   // With theta = 1/(1 + max_k chi~_k / H) and max_k chi~_k = tau / min_k(beta_k
   // + eps) (eq. 3.2), floor(theta (B_u - B_l)) >= j  <=>  max chi~ <=
@@ -90,9 +110,8 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 // Arithmetic (all exact rewrites of the paper's formulas, evaluated in FP64):
 //  * with first differences e_k = v_{k+1} - v_k, the indicator terms of
 //    eq. 2.9-2.11 are a_0 = e1 - e0, c_0 = 3 e1 - e0, a_1 = e2 - e1,
-//    c_1 = -(e1 + e2), a_2 = e3 - e2, c_2 = e3 - 3 e2, and the candidate
-//    fluxes of eq. 2.4-2.6 are v2 + (5 e1/6 - e0/3), v2 + (e1/6 + e2/3),
-//    v2 + (2 e2/3 - e3/6);
+//    c_1 = -(e1 + e2), a_2 = e3 - e2, c_2 = e3 - 3 e2, and the weighted sum
+//    of the candidate fluxes (eq. 2.4-2.7) is v2 + sum_k c_coef[sel][k] e_k;
 //  * m of eq. 3.1 counts the thresholds tau <= thr_j * min_k(beta_k + eps)
 //    (see Scheme), found by binary search over the decreasing thresholds;
 //  * the cutoff chi_k >= C_T of eq. 2.13-2.14 is decided without division:
@@ -102,26 +121,34 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 //    holds for every k (Scheme::keep_all), all stencils are kept without
 //    evaluating gamma.
 // ---------------------------------------------------------------------------
+template <bool WITH_M>
 __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
                                             double v3, double v4,
                                             const Scheme& S, unsigned& flag) {
   const double e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
-  // eq. 2.9-2.11
-  const double k13_12 = 13.0 / 12.0;
+  // eq. 2.9-2.11 scaled by 4: 4 beta_k = (13/3) a_k^2 + c_k^2.  Every use of
+  // beta_k below is through ratios tau / (beta_k + eps) and products that are
+  // homogeneous in (beta, tau, eps), so the common factor 4 (with eps -> 4 eps)
+  // leaves m and delta unchanged.
+  const double k13_3 = 13.0 / 3.0;
   const double a0 = e1 - e0, a1 = e2 - e1, a2 = e3 - e2;
-  const double h0 = 0.5 * fma(3.0, e1, -e0);
-  const double h1 = 0.5 * (e1 + e2);
-  const double h2 = 0.5 * fma(-3.0, e2, e3);
-  const double beta0 = fma(k13_12 * a0, a0, h0 * h0);
-  const double beta1 = fma(k13_12 * a1, a1, h1 * h1);
-  const double beta2 = fma(k13_12 * a2, a2, h2 * h2);
-  // eq. 2.12
+  const double c0 = fma(3.0, e1, -e0);
+  const double c1 = e1 + e2;
+  const double c2 = fma(-3.0, e2, e3);
+  const double beta0 = fma(k13_3 * a0, a0, c0 * c0);
+  const double beta1 = fma(k13_3 * a1, a1, c1 * c1);
+  const double beta2 = fma(k13_3 * a2, a2, c2 * c2);
+  // eq. 2.12 (scaled)
   const double tau = fabs(beta2 - beta0);
-  const double d0 = beta0 + S.eps, d1 = beta1 + S.eps, d2 = beta2 + S.eps;
-  // eq. 3.1-3.2: m = B_l + #{j : tau <= thr_j * min_k D_k}
-  const unsigned long long bmin = min(dbits(d0), min(dbits(d1), dbits(d2)));
-  const double dmin = __longlong_as_double(static_cast<long long>(bmin));
+  // eq. 3.1-3.2: m = B_l + #{j : tau <= thr_j * min_k D_k}, D_k = beta_k + eps
+  const unsigned long long bmin = min(dbits(beta0), min(dbits(beta1), dbits(beta2)));
+  const double dmin = __longlong_as_double(static_cast<long long>(bmin)) + S.eps4;
   const unsigned long long btau = dbits(tau);
+  if (!WITH_M && S.keep_idx >= 0 && btau <= dbits(S.thr[S.keep_idx] * dmin)) {
+    // m lies in the keep-all range (a suffix of B_l..B_u): every stencil is kept
+    flag = 7u;
+    return fma(c_coef[7][0], e0, fma(c_coef[7][1], e1, fma(c_coef[7][2], e2, fma(c_coef[7][3], e3, v2))));
+  }
   int cnt = 0;
 #pragma unroll
   for (int step = 8; step >= 1; step >>= 1) {
@@ -136,6 +163,7 @@ __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
   if (!((S.keep_all >> m) & 1u)) {
     // eq. 3.4, eq. 2.8, eq. 2.13-2.14 (division-free form, see above)
     const double ct = c_lad[m];
+    const double d0 = beta0 + S.eps4, d1 = beta1 + S.eps4, d2 = beta2 + S.eps4;
     const double n0 = d0 + tau, n1 = d1 + tau, n2 = d2 + tau;
     const double p0 = n0 * (d1 * d2), p1 = n1 * (d0 * d2), p2 = n2 * (d0 * d1);
     double q0 = p0 * p0, q1 = p1 * p1, q2 = p2 * p2;
@@ -162,11 +190,8 @@ __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
     }
   }
   flag = sel | (static_cast<unsigned>(m) << 3);
-  // eq. 2.4-2.6 relative to v2, eq. 2.15, eq. 2.7
-  const double r0 = fma(5.0 / 6.0, e1, (-1.0 / 3.0) * e0);
-  const double r1 = fma(1.0 / 6.0, e1, (1.0 / 3.0) * e2);
-  const double r2 = fma(2.0 / 3.0, e2, (-1.0 / 6.0) * e3);
-  return fma(c_omega[sel][0], r0, fma(c_omega[sel][1], r1, fma(c_omega[sel][2], r2, v2)));
+  // eq. 2.4-2.7 and 2.15 on first differences (c_coef)
+  return fma(c_coef[sel][0], e0, fma(c_coef[sel][1], e1, fma(c_coef[sel][2], e2, fma(c_coef[sel][3], e3, v2))));
 }
 
 }  // namespace teno

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "teno_device.cuh"
+#include "teno_flux.cuh"
 #include "teno_launch.h"
 
 namespace teno {
@@ -28,7 +29,8 @@ namespace teno {
 // p = (gamma-1)(E - (rho/2)|u|^2), c = sqrt(gamma p / rho), so the wave
 // speeds, and through them alpha and the CFL step, are the correctly rounded
 // values of these formulas.
-// aux layout: [ndim + 3][ncell]: u_0..u_{ndim-1}, p, sqrt(rho), (E+p)/sqrt(rho).
+// aux layout: [ndim + 3][ncell]: u_0/2..u_{ndim-1}/2, p/2, sqrt(rho),
+// (E+p)/sqrt(rho).
 // alpha layout (bit patterns of non-negative doubles): [ndim][3] =
 // max|u_d - c|, max|u_d|, max|u_d + c|.
 // ---------------------------------------------------------------------------
@@ -45,24 +47,8 @@ __global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
   bool bad = false;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
-    double rho = U[c];
-    double E = U[(NVAR - 1) * ncell + c];
-    double u[NDIM];
-    double q2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < NDIM; ++k) {
-      u[k] = __ddiv_rn(U[(1 + k) * ncell + c], rho);
-      q2 = __dadd_rn(q2, __dmul_rn(u[k], u[k]));
-    }
-    double p = __dmul_rn(gamma - 1.0, __dsub_rn(E, __dmul_rn(__dmul_rn(0.5, rho), q2)));
-    double cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
-    double sr = __dsqrt_rn(rho);
-    if (!(rho > 0.0) || !(p > 0.0) || !isfinite(E) || !isfinite(q2)) bad = true;
-#pragma unroll
-    for (int k = 0; k < NDIM; ++k) aux[k * ncell + c] = u[k];
-    aux[NDIM * ncell + c] = p;
-    aux[(NDIM + 1) * ncell + c] = sr;
-    aux[(NDIM + 2) * ncell + c] = (E + p) / sr;
+    double u[NDIM], cs;
+    if (!cell_primitives<NDIM>(U, ncell, c, gamma, aux, u, cs)) bad = true;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       lam[d][0] = fmax(lam[d][0], fabs(__dsub_rn(u[d], cs)));
@@ -99,37 +85,12 @@ __global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
 // Interface fluxes of direction DIR.
 // ---------------------------------------------------------------------------
 
-// Characteristic projection of one vector X (conservative ordering) onto the
-// left eigenvectors of the Roe state (reading of the convective-term
-// paragraph of Sec. 4; rows as in the library's design notes):
-//   l_0 X = A + B,  l_{nvar-1} X = A - B,  l_1 X = X_0 - 2A,
-//   l_t X = X_{1+t} - u_t X_0 (shear, t != DIR),
-// with A = (b2 X_0 - b1 (u . X_mom - X_E)) / 2 and B = (u_n X_0 - X_{1+n})/(2c).
-template <int NDIM, int DIR>
-__device__ __forceinline__ void project(const double (&X)[NDIM + 2],
-                                        const double (&u)[NDIM], double hb1,
-                                        double hb2, double hic,
-                                        double (&w)[NDIM + 2]) {
-  constexpr int NVAR = NDIM + 2;
-  double S = -X[NVAR - 1];
-#pragma unroll
-  for (int k = 0; k < NDIM; ++k) S = fma(u[k], X[1 + k], S);
-  double A = fma(hb2, X[0], -hb1 * S);
-  double B = fma(u[DIR], X[0], -X[1 + DIR]) * hic;
-  w[0] = A + B;
-  w[1] = fma(-2.0, A, X[0]);
-  int f = 2;
-#pragma unroll
-  for (int t = 0; t < NDIM; ++t) {
-    if (t == DIR) continue;
-    w[f] = fma(-u[t], X[0], X[1 + t]);
-    ++f;
-  }
-  w[NVAR - 1] = A - B;
-}
+#ifndef TENO_FLUX_MINBLOCKS
+#define TENO_FLUX_MINBLOCKS 1
+#endif
 
-template <int NDIM, int DIR>
-__global__ void __launch_bounds__(128) flux_kernel(
+template <int NDIM, int DIR, bool WITH_FLAGS>
+__global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
     const double* __restrict__ U, const double* __restrict__ aux,
     const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
     uint8_t* __restrict__ flags, int* __restrict__ status, Grid G, Scheme S) {
@@ -165,84 +126,13 @@ __global__ void __launch_bounds__(128) flux_kernel(
                        : (DIR == 1) ? i2 * G.n[1] * G.n[0] + i0
                                     : i1 * G.n[0] + i0;
 
-    // six-point stencil i-2..i+3 with i = id - 1
-    double Ux[6][NVAR], un[6], pn[6];
-    double sr2, sr3, sh2, sh3, uu2[NDIM], uu3[NDIM];
+    int64_t cells[6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const int64_t c = base + ghost(id - 3 + j, nd, bcd) * stride_d;
-#pragma unroll
-      for (int v = 0; v < NVAR; ++v) Ux[j][v] = U[v * ncell + c];
-      un[j] = aux[DIR * ncell + c];
-      pn[j] = aux[NDIM * ncell + c];
-      if (j == 2 || j == 3) {
-        double* uu = (j == 2) ? uu2 : uu3;
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) uu[k] = (k == DIR) ? un[j] : aux[k * ncell + c];
-        if (j == 2) {
-          sr2 = aux[(NDIM + 1) * ncell + c];
-          sh2 = aux[(NDIM + 2) * ncell + c];
-        } else {
-          sr3 = aux[(NDIM + 1) * ncell + c];
-          sh3 = aux[(NDIM + 2) * ncell + c];
-        }
-      }
-    }
-    // Roe average of cells i and i+1
-    const double inv = 1.0 / (sr2 + sr3);
-    double u[NDIM];
-    double q2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < NDIM; ++k) {
-      u[k] = fma(sr2, uu2[k], sr3 * uu3[k]) * inv;
-      q2 = fma(u[k], u[k], q2);
-    }
-    const double H = (sh2 + sh3) * inv;
-    const double c2 = S.gm1 * fma(-0.5, q2, H);
-    if (!(c2 > 0.0)) atomicOr(status, kStatusNonphysical);
-    const double ic = rsqrt(c2);
-    const double cs = c2 * ic;
-    const double b1 = S.gm1 * ic * ic;
-    const double b2 = 0.5 * b1 * q2;
-    const double hb1 = 0.5 * b1, hb2 = 0.5 * b2, hic = 0.5 * ic;
-
-    // Characteristic values w = L U and the split fluxes v+- = (g +- alpha w)/2
-    // with g = L F.  Since F(U) = u_d U + p (0, e_d, u_d) (eq. 4.7),
-    // g = u_d w + p z with z = (hb1 du - hic, -2 hb1 du, 0.., hb1 du + hic),
-    // du = u_d - u~_d, so v+- = (u_d/2 +- alpha/2) w + (p/2) z.
-    double fchar[NVAR];
-    double vp[6][NVAR], vm[6][NVAR];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      double w[NVAR];
-      project<NDIM, DIR>(Ux[j], u, hb1, hb2, hic, w);
-      const double hu = 0.5 * un[j];
-      const double hp = 0.5 * pn[j];
-      const double zeta = hb1 * (un[j] - u[DIR]);
-      const double t0 = hp * (zeta - hic);
-      const double tE = hp * (zeta + hic);
-      const double t1 = -2.0 * (hp * zeta);
-      vp[j][0] = fma(hu + alpha[0], w[0], t0);
-      vm[j][0] = fma(hu - alpha[0], w[0], t0);
-      vp[j][NVAR - 1] = fma(hu + alpha[NVAR - 1], w[NVAR - 1], tE);
-      vm[j][NVAR - 1] = fma(hu - alpha[NVAR - 1], w[NVAR - 1], tE);
-      const double sp = hu + alpha[1], sm = hu - alpha[1];
-      vp[j][1] = fma(sp, w[1], t1);
-      vm[j][1] = fma(sm, w[1], t1);
-#pragma unroll
-      for (int f = 2; f < NVAR - 1; ++f) {
-        vp[j][f] = sp * w[f];
-        vm[j][f] = sm * w[f];
-      }
-    }
+    for (int j = 0; j < 6; ++j) cells[j] = base + ghost(id - 3 + j, nd, bcd) * stride_d;
+    double out[NVAR];
     unsigned fl[NVAR][2];
-#pragma unroll
-    for (int s = 0; s < NVAR; ++s) {
-      const double hp = teno5_lad(vp[0][s], vp[1][s], vp[2][s], vp[3][s], vp[4][s], S, fl[s][0]);
-      const double hm = teno5_lad(vm[5][s], vm[4][s], vm[3][s], vm[2][s], vm[1][s], S, fl[s][1]);
-      fchar[s] = hp + hm;
-    }
-    if (flags) {
+    interface_flux<NDIM, DIR, WITH_FLAGS>(U, aux, ncell, cells, alpha, S, out, fl, status);
+    if (WITH_FLAGS) {
       // direction block offset is applied by the caller through `flags`
 #pragma unroll
       for (int s = 0; s < NVAR; ++s)
@@ -250,28 +140,6 @@ __global__ void __launch_bounds__(128) flux_kernel(
         for (int side = 0; side < 2; ++side)
           flags[(int64_t)(s * 2 + side) * nifc + q] = (uint8_t)fl[s][side];
     }
-    // back-projection F^ = R f^char, columns r_0 = (1, u - c e_n, H - u_n c),
-    // r_1 = (1, u, q2/2), r_t = (0, e_t, u_t), r_{nvar-1} = (1, u + c e_n, H + u_n c)
-    const double sa = fchar[0] + fchar[NVAR - 1];
-    const double da = fchar[NVAR - 1] - fchar[0];
-    const double rho_f = sa + fchar[1];
-    double out[NVAR];
-    out[0] = rho_f;
-    double eng = fma(H, sa, fma(u[DIR] * cs, da, 0.5 * q2 * fchar[1]));
-    {
-      int f = 2;
-#pragma unroll
-      for (int k = 0; k < NDIM; ++k) {
-        if (k == DIR) {
-          out[1 + k] = fma(u[k], rho_f, cs * da);
-        } else {
-          out[1 + k] = fma(u[k], rho_f, fchar[f]);
-          eng = fma(u[k], fchar[f], eng);
-          ++f;
-        }
-      }
-    }
-    out[NVAR - 1] = eng;
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
   }
@@ -312,21 +180,8 @@ __global__ void __launch_bounds__(256) diff_kernel(
       double d = (Fhat[v * nifc + left] - Fhat[v * nifc + right]) * idx;
       const int64_t e = v * ncell + c;
       if (acc) d += R[e];
-      switch (mode) {
-        case 0:
-        case 1:
-          R[e] = d;
-          break;
-        case 2:
-          Uout[e] = fma(dt, d, Un[e]);
-          break;
-        case 3:
-          Uout[e] = fma(0.25 * dt, d, fma(0.75, Un[e], 0.25 * Uk[e]));
-          break;
-        default:
-          Uout[e] = fma((2.0 / 3.0) * dt, d, fma(1.0 / 3.0, Un[e], (2.0 / 3.0) * Uk[e]));
-          break;
-      }
+      if (mode <= 1) R[e] = d;
+      else Uout[e] = stage_value(mode, dt, d, Un, Uk, e);
     }
   }
 }
@@ -381,6 +236,7 @@ Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u) {
   S.gamma = gamma;
   S.gm1 = gamma - 1.0;
   S.eps = eps;
+  S.eps4 = 4.0 * eps;
   S.b_l = b_l;
   S.b_u = b_u;
   const int K = b_u - b_l;
@@ -401,6 +257,15 @@ Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u) {
     const double x = 1.0 + S.thr[c - 1];
     const double x6 = x * x * x * x * x * x;
     if (3.0 * x6 * kPow10Neg[m] <= 1.0 - 1e-9) S.keep_all |= 1u << m;
+  }
+  // the keep-all set is a suffix of B_l..B_u (the bound loosens as m grows)
+  S.keep_idx = -1;
+  for (int c = 1; c <= K; ++c) {
+    const unsigned suffix = ((1u << (b_u + 1)) - 1u) & ~((1u << (b_l + c)) - 1u);
+    if (S.keep_all == suffix) {
+      S.keep_idx = c - 1;
+      break;
+    }
   }
   return S;
 }
@@ -433,7 +298,10 @@ static void flux_launch(int blocks, int threads, cudaStream_t st, const double* 
                         const double* aux, const unsigned long long* alpha,
                         double* Fhat, uint8_t* flags, int* status, const Grid& G,
                         const Scheme& S) {
-  flux_kernel<NDIM, DIR><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
+  if (flags)
+    flux_kernel<NDIM, DIR, true><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
+  else
+    flux_kernel<NDIM, DIR, false><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
 }
 
 cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux,

@@ -131,3 +131,36 @@ def test_four_quadrant_2048_sampled(api, oracle):
 @pytest.mark.slow
 def test_turbulence_256_sampled(api, oracle):
     _sampled(api, oracle, inputs.solenoidal_turbulence(n=256), 2000, 2)
+
+
+@pytest.mark.parametrize("case", ["sod", "rand2d", "rand3d", "turb"])
+def test_flag_free_path_identical(api, case):
+    """Without a flag output the kernel decides 'all stencils kept' with a single
+    comparison; the right-hand side must equal the flag-producing path bit for bit."""
+    P = {"sod": lambda: inputs.shock_tube(300),
+         "rand2d": lambda: inputs.Problem("r2", inputs.random_discontinuous_state(2, (40, 30), seed=5),
+                                          (40, 30), (0.02, 0.03), (1, 0), 0.0),
+         "rand3d": lambda: inputs.Problem("r3", inputs.random_discontinuous_state(3, (12, 10, 9), seed=6),
+                                          (12, 10, 9), (0.1, 0.1, 0.1), (0, 1, 0), 0.0),
+         "turb": lambda: inputs.solenoidal_turbulence(n=32)}[case]()
+    a, _ = _gpu_rhs(api, P, want_flags=True)
+    b, _ = _gpu_rhs(api, P, want_flags=False)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_cuda_graph_replay_matches_eager(api):
+    """Steps captured in a CUDA graph give the same state as eager steps."""
+    P = inputs.shu_osher(1024)
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    U1 = torch.from_numpy(P.U0).cuda()
+    U2 = U1.clone()
+    s1 = api.Solver(grid)
+    for _ in range(11):
+        s1.step(U1, P.t_end)
+    s2 = api.Solver(grid)
+    s2.capture(U2, 5, P.t_end)        # one eager warm-up step + graph of 5
+    s2.graph.replay()
+    s2.graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(U1, U2)
+    assert s1.t.item() == s2.t.item()
