@@ -185,6 +185,42 @@ teno_status teno_rk3_step_batched(const teno_batch* b, const int64_t* offsets,
                                   const teno_batch_tuning* tuning, void* ws,
                                   size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Adjoint (vector-Jacobian products).                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes of teno_rhs_adjoint (op = TENO_OP_RHS_ADJOINT) or
+ * teno_rk3_step_adjoint (op = TENO_OP_RK3_ADJOINT) on grid g; 0 if invalid. */
+size_t teno_adjoint_workspace_bytes(const teno_grid* g, int op);
+
+/*
+ * teno_rhs_adjoint -- U_bar += J(U)^T dUdt_bar, J = dL/dU of the right-hand
+ * side of teno_rhs (eq. 2.2).  The stencil selections (delta of eq. 2.14 and
+ * m of eq. 3.1) are held at their values for U: the cutoff is piecewise
+ * constant, so J is the derivative of L almost everywhere.  The global
+ * Lax-Friedrichs speed max_cells |lambda_s| is differentiated through its
+ * arg-max cell (the lowest linear index on ties).  Deterministic: no atomics
+ * on floating-point data.
+ *   U, dUdt_bar : [in] device, nvar * ncell doubles.
+ *   U_bar       : [in/out] device, accumulated; must not alias the inputs.
+ *   ws          : >= teno_adjoint_workspace_bytes(g, TENO_OP_RHS_ADJOINT).
+ */
+teno_status teno_rhs_adjoint(const teno_grid* g, const double* U,
+                             const double* dUdt_bar, double* U_bar, void* ws,
+                             size_t ws_bytes, void* stream);
+
+/*
+ * teno_rk3_step_adjoint -- reverse of one SSP-RK3 step of fixed size dt
+ * (eq. 4.1-4.3) taken from U_n: recomputes the stages U1, U2 and returns
+ *   Ubar_n = dJ/dU_n given Ubar_next = dJ/dU_{n+1}
+ * (Ubar_n is overwritten; it may alias Ubar_next).  dt carries no gradient.
+ *   ws : >= teno_adjoint_workspace_bytes(g, TENO_OP_RK3_ADJOINT).
+ */
+teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n,
+                                  double dt, const double* Ubar_next,
+                                  double* Ubar_n, void* ws, size_t ws_bytes,
+                                  void* stream);
+
 /*
  * teno_get_device_status -- waits for `stream`, then returns in *status the
  * status recorded on the device in workspace `ws` since the last call

@@ -249,3 +249,85 @@ class BatchSolver:
 
     def status(self) -> int:
         return device_status(self.ws)
+
+
+def rhs_adjoint(grid: EulerGrid, U: torch.Tensor, dUdt_bar: torch.Tensor, U_bar: torch.Tensor | None = None,
+                ws: torch.Tensor | None = None) -> torch.Tensor:
+    """U_bar (+)= J(U)^T dUdt_bar with the stencil selections held at their values
+    for U (``teno_rhs_adjoint``).  Returns U_bar."""
+    _check_state(U, grid.nvar, grid.ncell)
+    _check_state(dUdt_bar, grid.nvar, grid.ncell, "dUdt_bar")
+    out = torch.zeros_like(U) if U_bar is None else U_bar
+    if ws is None:
+        nb = grid.lib.teno_adjoint_workspace_bytes(ctypes.byref(grid.c), _lib.OP_RHS_ADJOINT)
+        ws = alloc_workspace(nb, U.device)
+    st = grid.lib.teno_rhs_adjoint(ctypes.byref(grid.c), _ptr(U), _ptr(dUdt_bar), _ptr(out), _ptr(ws),
+                                   ws.numel(), _stream_ptr())
+    _lib.check(st, "teno_rhs_adjoint")
+    return out
+
+
+class AdjointStepper:
+    """Reverse of fixed-dt SSP-RK3 steps (``teno_rk3_step_adjoint``)."""
+
+    def __init__(self, grid: EulerGrid, device="cuda"):
+        self.grid = grid
+        nb = grid.lib.teno_adjoint_workspace_bytes(ctypes.byref(grid.c), _lib.OP_RK3_ADJOINT)
+        self.ws = alloc_workspace(nb, torch.device(device))
+
+    def step(self, U_n: torch.Tensor, dt: float, Ubar_next: torch.Tensor, Ubar_n: torch.Tensor | None = None):
+        g = self.grid
+        out = torch.empty_like(Ubar_next) if Ubar_n is None else Ubar_n
+        st = g.lib.teno_rk3_step_adjoint(ctypes.byref(g.c), _ptr(U_n), float(dt), _ptr(Ubar_next), _ptr(out),
+                                         _ptr(self.ws), self.ws.numel(), _stream_ptr())
+        _lib.check(st, "teno_rk3_step_adjoint")
+        return out
+
+    def status(self) -> int:
+        return device_status(self.ws)
+
+
+class TenoRK3Rollout(torch.autograd.Function):
+    """``steps`` fixed-dt SSP-RK3 steps (eq. 4.1-4.3) of the TENO5-LAD Euler
+    solver as a differentiable map U0 -> U_steps.
+
+    Forward keeps one state every ``checkpoint_every`` steps; backward replays
+    each segment from its checkpoint (storing the segment's states) and runs the
+    step adjoints in reverse (RK-stage checkpointing: the stages themselves are
+    recomputed inside ``teno_rk3_step_adjoint``)."""
+
+    @staticmethod
+    def forward(ctx, U0: torch.Tensor, grid: EulerGrid, steps: int, dt: float, checkpoint_every: int = 0):
+        k = checkpoint_every if checkpoint_every > 0 else max(1, int(round(steps ** 0.5)))
+        solver = Solver(grid, device=U0.device)
+        U = U0.detach().clone()
+        ckpts = {0: U.clone()}
+        for n in range(steps):
+            solver.step(U, float("inf"), dt_fixed=dt)
+            if (n + 1) % k == 0 and n + 1 < steps:
+                ckpts[n + 1] = U.clone()
+        ctx.grid, ctx.steps, ctx.dt, ctx.k, ctx.ckpts, ctx.solver = grid, steps, dt, k, ckpts, solver
+        return U
+
+    @staticmethod
+    def backward(ctx, Ubar: torch.Tensor):
+        grid, steps, dt, k = ctx.grid, ctx.steps, ctx.dt, ctx.k
+        adj = AdjointStepper(grid, device=Ubar.device)
+        solver = ctx.solver
+        B = Ubar.detach().contiguous().clone()
+        seg_starts = sorted(ctx.ckpts)
+        for s0 in reversed(seg_starts):
+            s1 = min(s0 + k, steps)
+            states = [ctx.ckpts[s0].clone()]
+            for _ in range(s0, s1 - 1):
+                U = states[-1].clone()
+                solver.step(U, float("inf"), dt_fixed=dt)
+                states.append(U)
+            for n in range(s1 - 1, s0 - 1, -1):
+                adj.step(states[n - s0], dt, B, B)
+        return B, None, None, None, None
+
+
+def rollout(U0: torch.Tensor, grid: EulerGrid, steps: int, dt: float, checkpoint_every: int = 0) -> torch.Tensor:
+    """Differentiable fixed-dt rollout (see TenoRK3Rollout)."""
+    return TenoRK3Rollout.apply(U0, grid, steps, dt, checkpoint_every)

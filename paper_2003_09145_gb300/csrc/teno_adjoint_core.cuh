@@ -1,0 +1,297 @@
+// teno_adjoint_core.cuh -- vector-Jacobian product of one interface flux of the
+// TENO5-LAD Euler right-hand side, with the stencil selections frozen (the
+// cutoff of eq. 2.14 is a piecewise-constant selector, so with delta fixed the
+// reconstruction of eq. 2.4-2.7 is linear in the split fluxes).
+//
+// Forward map at the interface i+1/2 of direction DIR, points j = 0..5 being
+// cells i-2..i+3:
+//   U_j -> (rho, u, p)_j -> F_j (eq. 4.7)
+//   (U_2, U_3) -> Roe state (u~, H~) -> c, b1 = (gamma-1)/c^2, b2 = b1 |u~|^2/2
+//            -> L (left eigenvectors, rows), R (right eigenvectors, columns)
+//   w_j = L U_j,  g_j = L F_j
+//   fchar_s = sum_j P_sj g_js + alpha_s M_sj w_js
+//     with P = (A+ + A-)/2, M = (A+ - A-)/2 and A+- the linear weights of the
+//     frozen reconstructions of f^+ (points 0..4) and f^- (points 5..1)
+//   F^ = R fchar
+// Reverse pass: given Fbar = dJ/dF^, returns dJ/dU_j for the six points and
+// dJ/dalpha_s.  Plain FP64 arithmetic, usable on host and device.
+#pragma once
+
+#include <cmath>
+
+#ifdef __CUDACC__
+#define TENO_HD __host__ __device__
+#else
+#define TENO_HD
+#endif
+
+namespace teno_adj {
+
+// Linear weights of the reconstruction with selection `sel` (delta bits):
+// f^ = sum_k a[k] v_k over v = (f_{i-2}, ..., f_{i+2}), from the TENO weights
+// of eq. 2.15 and the candidate fluxes of eq. 2.4-2.6.
+TENO_HD inline void lin_weights(unsigned sel, double a[5]) {
+  const double d0 = double(sel & 1u), d1 = double((sel >> 1) & 1u), d2 = double((sel >> 2) & 1u);
+  const double s = d0 * 0.1 + d1 * 0.6 + d2 * 0.3;
+  const double o0 = d0 * 0.1 / s, o1 = d1 * 0.6 / s, o2 = d2 * 0.3 / s;
+  a[0] = o0 / 3.0;
+  a[1] = -7.0 / 6.0 * o0 - 1.0 / 6.0 * o1;
+  a[2] = 11.0 / 6.0 * o0 + 5.0 / 6.0 * o1 + 1.0 / 3.0 * o2;
+  a[3] = 1.0 / 3.0 * o1 + 5.0 / 6.0 * o2;
+  a[4] = -1.0 / 6.0 * o2;
+}
+
+template <int NDIM, int DIR>
+TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double (&alpha)[NDIM + 2],
+                                  const unsigned (&sel)[NDIM + 2][2], double gamma,
+                                  const double (&Fb)[NDIM + 2], double (&Ub)[6][NDIM + 2],
+                                  double (&ab)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  constexpr int E = NDIM + 1;
+  constexpr int N = DIR;
+  const double gm1 = gamma - 1.0;
+
+  // ---- forward --------------------------------------------------------------
+  double rho[6], u[6][NDIM], p[6], q[6], F[6][NV];
+  for (int j = 0; j < 6; ++j) {
+    rho[j] = Up[j][0];
+    q[j] = 0.0;
+    for (int k = 0; k < NDIM; ++k) {
+      u[j][k] = Up[j][1 + k] / rho[j];
+      q[j] += u[j][k] * u[j][k];
+    }
+    p[j] = gm1 * (Up[j][E] - 0.5 * rho[j] * q[j]);
+    F[j][0] = rho[j] * u[j][N];
+    for (int k = 0; k < NDIM; ++k) F[j][1 + k] = Up[j][1 + k] * u[j][N] + (k == N ? p[j] : 0.0);
+    F[j][E] = u[j][N] * (Up[j][E] + p[j]);
+  }
+  const double sa = sqrt(rho[2]), sb = sqrt(rho[3]), S = sa + sb;
+  const double Ha = (Up[2][E] + p[2]) / rho[2], Hb = (Up[3][E] + p[3]) / rho[3];
+  double ut[NDIM], q2 = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    ut[k] = (sa * u[2][k] + sb * u[3][k]) / S;
+    q2 += ut[k] * ut[k];
+  }
+  const double H = (sa * Ha + sb * Hb) / S;
+  const double c2 = gm1 * (H - 0.5 * q2);
+  const double c = sqrt(c2);
+  const double b1 = gm1 / c2;
+  const double b2 = 0.5 * b1 * q2;
+  const double un = ut[N];
+
+  double L[NV][NV], R[NV][NV];
+  for (int r = 0; r < NV; ++r)
+    for (int k = 0; k < NV; ++k) L[r][k] = R[r][k] = 0.0;
+  R[0][0] = 1.0;
+  for (int k = 0; k < NDIM; ++k) R[1 + k][0] = ut[k] - (k == N ? c : 0.0);
+  R[E][0] = H - un * c;
+  L[0][0] = 0.5 * (b2 + un / c);
+  for (int k = 0; k < NDIM; ++k) L[0][1 + k] = 0.5 * (-b1 * ut[k] - (k == N ? 1.0 / c : 0.0));
+  L[0][E] = 0.5 * b1;
+  R[0][1] = 1.0;
+  for (int k = 0; k < NDIM; ++k) R[1 + k][1] = ut[k];
+  R[E][1] = 0.5 * q2;
+  L[1][0] = 1.0 - b2;
+  for (int k = 0; k < NDIM; ++k) L[1][1 + k] = b1 * ut[k];
+  L[1][E] = -b1;
+  int tf[NDIM > 1 ? NDIM - 1 : 1];   // tangential direction of shear field 2 + i
+  {
+    int f = 2;
+    for (int t = 0; t < NDIM; ++t) {
+      if (t == N) continue;
+      tf[f - 2] = t;
+      R[1 + t][f] = 1.0;
+      R[E][f] = ut[t];
+      L[f][0] = -ut[t];
+      L[f][1 + t] = 1.0;
+      ++f;
+    }
+  }
+  R[0][E] = 1.0;
+  for (int k = 0; k < NDIM; ++k) R[1 + k][E] = ut[k] + (k == N ? c : 0.0);
+  R[E][E] = H + un * c;
+  L[E][0] = 0.5 * (b2 - un / c);
+  for (int k = 0; k < NDIM; ++k) L[E][1 + k] = 0.5 * (-b1 * ut[k] + (k == N ? 1.0 / c : 0.0));
+  L[E][E] = 0.5 * b1;
+
+  double w[6][NV], g[6][NV];
+  for (int j = 0; j < 6; ++j)
+    for (int s = 0; s < NV; ++s) {
+      double aw = 0.0, ag = 0.0;
+      for (int k = 0; k < NV; ++k) {
+        aw += L[s][k] * Up[j][k];
+        ag += L[s][k] * F[j][k];
+      }
+      w[j][s] = aw;
+      g[j][s] = ag;
+    }
+  double Pw[NV][6], Mw[NV][6], fchar[NV];
+  for (int s = 0; s < NV; ++s) {
+    double ap[5], am[5];
+    lin_weights(sel[s][0], ap);
+    lin_weights(sel[s][1], am);
+    fchar[s] = 0.0;
+    for (int j = 0; j < 6; ++j) {
+      const double Ap = j < 5 ? ap[j] : 0.0;
+      const double Am = j >= 1 ? am[5 - j] : 0.0;
+      Pw[s][j] = 0.5 * (Ap + Am);
+      Mw[s][j] = 0.5 * (Ap - Am);
+      fchar[s] += Pw[s][j] * g[j][s] + alpha[s] * Mw[s][j] * w[j][s];
+    }
+  }
+
+  // ---- reverse ----------------------------------------------------------------
+  double fb[NV];
+  for (int s = 0; s < NV; ++s) {
+    fb[s] = 0.0;
+    for (int r = 0; r < NV; ++r) fb[s] += R[r][s] * Fb[r];
+  }
+  double wb[6][NV], gb[6][NV];
+  for (int s = 0; s < NV; ++s) {
+    double sm = 0.0;
+    for (int j = 0; j < 6; ++j) {
+      wb[j][s] = alpha[s] * Mw[s][j] * fb[s];
+      gb[j][s] = Pw[s][j] * fb[s];
+      sm += Mw[s][j] * w[j][s];
+    }
+    ab[s] = fb[s] * sm;
+  }
+  // direct terms of w = L U, g = L F; X[s][k] = sum_j wb_js U_jk + gb_js F_jk
+  double Fbar[6][NV], X[NV][NV];
+  for (int j = 0; j < 6; ++j)
+    for (int k = 0; k < NV; ++k) {
+      double a1 = 0.0, a2 = 0.0;
+      for (int s = 0; s < NV; ++s) {
+        a1 += L[s][k] * wb[j][s];
+        a2 += L[s][k] * gb[j][s];
+      }
+      Ub[j][k] = a1;
+      Fbar[j][k] = a2;
+    }
+  for (int s = 0; s < NV; ++s)
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int j = 0; j < 6; ++j) a += wb[j][s] * Up[j][k] + gb[j][s] * F[j][k];
+      X[s][k] = a;
+    }
+
+  // gradients of the Roe parameters
+  double utb[NDIM];
+  for (int k = 0; k < NDIM; ++k) utb[k] = 0.0;
+  double Hbar = 0.0, cb = 0.0, b1b = 0.0, b2b = 0.0, q2b = 0.0;
+  const double ic = 1.0 / c, ic2 = ic * ic;
+  // from L
+  b2b += 0.5 * X[0][0] - X[1][0] + 0.5 * X[E][0];
+  utb[N] += 0.5 * ic * (X[0][0] - X[E][0]);
+  cb += 0.5 * un * ic2 * (X[E][0] - X[0][0]);
+  for (int k = 0; k < NDIM; ++k) {
+    b1b += ut[k] * (-0.5 * X[0][1 + k] + X[1][1 + k] - 0.5 * X[E][1 + k]);
+    utb[k] += b1 * (-0.5 * X[0][1 + k] + X[1][1 + k] - 0.5 * X[E][1 + k]);
+  }
+  cb += 0.5 * ic2 * (X[0][1 + N] - X[E][1 + N]);
+  b1b += 0.5 * X[0][E] - X[1][E] + 0.5 * X[E][E];
+  for (int f = 2; f < NV - 1; ++f) utb[tf[f - 2]] -= X[f][0];
+  // from R (Rbar = Fb fchar^T)
+  const double fsum = fchar[0] + fchar[1] + fchar[E];
+  for (int k = 0; k < NDIM; ++k) utb[k] += Fb[1 + k] * fsum;
+  cb += Fb[1 + N] * (fchar[E] - fchar[0]);
+  Hbar += Fb[E] * (fchar[0] + fchar[E]);
+  utb[N] += c * Fb[E] * (fchar[E] - fchar[0]);
+  cb += un * Fb[E] * (fchar[E] - fchar[0]);
+  q2b += 0.5 * Fb[E] * fchar[1];
+  for (int f = 2; f < NV - 1; ++f) utb[tf[f - 2]] += Fb[E] * fchar[f];
+  // chain through b2, b1, c, c2, q2
+  b1b += 0.5 * q2 * b2b;
+  q2b += 0.5 * b1 * b2b;
+  double c2b = -(b1 / c2) * b1b + 0.5 * ic * cb;
+  Hbar += gm1 * c2b;
+  q2b += -0.5 * gm1 * c2b;
+  for (int k = 0; k < NDIM; ++k) utb[k] += 2.0 * ut[k] * q2b;
+  // Roe averages
+  double ub2[NDIM], ub3[NDIM], sab = 0.0, sbb = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    ub2[k] = sa / S * utb[k];
+    ub3[k] = sb / S * utb[k];
+    sab += (u[2][k] - ut[k]) / S * utb[k];
+    sbb += (u[3][k] - ut[k]) / S * utb[k];
+  }
+  const double Hab = sa / S * Hbar, Hbb = sb / S * Hbar;
+  sab += (Ha - H) / S * Hbar;
+  sbb += (Hb - H) / S * Hbar;
+
+  // per point: primitives -> conservative
+  for (int j = 0; j < 6; ++j) {
+    double rhob = 0.0, Eb = 0.0, pb = 0.0, ub_[NDIM];
+    for (int k = 0; k < NDIM; ++k) ub_[k] = 0.0;
+    if (j == 2 || j == 3) {
+      const double sx = (j == 2) ? sa : sb;
+      const double sxb = (j == 2) ? sab : sbb;
+      const double Hx = (j == 2) ? Ha : Hb;
+      const double Hxb = (j == 2) ? Hab : Hbb;
+      rhob += 0.5 / sx * sxb;
+      Eb += Hxb / rho[j];
+      pb += Hxb / rho[j];
+      rhob += -Hx / rho[j] * Hxb;
+      for (int k = 0; k < NDIM; ++k) ub_[k] += (j == 2) ? ub2[k] : ub3[k];
+    }
+    // F = (rho u_n, m_k u_n + p delta_kn, u_n (E + p))
+    double mb[NDIM];
+    for (int k = 0; k < NDIM; ++k) mb[k] = 0.0;
+    rhob += Fbar[j][0] * u[j][N];
+    ub_[N] += Fbar[j][0] * rho[j];
+    for (int k = 0; k < NDIM; ++k) {
+      mb[k] += Fbar[j][1 + k] * u[j][N];
+      ub_[N] += Fbar[j][1 + k] * Up[j][1 + k];
+    }
+    pb += Fbar[j][1 + N];
+    ub_[N] += Fbar[j][E] * (Up[j][E] + p[j]);
+    Eb += Fbar[j][E] * u[j][N];
+    pb += Fbar[j][E] * u[j][N];
+    // p = (gamma-1)(E - rho q / 2)
+    Eb += gm1 * pb;
+    rhob += -0.5 * gm1 * q[j] * pb;
+    for (int k = 0; k < NDIM; ++k) ub_[k] += -gm1 * rho[j] * u[j][k] * pb;
+    // u = m / rho
+    for (int k = 0; k < NDIM; ++k) {
+      mb[k] += ub_[k] / rho[j];
+      rhob += -u[j][k] / rho[j] * ub_[k];
+    }
+    Ub[j][0] += rhob;
+    for (int k = 0; k < NDIM; ++k) Ub[j][1 + k] += mb[k];
+    Ub[j][E] += Eb;
+  }
+}
+
+// d|lambda|/dU at one cell for lambda = u_d - c (kind 0), u_d (kind 1) or
+// u_d + c (kind 2), c = sqrt(gamma p / rho); returns the gradient scaled by s.
+template <int NDIM>
+TENO_HD inline void wave_speed_grad(const double (&Uc)[NDIM + 2], int d, int kind, double gamma,
+                                    double s, double (&out)[NDIM + 2]) {
+  constexpr int E = NDIM + 1;
+  const double gm1 = gamma - 1.0;
+  const double rho = Uc[0];
+  double u[NDIM], q = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    u[k] = Uc[1 + k] / rho;
+    q += u[k] * u[k];
+  }
+  const double p = gm1 * (Uc[E] - 0.5 * rho * q);
+  const double c = sqrt(gamma * p / rho);
+  const double lam = kind == 0 ? u[d] - c : (kind == 1 ? u[d] : u[d] + c);
+  const double sg = lam > 0.0 ? 1.0 : (lam < 0.0 ? -1.0 : 0.0);
+  const double cs = kind == 0 ? -1.0 : (kind == 1 ? 0.0 : 1.0);   // d lambda / d c
+  // d u_d / dU
+  double g[NDIM + 2];
+  for (int i = 0; i < NDIM + 2; ++i) g[i] = 0.0;
+  g[0] += -u[d] / rho;
+  g[1 + d] += 1.0 / rho;
+  // d c / dU: c = sqrt(gamma p / rho); dc = gamma/(2 rho c) dp - c/(2 rho) drho
+  const double cp = gamma / (2.0 * rho * c), cr = -c / (2.0 * rho);
+  // dp/drho = gm1 q / 2, dp/dm_k = -gm1 u_k, dp/dE = gm1
+  g[0] += cs * (cp * 0.5 * gm1 * q + cr);
+  for (int k = 0; k < NDIM; ++k) g[1 + k] += cs * cp * (-gm1 * u[k]);
+  g[E] += cs * cp * gm1;
+  for (int i = 0; i < NDIM + 2; ++i) out[i] += s * sg * g[i];
+}
+
+}  // namespace teno_adj

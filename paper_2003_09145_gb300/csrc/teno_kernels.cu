@@ -360,4 +360,40 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
   return cudaGetLastError();
 }
 
+teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
+                          size_t alpha_off, size_t aux_off, size_t fhat_off, const double* U,
+                          double* R, int mode, const double* Un, const double* Uk, double* Uout,
+                          cudaStream_t st) {
+  Grid G;
+  for (int k = 0; k < 3; ++k) {
+    G.n[k] = g->n[k];
+    G.bc[k] = k < g->ndim ? g->bc[k] : 0;
+    G.dx[k] = k < g->ndim ? g->dx[k] : 1.0;
+    G.inv_dx[k] = 1.0 / G.dx[k];
+  }
+  G.ncell = g->n[0] * g->n[1] * g->n[2];
+  const Scheme S = make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    nsm = 152;
+  int* status = reinterpret_cast<int*>(ws + status_off);
+  const double* dt = reinterpret_cast<const double*>(ws + dt_off);
+  auto* alpha = reinterpret_cast<unsigned long long*>(ws + alpha_off);
+  double* aux = reinterpret_cast<double*>(ws + aux_off);
+  double* Fhat = reinterpret_cast<double*>(ws + fhat_off);
+  if (cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
+  if (launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
+    return TENO_ERR_CUDA;
+  for (int d = 0; d < g->ndim; ++d) {
+    if (launch_flux(g->ndim, d, U, aux, alpha, Fhat, nullptr, status, G, S, nsm, st) != cudaSuccess)
+      return TENO_ERR_CUDA;
+    const bool last = (d == g->ndim - 1);
+    const int m = last ? mode : (d == 0 ? 0 : 1);
+    if (launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt, G, m, d > 0 ? 1 : 0, nsm, st) != cudaSuccess)
+      return TENO_ERR_CUDA;
+  }
+  return TENO_OK;
+}
+
 }  // namespace teno

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "teno.h"
 #include "teno_device.cuh"
 
 namespace teno {
@@ -29,5 +30,15 @@ cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
 cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
                       double cfl, double dt_fixed, double* t_dev, double t_end,
                       double* dt_ws, double* dt_out, cudaStream_t st);
+
+// One right-hand-side evaluation of U fused with the SSP-RK3 stage `mode`
+// (2, 3 or 4; see diff_kernel) into Uout, with dt read from the workspace
+// word at dt_off.  `ws` offsets locate the status word, the LF speeds, the
+// per-cell primitives and the interface-flux buffer; R holds the partial sums
+// of the multi-dimensional difference.
+teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
+                          size_t alpha_off, size_t aux_off, size_t fhat_off, const double* U,
+                          double* R, int mode, const double* Un, const double* Uk, double* Uout,
+                          cudaStream_t st);
 
 }  // namespace teno
