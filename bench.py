@@ -115,28 +115,38 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+FLUX_KERNEL_SOURCES = ("teno_device.cuh", "teno_flux.cuh", "teno_kernels.cu")
+
+
 def _source_hash() -> str:
+    """Hash of the sources the interface-flux kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2003_09145_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fn.encode() + fh.read())
+    for fn in FLUX_KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
 def _traffic_per_launch():
-    """DRAM bytes per flux-kernel launch from the committed ncu summary, if it was
-    taken on the current kernel sources; otherwise None."""
-    path = os.path.join(ROOT, "profiles", "flux_kernel_traffic.json")
+    """DRAM bytes per flux-kernel launch at the benchmark size, from the committed
+    ncu summary, if that was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "flux_kernel_traffic.txt")
+    rec = {}
     try:
         with open(path) as fh:
-            rec = json.load(fh)
-    except (OSError, ValueError):
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+    except OSError:
         return None
     if rec.get("source_hash") != _source_hash():
         return None
-    return rec.get("bytes_per_launch_full_size")
+    try:
+        return float(rec["bytes_per_launch_256"])
+    except (KeyError, ValueError):
+        return None
 
 
 def cpu_baseline(sample_n: int = 96, steps: int = 2) -> dict:
@@ -257,6 +267,28 @@ def bench_batched(api, device, steps: int) -> dict:
             "tuning": {"block": tuning[0], "ctas_per_sm": tuning[1]}, "graph_steps": steps,
             "one_by_one": {"value": B.ncell / (ms_single * 1e-3) / 1e9, "unit": UNIT,
                            "ms_per_step": ms_single}}
+
+
+def bench_adjoint(api, device, grid, U0, steps: int) -> dict:
+    """The adjoint form on the same 256^3 box: reverse of fixed-dt SSP-RK3 steps
+    (teno_rk3_step_adjoint: two recomputed forward stages + three right-hand-side
+    adjoints per step), reported like the forward path (cells x steps / time)."""
+    import torch
+    adj = api.AdjointStepper(grid, device=device)
+    dt = 1e-3
+    B = torch.ones_like(U0)
+    adj.step(U0, dt, B, B)                      # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        adj.step(U0, dt, B, B)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    assert adj.status() == 0
+    return {"value": grid.ncell / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "workload": "reverse of one fixed-dt SSP-RK3 step on the 256^3 turbulence box, FP64"}
 
 
 def main() -> None:
@@ -390,6 +422,7 @@ def main() -> None:
     forms = {}
     if not args.no_forms:
         forms["batched"] = bench_batched(api, device, max(args.steps, 4))
+        forms["adjoint"] = bench_adjoint(api, device, grid, U0, 2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
