@@ -65,6 +65,9 @@ struct Scheme {
   int top;        // largest power of two <= nthr (binary-search start)
   unsigned keep_all;  // bit m set: every chi_k >= C_T is guaranteed at this m
   int keep_idx;   // keep_all = {m >= B_l + keep_idx + 1}: tau <= thr[keep_idx] dmin (-1: none)
+  float thr_keep_f;   // thr[keep_idx] rounded down to binary32
+  float eps4_f;       // 4 eps rounded down to binary32
+  float kerr_f;       // 5000 * 2^-24: error bound factor of the FP32 pre-test
   // m = B_l + #{ j in 1..B_u-B_l : tau <= thr[j-1] * min_k(beta_k + eps) }.
   // With theta = 1/(1 + max_k chi~_k / H) and max_k chi~_k = tau / min_k(beta_k
   // + eps) (eq. 3.2), floor(theta (B_u - B_l)) >= j  <=>  max chi~ <=
@@ -102,6 +105,17 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
   return static_cast<unsigned long long>(__double_as_longlong(x));
 }
 
+// binary32 approximation of a double built on the integer pipe from its high
+// word: exponent rebiased, mantissa truncated to 20 bits (|f - x| < 2^-20 |x|),
+// magnitudes clamped to [2^-126, 2^128).
+__device__ __forceinline__ float hi_float(double x) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  unsigned mag = hi & 0x7fffffffu;
+  mag = max(mag, 897u << 20);
+  mag = min(mag, (1150u << 20) | 0xFFFFFu);
+  return __uint_as_float(((mag - (896u << 20)) << 3) | (hi & 0x80000000u));
+}
+
 // ---------------------------------------------------------------------------
 // TENO5-LAD scalar reconstruction of the interface value from five values
 // v0..v4 = (f_{i-2}, ..., f_{i+2}).  Returns f^ (eq. 2.7); `flag` receives
@@ -126,6 +140,32 @@ __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
                                             double v3, double v4,
                                             const Scheme& S, unsigned& flag) {
   const double e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
+  if (!WITH_M && S.keep_idx >= 0) {
+    // Certified single-precision pre-test of "every stencil kept": the scaled
+    // indicators below are evaluated in FP32 from 20-bit truncations of the
+    // differences (hi_float, integer pipe).  With E = max |e_k| each differs
+    // from its exact value by at most 67 u_c E^2 + 199 u E^2 <= 1266 u E^2
+    // (u_c = 2^-20, u = 2^-24; kerr_f carries a further factor 4), so when
+    // tau + 2 err <= thr (dmin - err) holds here, tau <= thr * dmin holds for
+    // the exact values with margin: the binary64 test below and the bound of
+    // Scheme::keep_all would both keep every stencil.  Otherwise fall through.
+    const float f0 = hi_float(e0), f1 = hi_float(e1);
+    const float f2 = hi_float(e2), f3 = hi_float(e3);
+    const float Ef = fmaxf(fmaxf(fabsf(f0), fabsf(f1)), fmaxf(fabsf(f2), fabsf(f3)));
+    const float k13_3f = 13.0f / 3.0f;
+    const float a0f = f1 - f0, a1f = f2 - f1, a2f = f3 - f2;
+    const float c0f = fmaf(3.0f, f1, -f0), c1f = f1 + f2, c2f = fmaf(-3.0f, f2, f3);
+    const float b0f = fmaf(k13_3f * a0f, a0f, c0f * c0f);
+    const float b1f = fmaf(k13_3f * a1f, a1f, c1f * c1f);
+    const float b2f = fmaf(k13_3f * a2f, a2f, c2f * c2f);
+    const float tauf = fabsf(b2f - b0f);
+    const float dminf = fminf(b0f, fminf(b1f, b2f)) + S.eps4_f;
+    const float err = S.kerr_f * Ef * Ef;
+    if (err <= 1.0e38f && tauf + 2.0f * err <= S.thr_keep_f * (dminf - err) * (1.0f - 1e-5f)) {
+      flag = 7u;
+      return fma(c_coef[7][0], e0, fma(c_coef[7][1], e1, fma(c_coef[7][2], e2, fma(c_coef[7][3], e3, v2))));
+    }
+  }
   // eq. 2.9-2.11 scaled by 4: 4 beta_k = (13/3) a_k^2 + c_k^2.  Every use of
   // beta_k below is through ratios tau / (beta_k + eps) and products that are
   // homogeneous in (beta, tau, eps), so the common factor 4 (with eps -> 4 eps)

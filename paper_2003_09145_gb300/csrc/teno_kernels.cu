@@ -12,6 +12,7 @@
 //                    back-projection to the interface flux F^;
 //   diff_kernel<D> : per cell, -(F^_{i+1/2} - F^_{i-1/2}) / dx_D, written,
 //                    accumulated, or fused into the SSP-RK3 stage (eq. 4.1-4.3).
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <cuda_runtime.h>
@@ -267,6 +268,15 @@ Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u) {
       break;
     }
   }
+  // binary32 constants of the pre-test, rounded towards zero (conservative)
+  auto down = [](double x) {
+    float f = static_cast<float>(x);
+    while (static_cast<double>(f) > x) f = std::nextafter(f, 0.0f);
+    return std::nextafter(f, 0.0f);
+  };
+  S.thr_keep_f = S.keep_idx >= 0 ? down(S.thr[S.keep_idx]) : 0.0f;
+  S.eps4_f = down(4.0 * eps);
+  S.kerr_f = static_cast<float>(5000.0 * 0x1p-24);
   return S;
 }
 
