@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_flux_kernel(
     fa[NVAR - 1] = ap;
     for (int f = 0; f < NVAR; ++f) ha[f] = 0.5 * fa[f];
   }
+  double nfa[NVAR];
+  for (int f = 0; f < NVAR; ++f) nfa[f] = -2.0 * ha[f];
   const double fscale = scale * G.inv_dx[DIR];
   double asum[3] = {0.0, 0.0, 0.0};
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nifc;
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_flux_kernel(
     // the primal selections, by the forward device code
     double fout[NVAR];
     unsigned fl[NVAR][2];
-    teno::interface_flux<NDIM, DIR, true>(U, aux, ncell, cells, ha, S, fout, fl, status);
+    teno::interface_flux<NDIM, DIR, true>(U, aux, ncell, cells, ha, nfa, S, fout, fl, status);
     unsigned sel[NVAR][2];
     for (int s = 0; s < NVAR; ++s) {
       sel[s][0] = fl[s][0] & 7u;

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
     const double dt = s_dt;
     if (!(dt > 0.0)) continue;
     const double alpha[3] = {s_alpha[0], s_alpha[1], s_alpha[2]};
+    const double nal[3] = {-2.0 * s_alpha[0], -2.0 * s_alpha[1], -2.0 * s_alpha[2]};
     const double idx = s_idx;
 
     // (B) fluxes tile by tile, difference fused with the stage update
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
         for (int j = 0; j < 6; ++j) cells[j] = off + teno::ghost(face - 3 + j, n, A.bc);
         double out[3];
         unsigned fl[3][2];
-        teno::interface_flux<1, 0, false>(A.Uin, A.aux, A.ncell, cells, alpha, S, out, fl, A.status);
+        teno::interface_flux<1, 0, false>(A.Uin, A.aux, A.ncell, cells, alpha, nal, S, out, fl, A.status);
         s_F[tid][0] = out[0];
         s_F[tid][1] = out[1];
         s_F[tid][2] = out[2];

@@ -47,6 +47,23 @@ static __constant__ double c_coef[8][4] = {
     TENO_COEF_ROW(0.1 / (0.1 + 0.6 + 0.3), 0.6 / (0.1 + 0.6 + 0.3), 0.3 / (0.1 + 0.6 + 0.3))};
 #undef TENO_COEF_ROW
 
+// The same flux on the point values: f^ = sum_j c_lin[sel][j] v_j with
+// (omega_0/3, -7 omega_0/6 - omega_1/6, 11 omega_0/6 + 5 omega_1/6 + omega_2/3,
+//  omega_1/3 + 5 omega_2/6, -omega_2/6) (eq. 2.4-2.7).
+#define TENO_LIN_ROW(o0, o1, o2)                                                              \
+  {(o0) / 3.0, -7.0 * (o0) / 6.0 - (o1) / 6.0, 11.0 * (o0) / 6.0 + 5.0 * (o1) / 6.0 + (o2) / 3.0, \
+   (o1) / 3.0 + 5.0 * (o2) / 6.0, -(o2) / 6.0}
+static __constant__ double c_lin[8][5] = {
+    TENO_LIN_ROW(0.0, 0.0, 0.0),
+    TENO_LIN_ROW(0.1 / 0.1, 0.0, 0.0),
+    TENO_LIN_ROW(0.0, 0.6 / 0.6, 0.0),
+    TENO_LIN_ROW(0.1 / (0.1 + 0.6), 0.6 / (0.1 + 0.6), 0.0),
+    TENO_LIN_ROW(0.0, 0.0, 0.3 / 0.3),
+    TENO_LIN_ROW(0.1 / (0.1 + 0.3), 0.0, 0.3 / (0.1 + 0.3)),
+    TENO_LIN_ROW(0.0, 0.6 / (0.6 + 0.3), 0.3 / (0.6 + 0.3)),
+    TENO_LIN_ROW(0.1 / (0.1 + 0.6 + 0.3), 0.6 / (0.1 + 0.6 + 0.3), 0.3 / (0.1 + 0.6 + 0.3))};
+#undef TENO_LIN_ROW
+
 constexpr int kMaxDim = 3;
 constexpr int kMaxVar = 5;
 constexpr int kMaxLadder = 16;
@@ -67,7 +84,7 @@ struct Scheme {
   int keep_idx;   // keep_all = {m >= B_l + keep_idx + 1}: tau <= thr[keep_idx] dmin (-1: none)
   float thr_keep_f;   // thr[keep_idx] rounded down to binary32
   float eps4_f;       // 4 eps rounded down to binary32
-  float kerr_f;       // 5000 * 2^-24: error bound factor of the FP32 pre-test
+  float kerr_f;       // 10000 * 2^-24: error bound factor of the FP32 pre-test
   // m = B_l + #{ j in 1..B_u-B_l : tau <= thr[j-1] * min_k(beta_k + eps) }.
   // With theta = 1/(1 + max_k chi~_k / H) and max_k chi~_k = tau / min_k(beta_k
   // + eps) (eq. 3.2), floor(theta (B_u - B_l)) >= j  <=>  max chi~ <=
@@ -118,14 +135,14 @@ __device__ __forceinline__ float hi_float(double x) {
 
 // ---------------------------------------------------------------------------
 // TENO5-LAD scalar reconstruction of the interface value from five values
-// v0..v4 = (f_{i-2}, ..., f_{i+2}).  Returns f^ (eq. 2.7); `flag` receives
-// delta bits 0..2 and m in bits 3..6.
+// v0..v4 = (f_{i-2}, ..., f_{i+2}).  Returns acc + f^ (eq. 2.7); `flag`
+// receives delta bits 0..2 and m in bits 3..6.
 //
 // Arithmetic (all exact rewrites of the paper's formulas, evaluated in FP64):
 //  * with first differences e_k = v_{k+1} - v_k, the indicator terms of
 //    eq. 2.9-2.11 are a_0 = e1 - e0, c_0 = 3 e1 - e0, a_1 = e2 - e1,
 //    c_1 = -(e1 + e2), a_2 = e3 - e2, c_2 = e3 - 3 e2, and the weighted sum
-//    of the candidate fluxes (eq. 2.4-2.7) is v2 + sum_k c_coef[sel][k] e_k;
+//    of the candidate fluxes (eq. 2.4-2.7) is sum_j c_lin[sel][j] v_j;
 //  * m of eq. 3.1 counts the thresholds tau <= thr_j * min_k(beta_k + eps)
 //    (see Scheme), found by binary search over the decreasing thresholds;
 //  * the cutoff chi_k >= C_T of eq. 2.13-2.14 is decided without division:
@@ -137,20 +154,22 @@ __device__ __forceinline__ float hi_float(double x) {
 // ---------------------------------------------------------------------------
 template <bool WITH_M>
 __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
-                                            double v3, double v4,
+                                            double v3, double v4, double acc,
                                             const Scheme& S, unsigned& flag) {
-  const double e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
   if (!WITH_M && S.keep_idx >= 0) {
     // Certified single-precision pre-test of "every stencil kept": the scaled
-    // indicators below are evaluated in FP32 from 20-bit truncations of the
-    // differences (hi_float, integer pipe).  With E = max |e_k| each differs
-    // from its exact value by at most 67 u_c E^2 + 199 u E^2 <= 1266 u E^2
-    // (u_c = 2^-20, u = 2^-24; kerr_f carries a further factor 4), so when
-    // tau + 2 err <= thr (dmin - err) holds here, tau <= thr * dmin holds for
-    // the exact values with margin: the binary64 test below and the bound of
-    // Scheme::keep_all would both keep every stencil.  Otherwise fall through.
-    const float f0 = hi_float(e0), f1 = hi_float(e1);
-    const float f2 = hi_float(e2), f3 = hi_float(e3);
+    // indicators are evaluated in FP32 from 20-bit truncations of the values
+    // (hi_float, integer pipe).  With V = max |v_j| and E = max |e_k| each
+    // differs from its exact value by at most 133 u_c E V + 200 u E^2
+    // <= 2528 u E V (u_c = 2^-20, u = 2^-24; kerr_f carries a further factor
+    // 4), so when tau + 2 err <= thr (dmin - err) holds here, tau <= thr * dmin
+    // holds for the exact values with margin: the binary64 test below and the
+    // bound of Scheme::keep_all would both keep every stencil.  Otherwise fall
+    // through to the binary64 evaluation.
+    const float g0 = hi_float(v0), g1 = hi_float(v1), g2 = hi_float(v2);
+    const float g3 = hi_float(v3), g4 = hi_float(v4);
+    const float Vf = fmaxf(fmaxf(fmaxf(fabsf(g0), fabsf(g1)), fmaxf(fabsf(g2), fabsf(g3))), fabsf(g4));
+    const float f0 = g1 - g0, f1 = g2 - g1, f2 = g3 - g2, f3 = g4 - g3;
     const float Ef = fmaxf(fmaxf(fabsf(f0), fabsf(f1)), fmaxf(fabsf(f2), fabsf(f3)));
     const float k13_3f = 13.0f / 3.0f;
     const float a0f = f1 - f0, a1f = f2 - f1, a2f = f3 - f2;
@@ -160,12 +179,13 @@ __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
     const float b2f = fmaf(k13_3f * a2f, a2f, c2f * c2f);
     const float tauf = fabsf(b2f - b0f);
     const float dminf = fminf(b0f, fminf(b1f, b2f)) + S.eps4_f;
-    const float err = S.kerr_f * Ef * Ef;
+    const float err = S.kerr_f * Ef * Vf;
     if (err <= 1.0e38f && tauf + 2.0f * err <= S.thr_keep_f * (dminf - err) * (1.0f - 1e-5f)) {
       flag = 7u;
-      return fma(c_coef[7][0], e0, fma(c_coef[7][1], e1, fma(c_coef[7][2], e2, fma(c_coef[7][3], e3, v2))));
+      return fma(c_lin[7][0], v0, fma(c_lin[7][1], v1, fma(c_lin[7][2], v2, fma(c_lin[7][3], v3, fma(c_lin[7][4], v4, acc)))));
     }
   }
+  const double e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
   // eq. 2.9-2.11 scaled by 4: 4 beta_k = (13/3) a_k^2 + c_k^2.  Every use of
   // beta_k below is through ratios tau / (beta_k + eps) and products that are
   // homogeneous in (beta, tau, eps), so the common factor 4 (with eps -> 4 eps)
@@ -184,54 +204,55 @@ __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
   const unsigned long long bmin = min(dbits(beta0), min(dbits(beta1), dbits(beta2)));
   const double dmin = __longlong_as_double(static_cast<long long>(bmin)) + S.eps4;
   const unsigned long long btau = dbits(tau);
+  unsigned sel = 7u;
+  int m = S.b_u;
   if (!WITH_M && S.keep_idx >= 0 && btau <= dbits(S.thr[S.keep_idx] * dmin)) {
     // m lies in the keep-all range (a suffix of B_l..B_u): every stencil is kept
     flag = 7u;
-    return fma(c_coef[7][0], e0, fma(c_coef[7][1], e1, fma(c_coef[7][2], e2, fma(c_coef[7][3], e3, v2))));
-  }
-  int cnt = 0;
+  } else {
+    int cnt = 0;
 #pragma unroll
-  for (int step = 8; step >= 1; step >>= 1) {
-    if (step <= S.top) {
-      const int idx = cnt + step - 1;
-      if (btau <= dbits(S.thr[idx] * dmin)) cnt += step;
+    for (int step = 8; step >= 1; step >>= 1) {
+      if (step <= S.top) {
+        const int idx = cnt + step - 1;
+        if (btau <= dbits(S.thr[idx] * dmin)) cnt += step;
+      }
     }
-  }
-  cnt = min(cnt, S.nthr);
-  const int m = S.b_l + cnt;
-  unsigned sel = 7u;
-  if (!((S.keep_all >> m) & 1u)) {
-    // eq. 3.4, eq. 2.8, eq. 2.13-2.14 (division-free form, see above)
-    const double ct = c_lad[m];
-    const double d0 = beta0 + S.eps4, d1 = beta1 + S.eps4, d2 = beta2 + S.eps4;
-    const double n0 = d0 + tau, n1 = d1 + tau, n2 = d2 + tau;
-    const double p0 = n0 * (d1 * d2), p1 = n1 * (d0 * d2), p2 = n2 * (d0 * d1);
-    double q0 = p0 * p0, q1 = p1 * p1, q2 = p2 * p2;
-    q0 = q0 * q0 * q0;
-    q1 = q1 * q1 * q1;
-    q2 = q2 * q2 * q2;
-    const double sum = q0 + q1 + q2;
-    if (sum > 0.0 && sum <= 1.7976931348623157e308) {
-      const unsigned long long lim = dbits(ct * sum);
-      sel = (dbits(q0) >= lim ? 1u : 0u) | (dbits(q1) >= lim ? 2u : 0u) |
-            (dbits(q2) >= lim ? 4u : 0u);
-    } else {
-      // outside the range of the products: gamma_k = (1 + tau/D_k)^6 directly
-      const double x0 = 1.0 + tau / d0, x1 = 1.0 + tau / d1, x2 = 1.0 + tau / d2;
-      double g0 = x0 * x0 * x0, g1 = x1 * x1 * x1, g2 = x2 * x2 * x2;
-      g0 *= g0;
-      g1 *= g1;
-      g2 *= g2;
-      const double gs = g0 + g1 + g2;
-      const unsigned long long lim = dbits(ct * gs);
-      sel = (dbits(g0) >= lim ? 1u : 0u) | (dbits(g1) >= lim ? 2u : 0u) |
-            (dbits(g2) >= lim ? 4u : 0u);
-      if (!(gs <= 1.7976931348623157e308)) sel = 7u;  // every chi_k undefined: keep all
+    cnt = min(cnt, S.nthr);
+    m = S.b_l + cnt;
+    if (!((S.keep_all >> m) & 1u)) {
+      // eq. 3.4, eq. 2.8, eq. 2.13-2.14 (division-free form, see above)
+      const double ct = c_lad[m];
+      const double d0 = beta0 + S.eps4, d1 = beta1 + S.eps4, d2 = beta2 + S.eps4;
+      const double n0 = d0 + tau, n1 = d1 + tau, n2 = d2 + tau;
+      const double p0 = n0 * (d1 * d2), p1 = n1 * (d0 * d2), p2 = n2 * (d0 * d1);
+      double q0 = p0 * p0, q1 = p1 * p1, q2 = p2 * p2;
+      q0 = q0 * q0 * q0;
+      q1 = q1 * q1 * q1;
+      q2 = q2 * q2 * q2;
+      const double sum = q0 + q1 + q2;
+      if (sum > 0.0 && sum <= 1.7976931348623157e308) {
+        const unsigned long long lim = dbits(ct * sum);
+        sel = (dbits(q0) >= lim ? 1u : 0u) | (dbits(q1) >= lim ? 2u : 0u) |
+              (dbits(q2) >= lim ? 4u : 0u);
+      } else {
+        // outside the range of the products: gamma_k = (1 + tau/D_k)^6 directly
+        const double x0 = 1.0 + tau / d0, x1 = 1.0 + tau / d1, x2 = 1.0 + tau / d2;
+        double h0 = x0 * x0 * x0, h1 = x1 * x1 * x1, h2 = x2 * x2 * x2;
+        h0 *= h0;
+        h1 *= h1;
+        h2 *= h2;
+        const double gs = h0 + h1 + h2;
+        const unsigned long long lim = dbits(ct * gs);
+        sel = (dbits(h0) >= lim ? 1u : 0u) | (dbits(h1) >= lim ? 2u : 0u) |
+              (dbits(h2) >= lim ? 4u : 0u);
+        if (!(gs <= 1.7976931348623157e308)) sel = 7u;  // every chi_k undefined: keep all
+      }
     }
+    flag = sel | (static_cast<unsigned>(m) << 3);
   }
-  flag = sel | (static_cast<unsigned>(m) << 3);
-  // eq. 2.4-2.7 and 2.15 on first differences (c_coef)
-  return fma(c_coef[sel][0], e0, fma(c_coef[sel][1], e1, fma(c_coef[sel][2], e2, fma(c_coef[sel][3], e3, v2))));
+  // eq. 2.4-2.7 with the weights of eq. 2.15 (c_lin)
+  return fma(c_lin[sel][0], v0, fma(c_lin[sel][1], v1, fma(c_lin[sel][2], v2, fma(c_lin[sel][3], v3, fma(c_lin[sel][4], v4, acc)))));
 }
 
 }  // namespace teno

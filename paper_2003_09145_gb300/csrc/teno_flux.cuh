@@ -42,7 +42,7 @@ __device__ __forceinline__ void project(const double (&X)[NDIM + 2],
 // Interface flux F^_{i+1/2} in direction DIR from the six cells i-2..i+3
 // (`cells`, linear indices into arrays of `ncell` entries per variable):
 // Roe-averaged eigensystem of cells i, i+1, characteristic projection, global
-// Lax-Friedrichs split with the halved speeds `alpha`, TENO5-LAD
+// Lax-Friedrichs split with the halved speeds `alpha` (nal = -2 alpha), TENO5-LAD
 // reconstruction of f^+ (cells i-2..i+2) and f^- (mirrored, i+3..i-1) for
 // every field, back-projection.  `fl` receives the flag bytes when WITH_FLAGS.
 // ---------------------------------------------------------------------------
@@ -51,6 +51,7 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
                                                const double* __restrict__ aux,
                                                int64_t ncell, const int64_t (&cells)[6],
                                                const double (&alpha)[NDIM + 2],
+                                               const double (&nal)[NDIM + 2],
                                                const Scheme& S, double (&out)[NDIM + 2],
                                                unsigned (&fl)[NDIM + 2][2],
                                                int* __restrict__ status) {
@@ -115,24 +116,24 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
       const double t0 = az - bz;
       const double tE = az + bz;
       const double t1 = -2.0 * az;
+      // v- = v+ - alpha w (nal = -alpha)
       vp[j][0] = fma(hu + alpha[0], w[0], t0);
-      vm[j][0] = fma(hu - alpha[0], w[0], t0);
+      vm[j][0] = fma(nal[0], w[0], vp[j][0]);
       vp[j][NVAR - 1] = fma(hu + alpha[NVAR - 1], w[NVAR - 1], tE);
-      vm[j][NVAR - 1] = fma(hu - alpha[NVAR - 1], w[NVAR - 1], tE);
-      const double sp = hu + alpha[1], sm = hu - alpha[1];
+      vm[j][NVAR - 1] = fma(nal[NVAR - 1], w[NVAR - 1], vp[j][NVAR - 1]);
+      const double sp = hu + alpha[1];
       vp[j][1] = fma(sp, w[1], t1);
-      vm[j][1] = fma(sm, w[1], t1);
+      vm[j][1] = fma(nal[1], w[1], vp[j][1]);
 #pragma unroll
       for (int f = 2; f < NVAR - 1; ++f) {
         vp[j][f] = sp * w[f];
-        vm[j][f] = sm * w[f];
+        vm[j][f] = fma(nal[1], w[f], vp[j][f]);
       }
     }
 #pragma unroll
     for (int s = 0; s < NVAR; ++s) {
-      const double hp = teno5_lad<WITH_FLAGS>(vp[0][s], vp[1][s], vp[2][s], vp[3][s], vp[4][s], S, fl[s][0]);
-      const double hm = teno5_lad<WITH_FLAGS>(vm[5][s], vm[4][s], vm[3][s], vm[2][s], vm[1][s], S, fl[s][1]);
-      fchar[s] = hp + hm;
+      const double hp = teno5_lad<WITH_FLAGS>(vp[0][s], vp[1][s], vp[2][s], vp[3][s], vp[4][s], 0.0, S, fl[s][0]);
+      fchar[s] = teno5_lad<WITH_FLAGS>(vm[5][s], vm[4][s], vm[3][s], vm[2][s], vm[1][s], hp, S, fl[s][1]);
     }
     // back-projection F^ = R f^char, columns r_0 = (1, u - c e_n, H - u_n c),
     // r_1 = (1, u, q2/2), r_t = (0, e_t, u_t), r_{nvar-1} = (1, u + c e_n, H + u_n c)
@@ -159,11 +160,11 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
 }
 
 // ---------------------------------------------------------------------------
-// Primitive variables of cell c, evaluated with explicit round-to-nearest
-// operations (no contraction) in the order u = m/rho, |u|^2 = sum u_k u_k,
-// p = (gamma-1)(E - (rho/2)|u|^2), c = sqrt(gamma p / rho).  Writes the aux
-// entries (u_k/2, p/2, sqrt(rho), (E+p)/sqrt(rho)) and returns u and c; false
-// if the state is not physical (rho <= 0, p <= 0 or non-finite).
+// Primitive variables of cell c from one reciprocal square root:
+// 1/sqrt(rho), sqrt(rho) = rho/sqrt(rho), 1/rho = (1/sqrt(rho))^2, u = m/rho,
+// p = (gamma-1)(E - rho |u|^2 / 2) (eq. 4.7), c = sqrt(gamma p / rho).  Writes
+// the aux entries (u_k/2, p/2, sqrt(rho), (E+p)/sqrt(rho)) and returns u and c;
+// false if the state is not physical (rho <= 0, p <= 0 or non-finite).
 // ---------------------------------------------------------------------------
 template <int NDIM>
 __device__ __forceinline__ bool cell_primitives(const double* __restrict__ U, int64_t ncell,
@@ -173,21 +174,24 @@ __device__ __forceinline__ bool cell_primitives(const double* __restrict__ U, in
   constexpr int NVAR = NDIM + 2;
   const double rho = U[c];
   const double E = U[(NVAR - 1) * ncell + c];
+  const double isr = rsqrt(rho);
+  const double sr = rho * isr;
+  const double r = isr * isr;
   double q2 = 0.0;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
-    u[k] = __ddiv_rn(U[(1 + k) * ncell + c], rho);
-    q2 = __dadd_rn(q2, __dmul_rn(u[k], u[k]));
+    u[k] = U[(1 + k) * ncell + c] * r;
+    q2 = fma(u[k], u[k], q2);
   }
-  const double p = __dmul_rn(gamma - 1.0, __dsub_rn(E, __dmul_rn(__dmul_rn(0.5, rho), q2)));
-  cs = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
-  const double sr = __dsqrt_rn(rho);
+  const double p = (gamma - 1.0) * fma(-0.5 * rho, q2, E);
+  const double gpr = gamma * p * r;
+  cs = gpr * rsqrt(gpr);
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) aux[k * ncell + c] = 0.5 * u[k];
   aux[NDIM * ncell + c] = 0.5 * p;
   aux[(NDIM + 1) * ncell + c] = sr;
-  aux[(NDIM + 2) * ncell + c] = (E + p) / sr;
-  return (rho > 0.0) && (p > 0.0) && isfinite(E) && isfinite(q2);
+  aux[(NDIM + 2) * ncell + c] = (E + p) * isr;
+  return (rho > 0.0) && (p > 0.0) && isfinite(E) && isfinite(q2) && (gpr > 0.0);
 }
 
 // SSP-RK3 stage value (eq. 4.1-4.3) of element e from d = L(U^(k))_e:
