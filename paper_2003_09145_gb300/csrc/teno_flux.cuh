@@ -39,6 +39,39 @@ __device__ __forceinline__ void project(const double (&X)[NDIM + 2],
 }
 
 // ---------------------------------------------------------------------------
+// Certified single-precision test that one reconstruction keeps every stencil.
+// v0..v4 are FP32 approximations of the split characteristic values, each
+// within `dlt` of its exact value (exact arithmetic on the binary64 state).
+// The scaled indicators of eq. 2.9-2.11 and their error bounds are carried in
+// FP32; the test passes only if tau <= thr * min_k(beta_k + eps) holds for the
+// exact values with margin, in which case the binary64 evaluation and the
+// bound behind Scheme::keep_all both keep every stencil (eq. 2.14 with
+// m >= B_l + keep_idx + 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool certify_keep(float v0, float v1, float v2, float v3, float v4,
+                                             float dlt, const Scheme& S) {
+  const float u = 0x1p-24f;
+  const float e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
+  const float a0 = e1 - e0, a1 = e2 - e1, a2 = e3 - e2;
+  const float c0 = fmaf(3.0f, e1, -e0), c1 = e1 + e2, c2 = fmaf(-3.0f, e2, e3);
+  const float k = 13.0f / 3.0f;
+  const float b0 = fmaf(k * a0, a0, c0 * c0);
+  const float b1 = fmaf(k * a1, a1, c1 * c1);
+  const float b2 = fmaf(k * a2, a2, c2 * c2);
+  // error bounds: |e| <= 2 dlt, |a| <= 4 dlt, |c| <= 8 dlt (plus the FP32
+  // rounding of beta itself)
+  const float da = 4.0f * dlt, dc = 8.0f * dlt;
+  const float db0 = fmaf(k * fmaf(2.0f, fabsf(a0), da), da, fmaf(2.0f, fabsf(c0), dc) * dc) + 4.0f * u * b0;
+  const float db1 = fmaf(k * fmaf(2.0f, fabsf(a1), da), da, fmaf(2.0f, fabsf(c1), dc) * dc) + 4.0f * u * b1;
+  const float db2 = fmaf(k * fmaf(2.0f, fabsf(a2), da), da, fmaf(2.0f, fabsf(c2), dc) * dc) + 4.0f * u * b2;
+  const float tau = fabsf(b2 - b0);
+  const float dtau = db0 + db2 + u * tau;
+  const float dmin = fminf(b0, fminf(b1, b2)) + S.eps4_f;
+  const float ddmin = fmaxf(db0, fmaxf(db1, db2)) + u * dmin;
+  return (dtau <= 1.0e38f) && (tau + dtau <= S.thr_keep_f * (dmin - ddmin) * (1.0f - 1e-5f));
+}
+
+// ---------------------------------------------------------------------------
 // Interface flux F^_{i+1/2} in direction DIR from the six cells i-2..i+3
 // (`cells`, linear indices into arrays of `ncell` entries per variable):
 // Roe-averaged eigensystem of cells i, i+1, characteristic projection, global
@@ -98,6 +131,127 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
     const double b2 = 0.5 * b1 * q2;
     const double hb1 = 0.5 * b1, hb2 = 0.5 * b2, hic = 0.5 * ic;
     const double hud = 0.5 * u[DIR];
+
+    if (!WITH_FLAGS && S.keep_idx >= 0) {
+      // ---- certification in FP32 (split characteristic values and bounds) ----
+      float uf[NDIM];
+#pragma unroll
+      for (int k = 0; k < NDIM; ++k) uf[k] = hi_float(u[k]);
+      const float hb1f = hi_float(hb1), hb2f = hi_float(hb2), hicf = hi_float(hic);
+      const float b1f = hi_float(b1), hudf = hi_float(hud);
+      float haf[NVAR];
+#pragma unroll
+      for (int f = 0; f < NVAR; ++f) haf[f] = hi_float(alpha[f]);
+      float vp32[6][NVAR], vm32[6][NVAR], mp[NVAR], mm[NVAR], vmax = 0.0f;
+#pragma unroll
+      for (int f = 0; f < NVAR; ++f) mp[f] = mm[f] = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        float X[NVAR], Xa[NVAR];
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) {
+          X[v] = hi_float(Ux[j][v]);
+          Xa[v] = fabsf(X[v]);
+        }
+        // projection (same form as project()) and its absolute-value evaluation
+        float Sv = -X[NVAR - 1], Sa = Xa[NVAR - 1];
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+          Sv = fmaf(uf[k], X[1 + k], Sv);
+          Sa = fmaf(fabsf(uf[k]), Xa[1 + k], Sa);
+        }
+        const float A = fmaf(hb2f, X[0], -hb1f * Sv);
+        const float Aa = fmaf(fabsf(hb2f), Xa[0], fabsf(hb1f) * Sa);
+        const float B = fmaf(uf[DIR], X[0], -X[1 + DIR]) * hicf;
+        const float Ba = fmaf(fabsf(uf[DIR]), Xa[0], Xa[1 + DIR]) * fabsf(hicf);
+        float w[NVAR], wa[NVAR];
+        w[0] = A + B;
+        wa[0] = Aa + Ba;
+        w[1] = fmaf(-2.0f, A, X[0]);
+        wa[1] = fmaf(2.0f, Aa, Xa[0]);
+        {
+          int f = 2;
+#pragma unroll
+          for (int t = 0; t < NDIM; ++t) {
+            if (t == DIR) continue;
+            w[f] = fmaf(-uf[t], X[0], X[1 + t]);
+            wa[f] = fmaf(fabsf(uf[t]), Xa[0], Xa[1 + t]);
+            ++f;
+          }
+        }
+        w[NVAR - 1] = A - B;
+        wa[NVAR - 1] = Aa + Ba;
+        const float huf = hi_float(un[j]), hpf = hi_float(pn[j]);
+        const float az = hpf * (b1f * (huf - hudf));
+        const float aza = fabsf(hpf) * (fabsf(b1f) * (fabsf(huf) + fabsf(hudf)));
+        const float bz = hpf * hicf, bza = fabsf(hpf) * fabsf(hicf);
+#pragma unroll
+        for (int f = 0; f < NVAR; ++f) {
+          const float t = (f == 0) ? az - bz : (f == NVAR - 1) ? az + bz : (f == 1) ? -2.0f * az : 0.0f;
+          const float ta = (f == 0 || f == NVAR - 1) ? aza + bza : (f == 1) ? 2.0f * aza : 0.0f;
+          vp32[j][f] = fmaf(huf + haf[f], w[f], t);
+          vm32[j][f] = fmaf(-2.0f * haf[f], w[f], vp32[j][f]);
+          const float pa = fmaf(fabsf(huf) + haf[f], wa[f], ta);
+          const float ma = fmaf(2.0f * haf[f], wa[f], pa);
+          if (j <= 4) mp[f] = fmaxf(mp[f], pa);
+          if (j >= 1) mm[f] = fmaxf(mm[f], ma);
+          vmax = fmaxf(vmax, fmaxf(fabsf(vp32[j][f]), fabsf(vm32[j][f])));
+        }
+      }
+      // |v32 - v| <= 8 * 2^-20 * (absolute evaluation) + 8 u max|v|: the
+      // inputs are 20-bit truncations, each FP32 operation adds 2^-24
+      const float kd = 8.0f * 0x1p-20f, ku = 8.0f * 0x1p-24f * vmax;
+      bool keep = true;
+#pragma unroll
+      for (int f = 0; f < NVAR; ++f) {
+        keep = keep && certify_keep(vp32[0][f], vp32[1][f], vp32[2][f], vp32[3][f], vp32[4][f],
+                                    fmaf(kd, mp[f], ku), S);
+        keep = keep && certify_keep(vm32[5][f], vm32[4][f], vm32[3][f], vm32[2][f], vm32[1][f],
+                                    fmaf(kd, mm[f], ku), S);
+      }
+      if (keep) {
+        // ---- every stencil kept at every field and side: closed form --------
+        // With fixed linear weights the characteristic reconstruction is
+        // F^ = R [ L sum_j P_j F_j + diag(alpha) L sum_j M_j U_j ] with
+        // P = (1,-8,37,37,-8,1)/60 (central) and M = (1,-5,10,-10,5,-1)/60;
+        // R L = I and alpha takes three values, so
+        // F^ = F~ + a_mid U~ + (a_0 - a_mid)(l_0.U~) r_0 + (a_E - a_mid)(l_E.U~) r_E.
+        const double P2[6] = {1.0 / 30.0, -8.0 / 30.0, 37.0 / 30.0, 37.0 / 30.0, -8.0 / 30.0, 1.0 / 30.0};
+        const double Mw[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+        double Ft[NVAR], Ut[NVAR];
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) Ft[v] = Ut[v] = 0.0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          // F_j / 2 = (u_d/2) U_j + (p/2) (0, e_d, u_d)
+          const double cu = P2[j] * un[j];
+#pragma unroll
+          for (int v = 0; v < NVAR; ++v) {
+            Ft[v] = fma(cu, Ux[j][v], Ft[v]);
+            Ut[v] = fma(Mw[j], Ux[j][v], Ut[v]);
+          }
+          Ft[1 + DIR] = fma(P2[j], pn[j], Ft[1 + DIR]);
+          Ft[NVAR - 1] = fma(cu + cu, pn[j], Ft[NVAR - 1]);
+        }
+        double wt[NVAR];
+        project<NDIM, DIR>(Ut, u, hb1, hb2, hic, wt);
+        const double amid = -nal[1];
+        const double g0 = (nal[1] - nal[0]) * wt[0];
+        const double gE = (nal[1] - nal[NVAR - 1]) * wt[NVAR - 1];
+        const double gs = g0 + gE, gd = gE - g0;
+        out[0] = fma(amid, Ut[0], Ft[0]) + gs;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+          double o = fma(u[k], gs, fma(amid, Ut[1 + k], Ft[1 + k]));
+          if (k == DIR) o = fma(cs, gd, o);
+          out[1 + k] = o;
+        }
+        out[NVAR - 1] = fma(H, gs, fma(u[DIR] * cs, gd, fma(amid, Ut[NVAR - 1], Ft[NVAR - 1])));
+#pragma unroll
+        for (int f = 0; f < NVAR; ++f) fl[f][0] = fl[f][1] = 7u;
+        return;
+      }
+    }
 
     // Characteristic values w = L U and the split fluxes v+- = (g +- alpha w)/2
     // with g = L F.  Since F(U) = u_d U + p (0, e_d, u_d) (eq. 4.7),

@@ -133,19 +133,27 @@ def test_turbulence_256_sampled(api, oracle):
     _sampled(api, oracle, inputs.solenoidal_turbulence(n=256), 2000, 2)
 
 
-@pytest.mark.parametrize("case", ["sod", "rand2d", "rand3d", "turb"])
-def test_flag_free_path_identical(api, case):
-    """Without a flag output the kernel decides 'all stencils kept' with a single
-    comparison; the right-hand side must equal the flag-producing path bit for bit."""
+@pytest.mark.parametrize("case", ["sod", "shu", "rand2d", "rand3d", "turb", "smooth3d"])
+def test_flag_free_path(api, oracle, case):
+    """Without a flag output the kernel takes the certified fast paths (FP32
+    pre-tests, and the closed form when every stencil is kept).  Its right-hand
+    side must match the oracle (under the selections the flag path reports) to
+    the same 1e-12, and the flag path to rounding."""
     P = {"sod": lambda: inputs.shock_tube(300),
+         "shu": lambda: inputs.shu_osher(4096),
          "rand2d": lambda: inputs.Problem("r2", inputs.random_discontinuous_state(2, (40, 30), seed=5),
                                           (40, 30), (0.02, 0.03), (1, 0), 0.0),
          "rand3d": lambda: inputs.Problem("r3", inputs.random_discontinuous_state(3, (12, 10, 9), seed=6),
                                           (12, 10, 9), (0.1, 0.1, 0.1), (0, 1, 0), 0.0),
-         "turb": lambda: inputs.solenoidal_turbulence(n=32)}[case]()
-    a, _ = _gpu_rhs(api, P, want_flags=True)
+         "turb": lambda: inputs.solenoidal_turbulence(n=32),
+         "smooth3d": lambda: inputs.Problem("s3", inputs.random_smooth_state(3, (20, 16, 12), seed=7, amp=0.03),
+                                            (20, 16, 12), (0.1, 0.1, 0.1), (0, 0, 0), 0.0)}[case]()
+    a, fl = _gpu_rhs(api, P, want_flags=True)
     b, _ = _gpu_rhs(api, P, want_flags=False)
-    np.testing.assert_array_equal(a, b)
+    assert rel_max_err(b, a, flux_scale(P.U0, P.n, P.dx)) <= 1e-13
+    err, rep = compare_rhs(P.U0, P.n, P.dx, P.bc, b, fl, oracle)
+    assert not rep.unexplained
+    assert err <= RHS_RTOL, err
 
 
 def test_cuda_graph_replay_matches_eager(api):
