@@ -34,15 +34,18 @@ SM_COUNT = 152
 FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
 # Algorithmic FP64 work of one interface flux at nvar = 5 (3D), counting the
 # formulas the kernel evaluates in binary64 (add/mul = 1 flop, FMA = 2,
-# divide / rsqrt = 1): Roe average and eigen-coefficients 34, projection of
-# six points 6 x 20, split fluxes 6 x 32, characteristic sum 5,
-# back-projection 21; per scalar reconstruction (10 per interface) 12 for the
-# differences and the weighted sum when the certified FP32 pre-test keeps every
-# stencil, else 49 for the binary64 indicators, m, candidates and weights plus
-# 21 for the cutoff test.  The FP32 pre-test itself runs on the FP32 pipe.
-ALG_FIXED_3D = 34 + 6 * 20 + 6 * 32 + 5 + 21
-ALG_PER_RECON_KEEP = 12
-ALG_PER_RECON = 49
+# divide / rsqrt = 1).
+# * Every stencil kept at all ten reconstructions (certified in FP32): the
+#   closed form F~ + a_mid U~ + acoustic corrections -- Roe 34, per point
+#   26 (F~ and U~ sums), projection of U~ 20, corrections and output 30: 240.
+# * Otherwise the characteristic path: Roe 34, projection 6 x 20, split 6 x 28,
+#   sum 5, back-projection 21 (= 348), plus per scalar reconstruction 9 when
+#   its own FP32 pre-test keeps every stencil, else 38 for the binary64
+#   indicators, m and weights plus 21 for the cutoff test.
+ALG_CLOSED_3D = 240
+ALG_FIXED_3D = 348
+ALG_PER_RECON_KEEP = 9
+ALG_PER_RECON = 38
 ALG_CUTOFF = 21
 # The survey's nominal count of a straightforward evaluation (reported for
 # reference): 1450 flops + 45 divisions per interface.
@@ -334,13 +337,26 @@ def main() -> None:
     torch.cuda.synchronize()
     assert solver.status() == 0, "non-physical state during warm-up"
 
-    # share of scalar reconstructions that evaluate the cutoff test (flag m at
-    # which keeping every stencil is not guaranteed), on the timed start state
+    # algorithmic FP64 flops per interface on the timed start state: the flags
+    # tell, per interface, how many of its ten reconstructions fall outside the
+    # magnitudes m at which every stencil is provably kept
     _, fl = api.rhs(grid, U, want_flags=True)
-    m = (fl >> 3).to(torch.int64)
     keep_all = _keep_all_mask(grid.scheme)
-    cut_frac = float((((keep_all >> m) & 1) == 0).double().mean().item())
-    del fl, m
+    nifc_d = (n + 1) * n * n
+    nvar = grid.nvar
+    alg_sum, nk_sum, tot = 0.0, 0.0, 0
+    for d in range(3):
+        blk = fl[d * nvar * 2 * nifc_d:(d + 1) * nvar * 2 * nifc_d].view(nvar * 2, nifc_d)
+        nk = (((keep_all >> (blk >> 3).to(torch.int64)) & 1) == 0).sum(dim=0).double()
+        per = torch.where(nk == 0, torch.full_like(nk, float(ALG_CLOSED_3D)),
+                          ALG_FIXED_3D + 10 * ALG_PER_RECON_KEEP
+                          + nk * (ALG_PER_RECON - ALG_PER_RECON_KEEP + ALG_CUTOFF))
+        alg_sum += float(per.sum())
+        nk_sum += float(nk.sum())
+        tot += nifc_d
+    alg_per_ifc = alg_sum / tot
+    cut_frac = nk_sum / (10 * tot)
+    del fl
 
     # ---- device-resident timed region --------------------------------------
     clocks = ClockSampler(local)
@@ -376,8 +392,6 @@ def main() -> None:
     flux_ms, flux_n = kinds["flux"]
     nifc = (n + 1) * n * n
     flux_avg_s = flux_ms / flux_n * 1e-3
-    alg_per_ifc = (ALG_FIXED_3D + 10 * ALG_PER_RECON_KEEP
-                   + 10 * cut_frac * (ALG_PER_RECON - ALG_PER_RECON_KEEP + ALG_CUTOFF))
     achieved = alg_per_ifc * nifc / flux_avg_s / 1e12
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))

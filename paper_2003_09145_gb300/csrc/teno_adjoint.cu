@@ -10,7 +10,8 @@
 // teno_rhs_adjoint, per direction d:
 //   adj_flux_kernel  : one thread per interface: the selections by the same
 //                      device code as the forward pass, then the interface VJP
-//                      (teno_adjoint_core.cuh) with Fbar from Rbar (eq. 2.2);
+//                      (teno_adjoint_core.cuh; the closed form when every
+//                      stencil is kept) with Fbar from Rbar (eq. 2.2);
 //                      the six cells' contributions are written to a buffer
 //                      and d/dalpha is summed per block (fixed order);
 //   adj_gather_kernel: one thread per cell sums the contributions of every
@@ -96,14 +97,17 @@ __global__ void __launch_bounds__(kAdjThreads) adj_flux_kernel(
     int64_t cells[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) cells[j] = base + teno::ghost(id - 3 + j, nd, bcd) * stride_d;
-    // the primal selections, by the forward device code
+    // the primal selections: the forward pass's own device code (the same
+    // certified tests and binary64 decisions teno_rhs / teno_rk3_step take)
     double fout[NVAR];
     unsigned fl[NVAR][2];
-    teno::interface_flux<NDIM, DIR, true>(U, aux, ncell, cells, ha, nfa, S, fout, fl, status);
+    teno::interface_flux<NDIM, DIR, false>(U, aux, ncell, cells, ha, nfa, S, fout, fl, status);
     unsigned sel[NVAR][2];
+    bool all_kept = true;
     for (int s = 0; s < NVAR; ++s) {
       sel[s][0] = fl[s][0] & 7u;
       sel[s][1] = fl[s][1] & 7u;
+      all_kept = all_kept && sel[s][0] == 7u && sel[s][1] == 7u;
     }
     double Up[6][NVAR];
     for (int j = 0; j < 6; ++j)
@@ -118,7 +122,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_flux_kernel(
       Fb[v] = a * fscale;
     }
     double Ub[6][NVAR], ab[NVAR];
-    teno_adj::interface_vjp<NDIM, DIR>(Up, fa, sel, S.gamma, Fb, Ub, ab);
+    if (all_kept)
+      teno_adj::interface_vjp_kept<NDIM, DIR>(Up, fa, S.gamma, Fb, Ub, ab);
+    else
+      teno_adj::interface_vjp<NDIM, DIR>(Up, fa, sel, S.gamma, Fb, Ub, ab);
     for (int j = 0; j < 6; ++j)
       for (int v = 0; v < NVAR; ++v) contrib[(int64_t)(j * NVAR + v) * nifc + q] = Ub[j][v];
     asum[0] += ab[0];

@@ -262,6 +262,174 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   }
 }
 
+// Vector-Jacobian product of the interface flux when every stencil of every
+// field and side is kept (delta = 1 everywhere).  The reconstruction then has
+// the fixed linear weights of eq. 2.3 and, with R L = I and the three distinct
+// LF speeds (a_0, a_mid, a_E),
+//   F^ = sum_j P_j F_j + a_mid U~ + (a_0 - a_mid)(l_0 . U~) r_0
+//                              + (a_E - a_mid)(l_E . U~) r_E,
+//   P = (1,-8,37,37,-8,1)/60,  U~ = sum_j M_j U_j,  M = (1,-5,10,-10,5,-1)/60.
+// Same inputs and outputs as interface_vjp (ab[1] receives the whole
+// derivative with respect to a_mid; the other middle entries are zero).
+template <int NDIM, int DIR>
+TENO_HD inline void interface_vjp_kept(const double (&Up)[6][NDIM + 2], const double (&alpha)[NDIM + 2],
+                                       double gamma, const double (&Fb)[NDIM + 2],
+                                       double (&Ub)[6][NDIM + 2], double (&ab)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  constexpr int E = NDIM + 1;
+  constexpr int N = DIR;
+  const double gm1 = gamma - 1.0;
+  const double P[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
+  const double M[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+
+  // ---- forward quantities ------------------------------------------------------
+  double rho[6], u[6][NDIM], p[6], q[6];
+  for (int j = 0; j < 6; ++j) {
+    rho[j] = Up[j][0];
+    q[j] = 0.0;
+    for (int k = 0; k < NDIM; ++k) {
+      u[j][k] = Up[j][1 + k] / rho[j];
+      q[j] += u[j][k] * u[j][k];
+    }
+    p[j] = gm1 * (Up[j][E] - 0.5 * rho[j] * q[j]);
+  }
+  const double sa = sqrt(rho[2]), sb = sqrt(rho[3]), S = sa + sb;
+  const double Ha = (Up[2][E] + p[2]) / rho[2], Hb = (Up[3][E] + p[3]) / rho[3];
+  double ut[NDIM], q2 = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    ut[k] = (sa * u[2][k] + sb * u[3][k]) / S;
+    q2 += ut[k] * ut[k];
+  }
+  const double H = (sa * Ha + sb * Hb) / S;
+  const double c2 = gm1 * (H - 0.5 * q2);
+  const double c = sqrt(c2);
+  const double b1 = gm1 / c2;
+  const double b2 = 0.5 * b1 * q2;
+  const double un = ut[N];
+  const double ic = 1.0 / c, ic2 = ic * ic;
+
+  double Ut[NV];
+  for (int v = 0; v < NV; ++v) {
+    Ut[v] = 0.0;
+    for (int j = 0; j < 6; ++j) Ut[v] += M[j] * Up[j][v];
+  }
+  // l_0 . X = A + B, l_E . X = A - B with A = (b2 X0 - b1 (u.Xm - XE))/2, B = (un X0 - X_{1+n})/(2c)
+  double Sx = -Ut[E];
+  for (int k = 0; k < NDIM; ++k) Sx += ut[k] * Ut[1 + k];
+  const double Ax = 0.5 * (b2 * Ut[0] - b1 * Sx);
+  const double Bx = 0.5 * (un * Ut[0] - Ut[1 + N]) * ic;
+  const double l0U = Ax + Bx, lEU = Ax - Bx;
+  // r_0 . Fb and r_E . Fb
+  double rs = Fb[0];
+  for (int k = 0; k < NDIM; ++k) rs += ut[k] * Fb[1 + k];
+  rs += H * Fb[E];
+  const double rd = c * (Fb[1 + N] + un * Fb[E]);
+  const double rho0 = rs - rd, rhoE = rs + rd;
+  const double amid = alpha[1];
+  const double d0 = alpha[0] - amid, dE = alpha[E] - amid;
+  const double g0 = d0 * l0U, gE = dE * lEU;
+
+  // ---- alpha ---------------------------------------------------------------
+  double FU = 0.0;
+  for (int v = 0; v < NV; ++v) FU += Fb[v] * Ut[v];
+  for (int s = 0; s < NV; ++s) ab[s] = 0.0;
+  ab[0] = rho0 * l0U;
+  ab[E] = rhoE * lEU;
+  ab[1] = FU - rho0 * l0U - rhoE * lEU;
+
+  // ---- U~ bar = a_mid Fb + d0 rho0 l_0 + dE rhoE l_E ---------------------------
+  const double w0 = d0 * rho0, wE = dE * rhoE;
+  double Utb[NV];
+  Utb[0] = amid * Fb[0] + 0.5 * (b2 * (w0 + wE) + un * ic * (w0 - wE));
+  for (int k = 0; k < NDIM; ++k)
+    Utb[1 + k] = amid * Fb[1 + k] - 0.5 * b1 * ut[k] * (w0 + wE) - (k == N ? 0.5 * ic * (w0 - wE) : 0.0);
+  Utb[E] = amid * Fb[E] + 0.5 * b1 * (w0 + wE);
+
+  // ---- gradients of the Roe parameters -------------------------------------
+  // L rows 0 and E are contracted with X0 = w0 U~ and XE = wE U~; R columns 0
+  // and E with fchar_0 = g0, fchar_E = gE (the other rows / columns do not
+  // enter the closed form).
+  double utb[NDIM];
+  for (int k = 0; k < NDIM; ++k) utb[k] = 0.0;
+  double Hbar = 0.0, cb = 0.0, b1b = 0.0, b2b = 0.0, q2b = 0.0;
+  {
+    const double sX = w0 + wE, dX = w0 - wE;
+    b2b += 0.5 * sX * Ut[0];
+    utb[N] += 0.5 * ic * dX * Ut[0];
+    cb += -0.5 * un * ic2 * dX * Ut[0];
+    for (int k = 0; k < NDIM; ++k) {
+      b1b += -0.5 * ut[k] * sX * Ut[1 + k];
+      utb[k] += -0.5 * b1 * sX * Ut[1 + k];
+    }
+    cb += 0.5 * ic2 * dX * Ut[1 + N];
+    b1b += 0.5 * sX * Ut[E];
+  }
+  {
+    const double fs = g0 + gE, fd = gE - g0;
+    for (int k = 0; k < NDIM; ++k) utb[k] += Fb[1 + k] * fs;
+    cb += Fb[1 + N] * fd;
+    Hbar += Fb[E] * fs;
+    utb[N] += c * Fb[E] * fd;
+    cb += un * Fb[E] * fd;
+  }
+  b1b += 0.5 * q2 * b2b;
+  q2b += 0.5 * b1 * b2b;
+  const double c2b = -(b1 / c2) * b1b + 0.5 * ic * cb;
+  Hbar += gm1 * c2b;
+  q2b += -0.5 * gm1 * c2b;
+  for (int k = 0; k < NDIM; ++k) utb[k] += 2.0 * ut[k] * q2b;
+  double ub2[NDIM], ub3[NDIM], sab = 0.0, sbb = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    ub2[k] = sa / S * utb[k];
+    ub3[k] = sb / S * utb[k];
+    sab += (u[2][k] - ut[k]) / S * utb[k];
+    sbb += (u[3][k] - ut[k]) / S * utb[k];
+  }
+  const double Hab = sa / S * Hbar, Hbb = sb / S * Hbar;
+  sab += (Ha - H) / S * Hbar;
+  sbb += (Hb - H) / S * Hbar;
+
+  // ---- per point: M_j U~bar directly, P_j Fb through the physical flux -------
+  for (int j = 0; j < 6; ++j) {
+    for (int v = 0; v < NV; ++v) Ub[j][v] = M[j] * Utb[v];
+    double Fbar[NV];
+    for (int v = 0; v < NV; ++v) Fbar[v] = P[j] * Fb[v];
+    double rhob = 0.0, Eb = 0.0, pb = 0.0, ub_[NDIM], mb[NDIM];
+    for (int k = 0; k < NDIM; ++k) ub_[k] = mb[k] = 0.0;
+    if (j == 2 || j == 3) {
+      const double sx = (j == 2) ? sa : sb;
+      const double sxb = (j == 2) ? sab : sbb;
+      const double Hx = (j == 2) ? Ha : Hb;
+      const double Hxb = (j == 2) ? Hab : Hbb;
+      rhob += 0.5 / sx * sxb;
+      Eb += Hxb / rho[j];
+      pb += Hxb / rho[j];
+      rhob += -Hx / rho[j] * Hxb;
+      for (int k = 0; k < NDIM; ++k) ub_[k] += (j == 2) ? ub2[k] : ub3[k];
+    }
+    rhob += Fbar[0] * u[j][N];
+    ub_[N] += Fbar[0] * rho[j];
+    for (int k = 0; k < NDIM; ++k) {
+      mb[k] += Fbar[1 + k] * u[j][N];
+      ub_[N] += Fbar[1 + k] * Up[j][1 + k];
+    }
+    pb += Fbar[1 + N];
+    ub_[N] += Fbar[E] * (Up[j][E] + p[j]);
+    Eb += Fbar[E] * u[j][N];
+    pb += Fbar[E] * u[j][N];
+    Eb += gm1 * pb;
+    rhob += -0.5 * gm1 * q[j] * pb;
+    for (int k = 0; k < NDIM; ++k) ub_[k] += -gm1 * rho[j] * u[j][k] * pb;
+    for (int k = 0; k < NDIM; ++k) {
+      mb[k] += ub_[k] / rho[j];
+      rhob += -u[j][k] / rho[j] * ub_[k];
+    }
+    Ub[j][0] += rhob;
+    for (int k = 0; k < NDIM; ++k) Ub[j][1 + k] += mb[k];
+    Ub[j][E] += Eb;
+  }
+}
+
 // d|lambda|/dU at one cell for lambda = u_d - c (kind 0), u_d (kind 1) or
 // u_d + c (kind 2), c = sqrt(gamma p / rho); returns the gradient scaled by s.
 template <int NDIM>

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
 // ---------------------------------------------------------------------------
 
 #ifndef TENO_FLUX_MINBLOCKS
-#define TENO_FLUX_MINBLOCKS 1
+#define TENO_FLUX_MINBLOCKS 4
 #endif
 
 template <int NDIM, int DIR, bool WITH_FLAGS>
