@@ -123,6 +123,37 @@ def _sampled(api, oracle, P, m, seed):
     return rep
 
 
+def _sampled_flag_free(api, oracle, P, m, seed):
+    """The benchmark's path (no flag output: certified fast paths) at full size,
+    against the oracle on m sampled cells, with the selections the flag path
+    reports for the same state."""
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
+    R_fast = api.rhs(grid, U, want_flags=False)
+    R_flag, fl = api.rhs(grid, U, want_flags=True)
+    torch.cuda.synchronize()
+    R_fast = R_fast.cpu().numpy().reshape(P.U0.shape[0], -1)
+    fl = fl.cpu().numpy()
+    rng = np.random.default_rng(seed)
+    cells = np.unique(np.concatenate([rng.integers(0, P.ncell, size=m), [0, P.ncell - 1]]))
+    Sf = oracle.euler_rhs_sample(P.U0, P.n, P.dx, P.bc, cells, flags_in=fl)
+    err = rel_max_err(R_fast[:, cells], np.ascontiguousarray(Sf.T), flux_scale(P.U0, P.n, P.dx))
+    assert err <= RHS_RTOL, err
+    # and the two GPU paths agree to rounding on the whole grid
+    assert rel_max_err(R_fast, R_flag.cpu().numpy().reshape(R_fast.shape),
+                       flux_scale(P.U0, P.n, P.dx)) <= 1e-13
+
+
+@pytest.mark.slow
+def test_turbulence_256_flag_free_sampled(api, oracle):
+    _sampled_flag_free(api, oracle, inputs.solenoidal_turbulence(n=256), 2000, 3)
+
+
+@pytest.mark.slow
+def test_four_quadrant_2048_flag_free_sampled(api, oracle):
+    _sampled_flag_free(api, oracle, inputs.riemann_2d(n=2048), 3000, 4)
+
+
 @pytest.mark.slow
 def test_four_quadrant_2048_sampled(api, oracle):
     _sampled(api, oracle, inputs.riemann_2d(n=2048), 4000, 1)
