@@ -8,12 +8,15 @@
 // through its arg-max cell (lowest linear index on ties).
 //
 // teno_rhs_adjoint, per direction d:
-//   adj_flux_kernel  : one thread per interface: the selections by the same
-//                      device code as the forward pass, then the interface VJP
-//                      (teno_adjoint_core.cuh; the closed form when every
-//                      stencil is kept) with Fbar from Rbar (eq. 2.2);
-//                      the six cells' contributions are written to a buffer
-//                      and d/dalpha is summed per block (fixed order);
+//   adj_kept_kernel  : one thread per interface: the forward pass's certified
+//                      FP32 test; where it keeps every stencil, the closed-form
+//                      interface VJP (teno_adjoint_core.cuh) with Fbar from
+//                      Rbar (eq. 2.2); the rest is marked pending;
+//   adj_general_kernel: the pending interfaces, compacted per warp: the
+//                      selections by the forward pass's binary64 decisions,
+//                      then the general VJP.  Both write the six cells'
+//                      contributions to a buffer and sum d/dalpha per block
+//                      (fixed order);
 //   adj_gather_kernel: one thread per cell sums the contributions of every
 //                      (interface, stencil slot) that maps to it (boundary
 //                      ghost copies included) -- deterministic, no atomics;
@@ -58,81 +61,66 @@ __global__ void argmax_kernel(const double* __restrict__ U, const unsigned long 
   }
 }
 
+// Geometry of interface q of direction DIR: its index id along DIR, the
+// linear index of its line's cell 0 and the six stencil cells (ghosts mapped).
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(kAdjThreads) adj_flux_kernel(
-    const double* __restrict__ U, const double* __restrict__ aux,
-    const unsigned long long* __restrict__ alpha_bits, const double* __restrict__ Rbar, double scale,
-    double* __restrict__ contrib, double* __restrict__ apart, int* __restrict__ status, Grid G, Scheme S) {
-  constexpr int NVAR = NDIM + 2;
-  const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1), m2 = G.n[2] + (DIR == 2);
-  const int64_t nifc = m0 * m1 * m2;
-  const int64_t ncell = G.ncell;
-  const int64_t stride_d = (DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1]);
-  const int64_t nd = G.n[DIR];
-  const int bcd = G.bc[DIR];
-  double ha[NVAR], fa[NVAR];
-  {
-    const double am = __longlong_as_double((long long)alpha_bits[DIR * 3 + 0]);
-    const double a0 = __longlong_as_double((long long)alpha_bits[DIR * 3 + 1]);
-    const double ap = __longlong_as_double((long long)alpha_bits[DIR * 3 + 2]);
-    fa[0] = am;
-    for (int f = 1; f < NVAR - 1; ++f) fa[f] = a0;
-    fa[NVAR - 1] = ap;
-    for (int f = 0; f < NVAR; ++f) ha[f] = 0.5 * fa[f];
-  }
-  double nfa[NVAR];
-  for (int f = 0; f < NVAR; ++f) nfa[f] = -2.0 * ha[f];
-  const double fscale = scale * G.inv_dx[DIR];
-  double asum[3] = {0.0, 0.0, 0.0};
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nifc;
-       q += (int64_t)gridDim.x * blockDim.x) {
+struct IfcGeom {
+  int64_t m0, m1, nifc, ncell, stride_d, nd;
+  int bcd;
+  __device__ explicit IfcGeom(const Grid& G)
+      : m0(G.n[0] + (DIR == 0)), m1(G.n[1] + (DIR == 1)),
+        nifc((G.n[0] + (DIR == 0)) * (G.n[1] + (DIR == 1)) * (G.n[2] + (DIR == 2))), ncell(G.ncell),
+        stride_d((DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1])), nd(G.n[DIR]), bcd(G.bc[DIR]) {}
+  __device__ void locate(int64_t q, const Grid& G, int64_t& id, int64_t& base, int64_t (&cells)[6]) const {
     const int64_t i0 = q % m0;
     const int64_t r = q / m0;
     const int64_t i1 = r % m1;
     const int64_t i2 = r / m1;
-    const int64_t id = (DIR == 0) ? i0 : (DIR == 1 ? i1 : i2);
-    const int64_t base = (DIR == 0) ? (i2 * G.n[1] + i1) * G.n[0]
-                       : (DIR == 1) ? i2 * G.n[1] * G.n[0] + i0
-                                    : i1 * G.n[0] + i0;
-    int64_t cells[6];
+    id = (DIR == 0) ? i0 : (DIR == 1 ? i1 : i2);
+    base = (DIR == 0) ? (i2 * G.n[1] + i1) * G.n[0] : (DIR == 1) ? i2 * G.n[1] * G.n[0] + i0 : i1 * G.n[0] + i0;
 #pragma unroll
     for (int j = 0; j < 6; ++j) cells[j] = base + teno::ghost(id - 3 + j, nd, bcd) * stride_d;
-    // the primal selections: the forward pass's own device code (the same
-    // certified tests and binary64 decisions teno_rhs / teno_rk3_step take)
-    double fout[NVAR];
-    unsigned fl[NVAR][2];
-    teno::interface_flux<NDIM, DIR, false>(U, aux, ncell, cells, ha, nfa, S, fout, fl, status);
-    unsigned sel[NVAR][2];
-    bool all_kept = true;
-    for (int s = 0; s < NVAR; ++s) {
-      sel[s][0] = fl[s][0] & 7u;
-      sel[s][1] = fl[s][1] & 7u;
-      all_kept = all_kept && sel[s][0] == 7u && sel[s][1] == 7u;
-    }
-    double Up[6][NVAR];
-    for (int j = 0; j < 6; ++j)
-      for (int v = 0; v < NVAR; ++v) Up[j][v] = U[v * ncell + cells[j]];
-    // Fbar of interface id: R_c = -(F^_{c+1/2} - F^_{c-1/2})/dx gives
-    // dJ/dF^_id = (Rbar_id [id < n] - Rbar_{id-1} [id >= 1]) / dx
-    double Fb[NVAR];
-    for (int v = 0; v < NVAR; ++v) {
-      double a = 0.0;
-      if (id < nd) a += Rbar[v * ncell + base + id * stride_d];
-      if (id >= 1) a -= Rbar[v * ncell + base + (id - 1) * stride_d];
-      Fb[v] = a * fscale;
-    }
-    double Ub[6][NVAR], ab[NVAR];
-    if (all_kept)
-      teno_adj::interface_vjp_kept<NDIM, DIR>(Up, fa, S.gamma, Fb, Ub, ab);
-    else
-      teno_adj::interface_vjp<NDIM, DIR>(Up, fa, sel, S.gamma, Fb, Ub, ab);
-    for (int j = 0; j < 6; ++j)
-      for (int v = 0; v < NVAR; ++v) contrib[(int64_t)(j * NVAR + v) * nifc + q] = Ub[j][v];
-    asum[0] += ab[0];
-    for (int f = 1; f < NVAR - 1; ++f) asum[1] += ab[f];
-    asum[2] += ab[NVAR - 1];
   }
-  // block sum in a fixed order
+};
+
+// The three distinct LF speeds of direction DIR per field: fa = alpha,
+// ha = alpha / 2, nfa = -alpha (the forward pass's arguments).
+template <int NDIM, int DIR>
+__device__ __forceinline__ void field_speeds(const unsigned long long* __restrict__ alpha_bits,
+                                             double (&fa)[NDIM + 2], double (&ha)[NDIM + 2],
+                                             double (&nfa)[NDIM + 2]) {
+  constexpr int NVAR = NDIM + 2;
+  const double am = __longlong_as_double((long long)alpha_bits[DIR * 3 + 0]);
+  const double a0 = __longlong_as_double((long long)alpha_bits[DIR * 3 + 1]);
+  const double ap = __longlong_as_double((long long)alpha_bits[DIR * 3 + 2]);
+  fa[0] = am;
+#pragma unroll
+  for (int f = 1; f < NVAR - 1; ++f) fa[f] = a0;
+  fa[NVAR - 1] = ap;
+#pragma unroll
+  for (int f = 0; f < NVAR; ++f) {
+    ha[f] = 0.5 * fa[f];
+    nfa[f] = -2.0 * ha[f];
+  }
+}
+
+// Fbar of interface id of a line: R_c = -(F^_{c+1/2} - F^_{c-1/2})/dx gives
+// dJ/dF^_id = (Rbar_id [id < n] - Rbar_{id-1} [id >= 1]) / dx (eq. 2.2).
+template <int NVAR>
+__device__ __forceinline__ void interface_fbar(const double* __restrict__ Rbar, int64_t ncell, int64_t base,
+                                               int64_t id, int64_t nd, int64_t stride_d, double fscale,
+                                               double (&Fb)[NVAR]) {
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    double a = 0.0;
+    if (id < nd) a += Rbar[v * ncell + base + id * stride_d];
+    if (id >= 1) a -= Rbar[v * ncell + base + (id - 1) * stride_d];
+    Fb[v] = a * fscale;
+  }
+}
+
+// Block sum of asum in a fixed order into apart[blockIdx.x].
+__device__ __forceinline__ void block_alpha_sum(const double (&asum)[3], double* __restrict__ apart) {
   __shared__ double red[kAdjThreads][3];
   for (int k = 0; k < 3; ++k) red[threadIdx.x][k] = asum[k];
   __syncthreads();
@@ -145,17 +133,218 @@ __global__ void __launch_bounds__(kAdjThreads) adj_flux_kernel(
     for (int k = 0; k < 3; ++k) apart[blockIdx.x * 3 + k] = red[0][k];
 }
 
-// Ubar_c += sum over (interface, slot j) whose stencil point maps to cell c.
+template <int NVAR>
+__device__ __forceinline__ void add_alpha(const double (&ab)[NVAR], double (&asum)[3]) {
+  asum[0] += ab[0];
+#pragma unroll
+  for (int f = 1; f < NVAR - 1; ++f) asum[1] += ab[f];
+  asum[2] += ab[NVAR - 1];
+}
+
+// One thread per interface: the forward pass's certified FP32 test (the
+// same device code teno_rhs / teno_rk3_step run).  Where it keeps every
+// stencil, the interface part of the closed-form VJP: U~bar and the
+// Roe-parameter terms of cells i and i+1 go to kb[15][nifc] (the flux
+// Jacobians are applied per cell by the gather); elsewhere the interface is
+// marked pending for adj_general_kernel.
+#ifndef TENO_ADJ_KEPT_MINBLOCKS
+#define TENO_ADJ_KEPT_MINBLOCKS 3   // 168 registers: 12 warps per SM
+#endif
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(256) adj_gather_kernel(const double* __restrict__ contrib,
-                                                         double* __restrict__ Ubar, Grid G) {
+__global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept_kernel(
+    const double* __restrict__ U, const double* __restrict__ aux,
+    const unsigned long long* __restrict__ alpha_bits, const double* __restrict__ Rbar, double scale,
+    double* __restrict__ kb, unsigned char* __restrict__ pending, double* __restrict__ apart,
+    int* __restrict__ status, Grid G, Scheme S) {
+  constexpr int NVAR = NDIM + 2;
+  const IfcGeom<NDIM, DIR> I(G);
+  double fa[NVAR], ha[NVAR], nfa[NVAR];
+  field_speeds<NDIM, DIR>(alpha_bits, fa, ha, nfa);
+  const double fscale = scale * G.inv_dx[DIR];
+  const double M[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+  double asum[3] = {0.0, 0.0, 0.0};
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < I.nifc;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t id, base, cells[6];
+    I.locate(q, G, id, base, cells);
+    double fout[NVAR];
+    unsigned fl[NVAR][2];
+    teno::interface_flux<NDIM, DIR, false, teno::kFluxCertify>(U, aux, I.ncell, cells, ha, nfa, S, fout, fl,
+                                                               status);
+    const bool kept = fl[0][0] != teno::kUndecided;
+    pending[q] = kept ? 0 : 1;
+    if (!kept) continue;
+    double Ut[NVAR];
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) {
+      double t = 0.0;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) t = fma(M[j], U[v * I.ncell + cells[j]], t);
+      Ut[v] = t;
+    }
+    // Roe state from the cell pass's primitives (u/2, p/2, sqrt(rho), (E+p)/sqrt(rho))
+    double ua[NDIM], ub[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+      ua[k] = 2.0 * aux[k * I.ncell + cells[2]];
+      ub[k] = 2.0 * aux[k * I.ncell + cells[3]];
+    }
+    teno_adj::RoeState<NDIM> R;
+    teno_adj::roe_from_primitives<NDIM>(aux[(NDIM + 1) * I.ncell + cells[2]], aux[(NDIM + 1) * I.ncell + cells[3]],
+                                        aux[(NDIM + 2) * I.ncell + cells[2]], aux[(NDIM + 2) * I.ncell + cells[3]],
+                                        ua, ub, S.gamma, R);
+    double Fb[NVAR];
+    interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
+    double Utb[NVAR], roeA[NVAR], roeB[NVAR], ab[NVAR];
+    teno_adj::interface_vjp_kept_ifc<NDIM, DIR>(R, Ut, fa, S.gamma, Fb, Utb, roeA, roeB, ab);
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) {
+      kb[(int64_t)v * I.nifc + q] = Utb[v];
+      kb[(int64_t)(NVAR + v) * I.nifc + q] = roeA[v];
+      kb[(int64_t)(2 * NVAR + v) * I.nifc + q] = roeB[v];
+    }
+    add_alpha<NVAR>(ab, asum);
+  }
+  block_alpha_sum(asum, apart);
+}
+
+// The pending interfaces: each warp scans its chunks of 32 in order, queues
+// the pending ones in shared memory and processes them 32 at a time (the
+// selections by the forward pass's own binary64 decisions, then the general
+// VJP, or the closed form where every stencil is kept after all); the six
+// cells' contributions go to contrib[6 nvar][nifc].  The order of the
+// d/dalpha sums is fixed by the grid, so results are deterministic.
+template <int NDIM, int DIR>
+__global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
+    const double* __restrict__ U, const double* __restrict__ aux,
+    const unsigned long long* __restrict__ alpha_bits, const double* __restrict__ Rbar, double scale,
+    double* __restrict__ contrib, const unsigned char* __restrict__ pending, double* __restrict__ apart,
+    int* __restrict__ status, Grid G, Scheme S) {
+  constexpr int NVAR = NDIM + 2;
+  constexpr int kWarps = kAdjThreads / 32;
+  __shared__ int64_t queue[kWarps][64];
+  const IfcGeom<NDIM, DIR> I(G);
+  double fa[NVAR], ha[NVAR], nfa[NVAR];
+  field_speeds<NDIM, DIR>(alpha_bits, fa, ha, nfa);
+  const double fscale = scale * G.inv_dx[DIR];
+  double asum[3] = {0.0, 0.0, 0.0};
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  int64_t chunk = (int64_t)blockIdx.x * kWarps + wid;   // chunks of 32 interfaces
+  const int64_t nchunk = (I.nifc + 31) / 32;
+  int qn = 0;                                           // queued entries (warp-uniform)
+  for (;;) {
+    while (qn < 32 && chunk < nchunk) {
+      const int64_t q = chunk * 32 + lane;
+      const bool p = q < I.nifc && pending[q] != 0;
+      const unsigned m = __ballot_sync(0xffffffffu, p);
+      if (p) queue[wid][qn + __popc(m & ((1u << lane) - 1u))] = q;
+      qn += __popc(m);
+      chunk += nwarps;
+    }
+    __syncwarp();
+    if (qn == 0) break;
+    if (lane < qn) {
+      const int64_t q = queue[wid][lane];
+      int64_t id, base, cells[6];
+      I.locate(q, G, id, base, cells);
+      double fout[NVAR];
+      unsigned fl[NVAR][2];
+      teno::interface_flux<NDIM, DIR, false, teno::kFluxSelect>(U, aux, I.ncell, cells, ha, nfa, S, fout, fl,
+                                                                status);
+      unsigned sel[NVAR][2];
+      bool all_kept = true;
+#pragma unroll
+      for (int f = 0; f < NVAR; ++f) {
+        sel[f][0] = fl[f][0] & 7u;
+        sel[f][1] = fl[f][1] & 7u;
+        all_kept = all_kept && sel[f][0] == 7u && sel[f][1] == 7u;
+      }
+      double Up[6][NVAR];
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) Up[j][v] = U[v * I.ncell + cells[j]];
+      double Fb[NVAR];
+      interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
+      double Ub[6][NVAR], ab[NVAR];
+      if (all_kept)
+        teno_adj::interface_vjp_kept<NDIM, DIR>(Up, fa, S.gamma, Fb, Ub, ab);
+      else
+        teno_adj::interface_vjp<NDIM, DIR>(Up, fa, sel, S.gamma, Fb, Ub, ab);
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) contrib[(int64_t)(j * NVAR + v) * I.nifc + q] = Ub[j][v];
+      add_alpha<NVAR>(ab, asum);
+    }
+    __syncwarp();
+    const int rest = qn > 32 ? qn - 32 : 0;
+    const int64_t moved = (lane < rest) ? queue[wid][32 + lane] : 0;
+    __syncwarp();
+    if (lane < rest) queue[wid][lane] = moved;
+    qn = rest;
+  }
+  block_alpha_sum(asum, apart);
+}
+
+// The all-kept weights of the stencil points: P for F~ = sum_j P_j F_j and M
+// for U~ = sum_j M_j U_j (indexed by a warp-uniform slot number).
+__constant__ double c_adjP[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
+__constant__ double c_adjM[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+
+// The share of interface q's slot j at the cell that slot maps to: the
+// pending interface's own contribution, or for a kept one M_j U~bar_q (plus
+// the Roe terms at j = 2, 3) into acc and P_j Fbar_q into Fsum.
+template <int NVAR>
+__device__ __forceinline__ void gather_slot(int j, int64_t q, int64_t qd, const double* __restrict__ contrib,
+                                            const double* __restrict__ kb,
+                                            const unsigned char* __restrict__ pending,
+                                            const double* __restrict__ Rbar, int64_t nifc, int64_t ncell,
+                                            int64_t line, int64_t nd, int64_t cstride,
+                                            double (&acc)[NVAR], double (&Fsum)[NVAR]) {
+  const double Pj = c_adjP[j], Mj = c_adjM[j];
+  if (pending[q]) {
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
+    return;
+  }
+  // P_j (Rbar_qd [qd < n] - Rbar_{qd-1} [qd >= 1]); the 1/dx follows per cell
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    const double ra = (qd < nd) ? Rbar[v * ncell + line + qd * cstride] : 0.0;
+    const double rb = (qd >= 1) ? Rbar[v * ncell + line + (qd - 1) * cstride] : 0.0;
+    Fsum[v] = fma(Pj, ra - rb, Fsum[v]);
+    acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
+  }
+  if (j == 2)
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(NVAR + v) * nifc + q];
+  if (j == 3)
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+}
+
+// Ubar_c += sum over (interface, slot j) whose stencil point maps to cell c
+// (boundary ghost copies included): the pending interfaces' contributions,
+// M_j U~bar and the Roe terms of the kept ones, and A(U_c)^T applied once to
+// sum_j P_j Fbar of the kept ones.  Deterministic, no atomics.
+template <int NDIM, int DIR>
+__global__ void __launch_bounds__(256) adj_gather_kernel(const double* __restrict__ U,
+                                                         const double* __restrict__ Rbar, double scale,
+                                                         const double* __restrict__ kb,
+                                                         const double* __restrict__ contrib,
+                                                         const unsigned char* __restrict__ pending,
+                                                         double* __restrict__ Ubar, Grid G, double gamma) {
   constexpr int NVAR = NDIM + 2;
   const int64_t ncell = G.ncell;
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
   const int64_t nifc = m0 * m1 * (G.n[2] + (DIR == 2));
   const int64_t sd = (DIR == 0) ? 1 : (DIR == 1 ? m0 : m0 * m1);   // interface-grid stride along DIR
+  const int64_t cstride = (DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1]);
   const int64_t nd = G.n[DIR];
   const int bc = G.bc[DIR];
+  const double fscale = scale * G.inv_dx[DIR];
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i0 = c % G.n[0];
@@ -163,37 +352,47 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const double* __restric
     const int64_t i1 = r % G.n[1];
     const int64_t i2 = r / G.n[1];
     const int64_t id = (DIR == 0) ? i0 : (DIR == 1 ? i1 : i2);
-    // interface-grid index of this line's interface 0
+    // interface-grid index of this line's interface 0, and the line's cell 0
     const int64_t q0 = (i2 * m1 + i1) * m0 + i0 - id * sd;
-    double acc[NVAR];
-    for (int v = 0; v < NVAR; ++v) acc[v] = 0.0;
+    const int64_t line = c - id * cstride;
+    double acc[NVAR], Fsum[NVAR];
+    for (int v = 0; v < NVAR; ++v) acc[v] = Fsum[v] = 0.0;
+    const int idl = int(id), ndl = int(nd);
     for (int j = 0; j < 6; ++j) {
       // interfaces qd in [0, nd] whose point j, ghost(qd - 3 + j), is cell id
       if (bc == 0) {
         // x = qd - 3 + j ranges over [j - 3, nd + j - 3]; x = id (mod nd)
-        int64_t x = id + ((j - 3 - id) / nd) * nd;
-        while (x < j - 3) x += nd;
-        while (x - nd >= j - 3) x -= nd;
-        for (; x <= nd + j - 3; x += nd) {
-          const int64_t qd = x + 3 - j;
-          for (int v = 0; v < NVAR; ++v) acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q0 + qd * sd];
+        int x = idl;
+        while (x - ndl >= j - 3) x -= ndl;
+        while (x < j - 3) x += ndl;
+        for (; x <= ndl + j - 3; x += ndl) {
+          const int qd = x + 3 - j;
+          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride,
+                            acc, Fsum);
         }
       } else {
         // transmissive: points below 0 map to cell 0, points above nd-1 to nd-1
-        int64_t lo = id + 3 - j, hi = id + 3 - j;
-        if (id == 0) lo = 0;
-        if (id == nd - 1) hi = nd;
+        int lo = idl + 3 - j, hi = idl + 3 - j;
+        if (idl == 0) lo = 0;
+        if (idl == ndl - 1) hi = ndl;
         if (lo < 0) lo = 0;
-        if (hi > nd) hi = nd;
-        for (int64_t qd = lo; qd <= hi; ++qd) {
-          const int64_t x = qd - 3 + j;
-          const int64_t mapped = x < 0 ? 0 : (x >= nd ? nd - 1 : x);
-          if (mapped != id) continue;
-          for (int v = 0; v < NVAR; ++v) acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q0 + qd * sd];
+        if (hi > ndl) hi = ndl;
+        for (int qd = lo; qd <= hi; ++qd) {
+          const int x = qd - 3 + j;
+          const int mapped = x < 0 ? 0 : (x >= ndl ? ndl - 1 : x);
+          if (mapped != idl) continue;
+          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride,
+                            acc, Fsum);
         }
       }
     }
-    for (int v = 0; v < NVAR; ++v) Ubar[v * ncell + c] += acc[v];
+    double Uc[NVAR], AF[NVAR];
+    for (int v = 0; v < NVAR; ++v) {
+      Uc[v] = U[v * ncell + c];
+      Fsum[v] *= fscale;
+    }
+    teno_adj::flux_vjp<NDIM, DIR>(Uc, gamma, Fsum, AF);
+    for (int v = 0; v < NVAR; ++v) Ubar[v * ncell + c] += acc[v] + AF[v];
   }
 }
 
@@ -262,7 +461,7 @@ int adj_blocks(int nsm) { return nsm * 8; }
 struct AdjLayout {
   // header: [0] status, [8] dt, [64] alpha bits (9 x 8), [160] arg-max (9 x 8)
   size_t status = 0, dt = 8, alpha = 64, argidx = 160;
-  size_t aux = 0, contrib = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0, total = 0;
+  size_t aux = 0, kb = 0, contrib = 0, pending = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0, total = 0;
 };
 
 AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
@@ -274,10 +473,14 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   size_t off = kAlign;
   L.aux = off;
   off += round_up(sizeof(double) * (g->ndim + 3) * ncell);
+  L.kb = off;
+  off += round_up(sizeof(double) * 3 * nvar * size_t(maxifc));
   L.contrib = off;
   off += round_up(sizeof(double) * 6 * nvar * size_t(maxifc));
+  L.pending = off;
+  off += round_up(size_t(maxifc));
   L.apart = off;
-  off += round_up(sizeof(double) * 3 * size_t(adj_blocks(nsm)));
+  off += round_up(sizeof(double) * 3 * 2 * size_t(adj_blocks(nsm)));
   if (op == TENO_OP_RK3_ADJOINT) {
     // forward recomputation (R, U1, U2) and the stage adjoints (B1, B2)
     L.R = off;
@@ -328,15 +531,19 @@ bool al(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 
 
 template <int NDIM, int DIR>
 void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const double* aux,
-                    const unsigned long long* alpha, const double* Rbar, double scale, double* contrib,
-                    double* apart, int* status, double* Ubar, const unsigned long long* argidx,
+                    const unsigned long long* alpha, const double* Rbar, double scale, double* kb,
+                    double* contrib, unsigned char* pending, double* apart, int* status, double* Ubar,
+                    const unsigned long long* argidx,
                     const Grid& G, const Scheme& S) {
-  adj_flux_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, contrib, apart,
+  adj_kept_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
                                                           status, G, S);
+  adj_general_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, contrib, pending,
+                                                             apart + 3 * nblk, status, G, S);
   int64_t gb = (G.ncell + 255) / 256;
   if (gb > int64_t(nsm) * 16) gb = int64_t(nsm) * 16;
-  adj_gather_kernel<NDIM, DIR><<<unsigned(gb), 256, 0, st>>>(contrib, Ubar, G);
-  adj_alpha_kernel<NDIM><<<1, 32, 0, st>>>(apart, nblk, argidx, DIR, U, Ubar, G.ncell, S.gamma);
+  adj_gather_kernel<NDIM, DIR><<<unsigned(gb), 256, 0, st>>>(U, Rbar, scale, kb, contrib, pending, Ubar, G,
+                                                              S.gamma);
+  adj_alpha_kernel<NDIM><<<1, 32, 0, st>>>(apart, 2 * nblk, argidx, DIR, U, Ubar, G.ncell, S.gamma);
 }
 
 // Ubar += scale * J(U)^T Rbar
@@ -350,8 +557,10 @@ teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, c
   auto* alpha = reinterpret_cast<unsigned long long*>(ws + L.alpha);
   auto* argidx = reinterpret_cast<unsigned long long*>(ws + L.argidx);
   double* aux = reinterpret_cast<double*>(ws + L.aux);
+  double* kb = reinterpret_cast<double*>(ws + L.kb);
   double* contrib = reinterpret_cast<double*>(ws + L.contrib);
   double* apart = reinterpret_cast<double*>(ws + L.apart);
+  auto* pending = reinterpret_cast<unsigned char*>(ws + L.pending);
   if (cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
   if (cudaMemsetAsync(argidx, 0xff, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
   if (teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
@@ -365,12 +574,12 @@ teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, c
     default: argmax_kernel<3><<<unsigned(cb), 256, 0, st>>>(U, alpha, argidx, G.ncell, g->gamma, aux); break;
   }
   for (int d = 0; d < g->ndim; ++d) {
-    if (g->ndim == 1) launch_adj_dir<1, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, contrib, apart, status, Ubar, argidx, G, S);
-    else if (g->ndim == 2 && d == 0) launch_adj_dir<2, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, contrib, apart, status, Ubar, argidx, G, S);
-    else if (g->ndim == 2) launch_adj_dir<2, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, contrib, apart, status, Ubar, argidx, G, S);
-    else if (d == 0) launch_adj_dir<3, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, contrib, apart, status, Ubar, argidx, G, S);
-    else if (d == 1) launch_adj_dir<3, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, contrib, apart, status, Ubar, argidx, G, S);
-    else launch_adj_dir<3, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, contrib, apart, status, Ubar, argidx, G, S);
+    if (g->ndim == 1) launch_adj_dir<1, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
+    else if (g->ndim == 2 && d == 0) launch_adj_dir<2, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
+    else if (g->ndim == 2) launch_adj_dir<2, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
+    else if (d == 0) launch_adj_dir<3, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
+    else if (d == 1) launch_adj_dir<3, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
+    else launch_adj_dir<3, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
     if (cudaGetLastError() != cudaSuccess) return TENO_ERR_CUDA;
   }
   return TENO_OK;

@@ -262,57 +262,146 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   }
 }
 
-// Vector-Jacobian product of the interface flux when every stencil of every
-// field and side is kept (delta = 1 everywhere).  The reconstruction then has
-// the fixed linear weights of eq. 2.3 and, with R L = I and the three distinct
-// LF speeds (a_0, a_mid, a_E),
-//   F^ = sum_j P_j F_j + a_mid U~ + (a_0 - a_mid)(l_0 . U~) r_0
-//                              + (a_E - a_mid)(l_E . U~) r_E,
-//   P = (1,-8,37,37,-8,1)/60,  U~ = sum_j M_j U_j,  M = (1,-5,10,-10,5,-1)/60.
-// Same inputs and outputs as interface_vjp (ab[1] receives the whole
-// derivative with respect to a_mid; the other middle entries are zero).
+// ---------------------------------------------------------------------------
+// Every stencil of every field and side kept (delta = 1 everywhere).  The
+// reconstruction then has the fixed linear weights of eq. 2.3 and, with
+// R L = I and the three distinct LF speeds (a_0, a_mid, a_E),
+//   F^ = F~ + a_mid U~ + (a_0 - a_mid)(l_0 . U~) r_0 + (a_E - a_mid)(l_E . U~) r_E,
+//   F~ = sum_j P_j F(U_j),  P = (1,-8,37,37,-8,1)/60,
+//   U~ = sum_j M_j U_j,     M = (1,-5,10,-10,5,-1)/60.
+// The stencil points enter through U~ (linearly) and F~ (through the flux
+// Jacobian of each point); l_0, r_0, l_E, r_E depend on cells i and i+1 only.
+// So dJ/dU_j = P_j A(U_j)^T Fbar + M_j U~bar (+ the Roe-parameter terms at
+// j = 2, 3), and A(U_j)^T can be applied once per cell to the sum of its
+// P-weighted Fbar over the interfaces that reach it.
+// ---------------------------------------------------------------------------
+
+// out = A(U)^T G with A = dF/dU the Euler flux Jacobian of direction DIR
+// (eq. 4.7): F = u_d U + p (0, e_d, u_d), so
+//   A^T G = u_d G + s (-u_d, e_d, 0) + t (|u|^2/2, -u, 1),
+//   s = (G.U + p G_E) / rho,  t = (gamma - 1)(G_{1+d} + u_d G_E).
 template <int NDIM, int DIR>
-TENO_HD inline void interface_vjp_kept(const double (&Up)[6][NDIM + 2], const double (&alpha)[NDIM + 2],
-                                       double gamma, const double (&Fb)[NDIM + 2],
-                                       double (&Ub)[6][NDIM + 2], double (&ab)[NDIM + 2]) {
+TENO_HD inline void flux_vjp(const double (&U)[NDIM + 2], double gamma, const double (&G)[NDIM + 2],
+                             double (&out)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  constexpr int E = NDIM + 1;
+  const double gm1 = gamma - 1.0;
+  const double ir = 1.0 / U[0];
+  double u[NDIM], q = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    u[k] = U[1 + k] * ir;
+    q += u[k] * u[k];
+  }
+  const double p = gm1 * (U[E] - 0.5 * U[0] * q);
+  double GU = 0.0;
+  for (int v = 0; v < NV; ++v) GU += G[v] * U[v];
+  const double sc = ir * (GU + p * G[E]);
+  const double t = gm1 * (G[1 + DIR] + u[DIR] * G[E]);
+  const double ud = u[DIR];
+  out[0] = ud * (G[0] - sc) + 0.5 * q * t;
+  for (int k = 0; k < NDIM; ++k) out[1 + k] = ud * G[1 + k] - t * u[k] + (k == DIR ? sc : 0.0);
+  out[E] = ud * G[E] + t;
+}
+
+// Roe state of cells i (a) and i+1 (b) with the point quantities its
+// derivative needs.
+template <int NDIM>
+struct RoeState {
+  double sa, sb, iS, ira, irb, ua[NDIM], ub[NDIM], qa, qb, Ha, Hb;
+  double ut[NDIM], q2, H, c2, ic, ic2, c, b1, b2;
+};
+
+// From sqrt(rho), (E + p)/sqrt(rho) and u of both cells (one reciprocal each).
+template <int NDIM>
+TENO_HD inline void roe_from_primitives(double sa, double sb, double sha, double shb, const double (&ua)[NDIM],
+                                        const double (&ub)[NDIM], double gamma, RoeState<NDIM>& R) {
+  const double gm1 = gamma - 1.0;
+  const double rsa = 1.0 / sa, rsb = 1.0 / sb;
+  R.sa = sa;
+  R.sb = sb;
+  R.ira = rsa * rsa;
+  R.irb = rsb * rsb;
+  R.Ha = sha * rsa;
+  R.Hb = shb * rsb;
+  R.iS = 1.0 / (sa + sb);
+  R.qa = R.qb = R.q2 = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    R.ua[k] = ua[k];
+    R.ub[k] = ub[k];
+    R.qa += ua[k] * ua[k];
+    R.qb += ub[k] * ub[k];
+    R.ut[k] = (sa * ua[k] + sb * ub[k]) * R.iS;
+    R.q2 += R.ut[k] * R.ut[k];
+  }
+  R.H = (sha + shb) * R.iS;
+  R.c2 = gm1 * (R.H - 0.5 * R.q2);
+#ifdef __CUDA_ARCH__
+  R.ic = rsqrt(R.c2);
+#else
+  R.ic = 1.0 / sqrt(R.c2);
+#endif
+  R.ic2 = R.ic * R.ic;
+  R.c = R.c2 * R.ic;
+  R.b1 = gm1 * R.ic2;
+  R.b2 = 0.5 * R.b1 * R.q2;
+}
+
+// From the conservative states of both cells.
+template <int NDIM>
+TENO_HD inline void roe_from_conservative(const double (&Ua)[NDIM + 2], const double (&Ub)[NDIM + 2], double gamma,
+                                          RoeState<NDIM>& R) {
+  constexpr int E = NDIM + 1;
+  const double gm1 = gamma - 1.0;
+  const double ira = 1.0 / Ua[0], irb = 1.0 / Ub[0];
+  double ua[NDIM], ub[NDIM], qa = 0.0, qb = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    ua[k] = Ua[1 + k] * ira;
+    ub[k] = Ub[1 + k] * irb;
+    qa += ua[k] * ua[k];
+    qb += ub[k] * ub[k];
+  }
+  const double pa = gm1 * (Ua[E] - 0.5 * Ua[0] * qa), pb = gm1 * (Ub[E] - 0.5 * Ub[0] * qb);
+  const double sa = sqrt(Ua[0]), sb = sqrt(Ub[0]);
+  roe_from_primitives<NDIM>(sa, sb, (Ua[E] + pa) / sa, (Ub[E] + pb) / sb, ua, ub, gamma, R);
+}
+
+// out += dJ/dU at one of the two Roe cells, from the adjoints of its Roe
+// parameters sx = sqrt(rho), Hx = (E + p)/rho and u (ir = 1/rho, q = |u|^2):
+// with p = (gamma-1)(E - rho q/2), dHx = (dE + dp - Hx drho)/rho and
+// du = (dm - u drho)/rho.
+template <int NDIM>
+TENO_HD inline void roe_point_vjp(double ir, const double (&u)[NDIM], double q, double sx, double Hx,
+                                  double gamma, double sxb, double Hxb, const double (&uxb)[NDIM],
+                                  double (&out)[NDIM + 2]) {
+  constexpr int E = NDIM + 1;
+  const double gm1 = gamma - 1.0;
+  double uub = 0.0;
+  for (int k = 0; k < NDIM; ++k) uub += u[k] * uxb[k];
+  const double pb = Hxb * ir;
+  out[0] += 0.5 * sx * ir * sxb - Hx * pb + 0.5 * gm1 * q * pb - ir * uub;
+  for (int k = 0; k < NDIM; ++k) out[1 + k] += ir * uxb[k] - gm1 * u[k] * pb;
+  out[E] += pb + gm1 * pb;
+}
+
+// The interface part of the all-kept VJP: from the Roe state of cells i,
+// i+1, U~ and Fbar, returns U~bar, the Roe-parameter terms of cells i (roeA)
+// and i+1 (roeB), and dJ/dalpha (ab[1] receives the whole derivative with
+// respect to a_mid; the other middle entries are zero).
+template <int NDIM, int DIR>
+TENO_HD inline void interface_vjp_kept_ifc(const RoeState<NDIM>& R, const double (&Ut)[NDIM + 2],
+                                           const double (&alpha)[NDIM + 2], double gamma,
+                                           const double (&Fb)[NDIM + 2], double (&Utb)[NDIM + 2],
+                                           double (&roeA)[NDIM + 2], double (&roeB)[NDIM + 2],
+                                           double (&ab)[NDIM + 2]) {
   constexpr int NV = NDIM + 2;
   constexpr int E = NDIM + 1;
   constexpr int N = DIR;
   const double gm1 = gamma - 1.0;
-  const double P[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
-  const double M[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
-
-  // ---- forward quantities ------------------------------------------------------
-  double rho[6], u[6][NDIM], p[6], q[6];
-  for (int j = 0; j < 6; ++j) {
-    rho[j] = Up[j][0];
-    q[j] = 0.0;
-    for (int k = 0; k < NDIM; ++k) {
-      u[j][k] = Up[j][1 + k] / rho[j];
-      q[j] += u[j][k] * u[j][k];
-    }
-    p[j] = gm1 * (Up[j][E] - 0.5 * rho[j] * q[j]);
-  }
-  const double sa = sqrt(rho[2]), sb = sqrt(rho[3]), S = sa + sb;
-  const double Ha = (Up[2][E] + p[2]) / rho[2], Hb = (Up[3][E] + p[3]) / rho[3];
-  double ut[NDIM], q2 = 0.0;
-  for (int k = 0; k < NDIM; ++k) {
-    ut[k] = (sa * u[2][k] + sb * u[3][k]) / S;
-    q2 += ut[k] * ut[k];
-  }
-  const double H = (sa * Ha + sb * Hb) / S;
-  const double c2 = gm1 * (H - 0.5 * q2);
-  const double c = sqrt(c2);
-  const double b1 = gm1 / c2;
-  const double b2 = 0.5 * b1 * q2;
+  const double sa = R.sa, sb = R.sb, iS = R.iS, Ha = R.Ha, Hb = R.Hb, H = R.H;
+  const double q2 = R.q2, ic = R.ic, ic2 = R.ic2, c = R.c, b1 = R.b1, b2 = R.b2;
+  const double* ut = R.ut;
   const double un = ut[N];
-  const double ic = 1.0 / c, ic2 = ic * ic;
 
-  double Ut[NV];
-  for (int v = 0; v < NV; ++v) {
-    Ut[v] = 0.0;
-    for (int j = 0; j < 6; ++j) Ut[v] += M[j] * Up[j][v];
-  }
   // l_0 . X = A + B, l_E . X = A - B with A = (b2 X0 - b1 (u.Xm - XE))/2, B = (un X0 - X_{1+n})/(2c)
   double Sx = -Ut[E];
   for (int k = 0; k < NDIM; ++k) Sx += ut[k] * Ut[1 + k];
@@ -339,7 +428,6 @@ TENO_HD inline void interface_vjp_kept(const double (&Up)[6][NDIM + 2], const do
 
   // ---- U~ bar = a_mid Fb + d0 rho0 l_0 + dE rhoE l_E ---------------------------
   const double w0 = d0 * rho0, wE = dE * rhoE;
-  double Utb[NV];
   Utb[0] = amid * Fb[0] + 0.5 * (b2 * (w0 + wE) + un * ic * (w0 - wE));
   for (int k = 0; k < NDIM; ++k)
     Utb[1 + k] = amid * Fb[1 + k] - 0.5 * b1 * ut[k] * (w0 + wE) - (k == N ? 0.5 * ic * (w0 - wE) : 0.0);
@@ -374,59 +462,51 @@ TENO_HD inline void interface_vjp_kept(const double (&Up)[6][NDIM + 2], const do
   }
   b1b += 0.5 * q2 * b2b;
   q2b += 0.5 * b1 * b2b;
-  const double c2b = -(b1 / c2) * b1b + 0.5 * ic * cb;
+  const double c2b = -(b1 * ic2) * b1b + 0.5 * ic * cb;
   Hbar += gm1 * c2b;
   q2b += -0.5 * gm1 * c2b;
   for (int k = 0; k < NDIM; ++k) utb[k] += 2.0 * ut[k] * q2b;
-  double ub2[NDIM], ub3[NDIM], sab = 0.0, sbb = 0.0;
+  double uab[NDIM], ubb[NDIM], sab = 0.0, sbb = 0.0;
   for (int k = 0; k < NDIM; ++k) {
-    ub2[k] = sa / S * utb[k];
-    ub3[k] = sb / S * utb[k];
-    sab += (u[2][k] - ut[k]) / S * utb[k];
-    sbb += (u[3][k] - ut[k]) / S * utb[k];
+    uab[k] = sa * iS * utb[k];
+    ubb[k] = sb * iS * utb[k];
+    sab += (R.ua[k] - ut[k]) * iS * utb[k];
+    sbb += (R.ub[k] - ut[k]) * iS * utb[k];
   }
-  const double Hab = sa / S * Hbar, Hbb = sb / S * Hbar;
-  sab += (Ha - H) / S * Hbar;
-  sbb += (Hb - H) / S * Hbar;
+  sab += (Ha - H) * iS * Hbar;
+  sbb += (Hb - H) * iS * Hbar;
+  for (int v = 0; v < NV; ++v) roeA[v] = roeB[v] = 0.0;
+  roe_point_vjp<NDIM>(R.ira, R.ua, R.qa, sa, Ha, gamma, sab, sa * iS * Hbar, uab, roeA);
+  roe_point_vjp<NDIM>(R.irb, R.ub, R.qb, sb, Hb, gamma, sbb, sb * iS * Hbar, ubb, roeB);
+}
 
-  // ---- per point: M_j U~bar directly, P_j Fb through the physical flux -------
+// The whole all-kept VJP of one interface, as interface_vjp (same inputs and
+// outputs): the interface part plus P_j A(U_j)^T Fbar at every point.
+template <int NDIM, int DIR>
+TENO_HD inline void interface_vjp_kept(const double (&Up)[6][NDIM + 2], const double (&alpha)[NDIM + 2],
+                                       double gamma, const double (&Fb)[NDIM + 2],
+                                       double (&Ub)[6][NDIM + 2], double (&ab)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  const double P[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
+  const double M[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+  double Ut[NV];
+  for (int v = 0; v < NV; ++v) {
+    Ut[v] = 0.0;
+    for (int j = 0; j < 6; ++j) Ut[v] += M[j] * Up[j][v];
+  }
+  RoeState<NDIM> R;
+  roe_from_conservative<NDIM>(Up[2], Up[3], gamma, R);
+  double Utb[NV], roeA[NV], roeB[NV];
+  interface_vjp_kept_ifc<NDIM, DIR>(R, Ut, alpha, gamma, Fb, Utb, roeA, roeB, ab);
   for (int j = 0; j < 6; ++j) {
-    for (int v = 0; v < NV; ++v) Ub[j][v] = M[j] * Utb[v];
-    double Fbar[NV];
-    for (int v = 0; v < NV; ++v) Fbar[v] = P[j] * Fb[v];
-    double rhob = 0.0, Eb = 0.0, pb = 0.0, ub_[NDIM], mb[NDIM];
-    for (int k = 0; k < NDIM; ++k) ub_[k] = mb[k] = 0.0;
-    if (j == 2 || j == 3) {
-      const double sx = (j == 2) ? sa : sb;
-      const double sxb = (j == 2) ? sab : sbb;
-      const double Hx = (j == 2) ? Ha : Hb;
-      const double Hxb = (j == 2) ? Hab : Hbb;
-      rhob += 0.5 / sx * sxb;
-      Eb += Hxb / rho[j];
-      pb += Hxb / rho[j];
-      rhob += -Hx / rho[j] * Hxb;
-      for (int k = 0; k < NDIM; ++k) ub_[k] += (j == 2) ? ub2[k] : ub3[k];
-    }
-    rhob += Fbar[0] * u[j][N];
-    ub_[N] += Fbar[0] * rho[j];
-    for (int k = 0; k < NDIM; ++k) {
-      mb[k] += Fbar[1 + k] * u[j][N];
-      ub_[N] += Fbar[1 + k] * Up[j][1 + k];
-    }
-    pb += Fbar[1 + N];
-    ub_[N] += Fbar[E] * (Up[j][E] + p[j]);
-    Eb += Fbar[E] * u[j][N];
-    pb += Fbar[E] * u[j][N];
-    Eb += gm1 * pb;
-    rhob += -0.5 * gm1 * q[j] * pb;
-    for (int k = 0; k < NDIM; ++k) ub_[k] += -gm1 * rho[j] * u[j][k] * pb;
-    for (int k = 0; k < NDIM; ++k) {
-      mb[k] += ub_[k] / rho[j];
-      rhob += -u[j][k] / rho[j] * ub_[k];
-    }
-    Ub[j][0] += rhob;
-    for (int k = 0; k < NDIM; ++k) Ub[j][1 + k] += mb[k];
-    Ub[j][E] += Eb;
+    double G[NV];
+    for (int v = 0; v < NV; ++v) G[v] = P[j] * Fb[v];
+    flux_vjp<NDIM, DIR>(Up[j], gamma, G, Ub[j]);
+    for (int v = 0; v < NV; ++v) Ub[j][v] += M[j] * Utb[v];
+  }
+  for (int v = 0; v < NV; ++v) {
+    Ub[2][v] += roeA[v];
+    Ub[3][v] += roeB[v];
   }
 }
 

@@ -77,9 +77,19 @@ __device__ __forceinline__ bool certify_keep(float v0, float v1, float v2, float
 // Roe-averaged eigensystem of cells i, i+1, characteristic projection, global
 // Lax-Friedrichs split with the halved speeds `alpha` (nal = -2 alpha), TENO5-LAD
 // reconstruction of f^+ (cells i-2..i+2) and f^- (mirrored, i+3..i-1) for
-// every field, back-projection.  `fl` receives the flag bytes when WITH_FLAGS.
+// every field, back-projection.  `fl` receives the flag bytes when WITH_FLAGS
+// (without flags, bits 0..2 still hold the selections used).
+// MODE kFluxFull computes the flux.  kFluxSelect only wants the selections:
+// it returns without the flux when the certified test keeps every stencil.
+// kFluxCertify stops after the certified test: fl = 7 everywhere if it keeps
+// every stencil, else fl[0][0] = kUndecided and nothing else is written.
 // ---------------------------------------------------------------------------
-template <int NDIM, int DIR, bool WITH_FLAGS>
+constexpr int kFluxFull = 0, kFluxSelect = 1, kFluxCertify = 2;
+constexpr unsigned kUndecided = 0xffu;
+
+// the certify-only instantiation ends early: its remaining code is unreachable
+#pragma nv_diag_suppress 128
+template <int NDIM, int DIR, bool WITH_FLAGS, int MODE = kFluxFull>
 __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
                                                const double* __restrict__ aux,
                                                int64_t ncell, const int64_t (&cells)[6],
@@ -209,6 +219,12 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
         keep = keep && certify_keep(vm32[5][f], vm32[4][f], vm32[3][f], vm32[2][f], vm32[1][f],
                                     fmaf(kd, mm[f], ku), S);
       }
+      if (MODE != kFluxFull && keep) {
+        // only the selections are wanted: every stencil kept
+#pragma unroll
+        for (int f = 0; f < NVAR; ++f) fl[f][0] = fl[f][1] = 7u;
+        return;
+      }
       if (keep) {
         // ---- every stencil kept at every field and side: closed form --------
         // With fixed linear weights the characteristic reconstruction is
@@ -251,6 +267,10 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
         for (int f = 0; f < NVAR; ++f) fl[f][0] = fl[f][1] = 7u;
         return;
       }
+    }
+    if (MODE == kFluxCertify) {
+      fl[0][0] = kUndecided;
+      return;
     }
 
     // Characteristic values w = L U and the split fluxes v+- = (g +- alpha w)/2
@@ -312,6 +332,7 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
     out[NVAR - 1] = eng;
   }
 }
+#pragma nv_diag_default 128
 
 // ---------------------------------------------------------------------------
 // Primitive variables of cell c from one reciprocal square root:
