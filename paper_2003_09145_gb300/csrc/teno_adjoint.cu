@@ -396,18 +396,29 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const double* __restric
   }
 }
 
-// Sum the per-block d/dalpha in a fixed order and add its effect at the
-// arg-max cells (one thread: the three kinds may share a cell).
+// Sum the per-block d/dalpha in a fixed order (one block of kAlphaThreads:
+// strided partial sums, then a tree) and add its effect at the arg-max cells
+// (one thread: the three kinds may share a cell).
+constexpr int kAlphaThreads = 256;
 template <int NDIM>
-__global__ void adj_alpha_kernel(const double* __restrict__ apart, int nblocks,
+__global__ void __launch_bounds__(kAlphaThreads) adj_alpha_kernel(const double* __restrict__ apart, int nblocks,
                                  const unsigned long long* __restrict__ argidx, int dir,
                                  const double* __restrict__ U, double* __restrict__ Ubar, int64_t ncell,
                                  double gamma) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   constexpr int NVAR = NDIM + 2;
+  __shared__ double red[kAlphaThreads][3];
   double s[3] = {0.0, 0.0, 0.0};
-  for (int b = 0; b < nblocks; ++b)
+  for (int b = threadIdx.x; b < nblocks; b += kAlphaThreads)
     for (int k = 0; k < 3; ++k) s[k] += apart[b * 3 + k];
+  for (int k = 0; k < 3; ++k) red[threadIdx.x][k] = s[k];
+  __syncthreads();
+  for (int w = kAlphaThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 3; ++k) red[threadIdx.x][k] += red[threadIdx.x + w][k];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < 3; ++k) s[k] = red[0][k];
   for (int k = 0; k < 3; ++k) {
     const unsigned long long c = argidx[dir * 3 + k];
     if (c >= (unsigned long long)ncell) continue;
@@ -459,9 +470,10 @@ int64_t nifc_of(const teno_grid* g, int d) {
 int adj_blocks(int nsm) { return nsm * 8; }
 
 struct AdjLayout {
-  // header: [0] status, [8] dt, [64] alpha bits (9 x 8), [160] arg-max (9 x 8)
+  // header: [0] status, [8] dt, [64] alpha bits (9 x 8), [136] pending-list counters of the
+  // recomputed forward stages (3 x 4), [160] arg-max (9 x 8)
   size_t status = 0, dt = 8, alpha = 64, argidx = 160;
-  size_t aux = 0, kb = 0, contrib = 0, pending = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0, total = 0;
+  size_t aux = 0, kb = 0, contrib = 0, pending = 0, list = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0, total = 0;
 };
 
 AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
@@ -479,6 +491,8 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   off += round_up(sizeof(double) * 6 * nvar * size_t(maxifc));
   L.pending = off;
   off += round_up(size_t(maxifc));
+  L.list = off;   // pending list of the recomputed forward stages
+  off += round_up(sizeof(uint32_t) * size_t(maxifc));
   L.apart = off;
   off += round_up(sizeof(double) * 3 * 2 * size_t(adj_blocks(nsm)));
   if (op == TENO_OP_RK3_ADJOINT) {
@@ -543,7 +557,7 @@ void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const d
   if (gb > int64_t(nsm) * 16) gb = int64_t(nsm) * 16;
   adj_gather_kernel<NDIM, DIR><<<unsigned(gb), 256, 0, st>>>(U, Rbar, scale, kb, contrib, pending, Ubar, G,
                                                               S.gamma);
-  adj_alpha_kernel<NDIM><<<1, 32, 0, st>>>(apart, 2 * nblk, argidx, DIR, U, Ubar, G.ncell, S.gamma);
+  adj_alpha_kernel<NDIM><<<1, kAlphaThreads, 0, st>>>(apart, 2 * nblk, argidx, DIR, U, Ubar, G.ncell, S.gamma);
 }
 
 // Ubar += scale * J(U)^T Rbar
@@ -635,10 +649,11 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double 
   // forward stages of the step (eq. 4.1-4.2) with the given dt
   set_value_kernel<<<1, 1, 0, st>>>(dtp, dt);
   if (cudaGetLastError() != cudaSuccess) return TENO_ERR_CUDA;
-  teno_status s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.contrib, U_n, R, 2, U_n,
-                                      nullptr, U1, st);
+  teno_status s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.contrib, L.list, U_n, R, 2,
+                                      U_n, nullptr, U1, st);
   if (s != TENO_OK) return s;
-  s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.contrib, U1, R, 3, U_n, U1, U2, st);
+  s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.contrib, L.list, U1, R, 3, U_n, U1, U2,
+                          st);
   if (s != TENO_OK) return s;
 
   // reverse of eq. 4.3: B2 = 2/3 Ubar' + 2/3 dt J(U2)^T Ubar';  Ubar_n = 1/3 Ubar'

@@ -49,8 +49,10 @@ int64_t nifc_of(const teno_grid* g, int d) {
 }
 
 struct Layout {
+  // header: [0] status, [8] dt, [64] LF speeds (9 x 8) then the pending-list
+  // counters (3 x 4)
   size_t status = 0, dt = 8, alpha = 64;
-  size_t aux = 0, fhat = 0, R = 0, U1 = 0, U2 = 0, total = 0;
+  size_t aux = 0, fhat = 0, list = 0, R = 0, U1 = 0, U2 = 0, total = 0;
 };
 
 Layout layout_of(const teno_grid* g, int op) {
@@ -64,6 +66,8 @@ Layout layout_of(const teno_grid* g, int op) {
   off += round_up(sizeof(double) * (g->ndim + 3) * ncell);
   L.fhat = off;
   off += round_up(sizeof(double) * nvar * size_t(maxifc));
+  L.list = off;
+  off += round_up(sizeof(uint32_t) * size_t(maxifc));
   if (op == TENO_OP_RK3) {
     L.R = off;
     off += round_up(sizeof(double) * nvar * ncell);
@@ -128,6 +132,7 @@ struct KernelTimer {
   int64_t dropped = 0;
   cudaEvent_t ev[2 * kTimerPairs];
   int kind[kTimerPairs];
+  int nlaunch[kTimerPairs];   // kernels launched inside the pair
 };
 KernelTimer g_timer;
 
@@ -139,7 +144,11 @@ struct TimerScope {
     if (g_timer.used >= kTimerPairs) { ++g_timer.dropped; return; }
     slot = g_timer.used++;
     g_timer.kind[slot] = kind;
+    g_timer.nlaunch[slot] = 1;
     cudaEventRecord(g_timer.ev[2 * slot], st);
+  }
+  void launches(int n) {
+    if (slot >= 0) g_timer.nlaunch[slot] = n;
   }
   ~TimerScope() {
     if (slot >= 0) cudaEventRecord(g_timer.ev[2 * slot + 1], st);
@@ -168,7 +177,9 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
   auto* alpha = reinterpret_cast<unsigned long long*>(ws + L.alpha);
   double* aux = reinterpret_cast<double*>(ws + L.aux);
   double* Fhat = reinterpret_cast<double*>(ws + L.fhat);
-  TENO_CUDA(cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st));
+  uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
+  unsigned* count = reinterpret_cast<unsigned*>(ws + L.alpha + teno::kPendingCountOffset);
+  TENO_CUDA(cudaMemsetAsync(alpha, 0, teno::kAlphaAndCountBytes, st));
   {
     TimerScope ts(st, TENO_KERNEL_CELL);
     TENO_CUDA(teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st));
@@ -182,7 +193,10 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
     uint8_t* fl = flags ? flags + foff : nullptr;
     {
       TimerScope ts(st, TENO_KERNEL_FLUX);
-      TENO_CUDA(teno::launch_flux(g->ndim, d, U, aux, alpha, Fhat, fl, status, G, S, nsm, st));
+      int nl = 1;
+      TENO_CUDA(teno::launch_flux(g->ndim, d, U, aux, alpha, Fhat, fl, list, count + d, status, G, S, nsm, st,
+                                  &nl));
+      ts.launches(nl);
     }
     foff += int64_t(g->ndim + 2) * 2 * nifc_of(g, d);
     const bool last = (d == g->ndim - 1);
@@ -309,7 +323,7 @@ teno_status teno_timer_end(double* ms, int64_t* launches) {
     if (cudaEventElapsedTime(&t, g_timer.ev[2 * i], g_timer.ev[2 * i + 1]) != cudaSuccess)
       return TENO_ERR_CUDA;
     ms[g_timer.kind[i]] += t;
-    launches[g_timer.kind[i]] += 1;
+    launches[g_timer.kind[i]] += g_timer.nlaunch[i];
   }
   return g_timer.dropped ? TENO_ERR_WORKSPACE : TENO_OK;
 }

@@ -72,6 +72,242 @@ __device__ __forceinline__ bool certify_keep(float v0, float v1, float v2, float
 }
 
 // ---------------------------------------------------------------------------
+// Roe state of the interface i+1/2 from the per-cell primitives of cells i
+// and i+1 (sqrt(rho), (E+p)/sqrt(rho) and the half velocities uu = u/2):
+// u~ = (sr_a u_a + sr_b u_b)/(sr_a + sr_b), H~ = (sh_a + sh_b)/(sr_a + sr_b),
+// c~^2 = (gamma-1)(H~ - |u~|^2/2), b1 = (gamma-1)/c~^2, b2 = b1 |u~|^2/2.
+// ---------------------------------------------------------------------------
+template <int NDIM>
+struct RoeIfc {
+  double u[NDIM], q2, H, cs, b1, hb1, hb2, hic, hud;
+};
+
+template <int NDIM, int DIR>
+__device__ __forceinline__ void roe_interface(double sr2, double sr3, double sh2, double sh3,
+                                              const double (&uu2)[NDIM], const double (&uu3)[NDIM],
+                                              const Scheme& S, RoeIfc<NDIM>& R, int* __restrict__ status) {
+  const double inv2 = 2.0 / (sr2 + sr3);
+  R.q2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) {
+    R.u[k] = fma(sr2, uu2[k], sr3 * uu3[k]) * inv2;
+    R.q2 = fma(R.u[k], R.u[k], R.q2);
+  }
+  R.H = (sh2 + sh3) * (0.5 * inv2);
+  const double c2 = S.gm1 * fma(-0.5, R.q2, R.H);
+  if (!(c2 > 0.0)) atomicOr(status, kStatusNonphysical);
+  const double ic = rsqrt(c2);
+  R.cs = c2 * ic;
+  R.b1 = S.gm1 * ic * ic;
+  const double b2 = 0.5 * R.b1 * R.q2;
+  R.hb1 = 0.5 * R.b1;
+  R.hb2 = 0.5 * b2;
+  R.hic = 0.5 * ic;
+  R.hud = 0.5 * R.u[DIR];
+}
+
+// ---------------------------------------------------------------------------
+// Certified FP32 test that all ten reconstructions of the interface keep
+// every stencil.  cert_point takes one stencil point (its state and half
+// u_d, p) to FP32 split characteristic values v+-[j] with the bounds of their
+// absolute evaluation; cert_keep runs certify_keep on every field and side
+// with the accumulated error bound.
+// ---------------------------------------------------------------------------
+template <int NDIM>
+struct CertIfc {
+  float uf[NDIM], hb1f, hb2f, hicf, b1f, hudf, haf[NDIM + 2];
+  float vp32[6][NDIM + 2], vm32[6][NDIM + 2], mp[NDIM + 2], mm[NDIM + 2], vmax;
+};
+
+template <int NDIM>
+__device__ __forceinline__ void cert_begin(const RoeIfc<NDIM>& R, const double (&alpha)[NDIM + 2],
+                                           CertIfc<NDIM>& C) {
+  constexpr int NVAR = NDIM + 2;
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) C.uf[k] = hi_float(R.u[k]);
+  C.hb1f = hi_float(R.hb1);
+  C.hb2f = hi_float(R.hb2);
+  C.hicf = hi_float(R.hic);
+  C.b1f = hi_float(R.b1);
+  C.hudf = hi_float(R.hud);
+#pragma unroll
+  for (int f = 0; f < NVAR; ++f) {
+    C.haf[f] = hi_float(alpha[f]);
+    C.mp[f] = C.mm[f] = 0.0f;
+  }
+  C.vmax = 0.0f;
+}
+
+template <int NDIM, int DIR>
+__device__ __forceinline__ void cert_point(int j, const double (&Uj)[NDIM + 2], double unj, double pnj,
+                                           CertIfc<NDIM>& C) {
+  constexpr int NVAR = NDIM + 2;
+  float X[NVAR], Xa[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    X[v] = hi_float(Uj[v]);
+    Xa[v] = fabsf(X[v]);
+  }
+  // projection (same form as project()) and its absolute-value evaluation
+  float Sv = -X[NVAR - 1], Sa = Xa[NVAR - 1];
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) {
+    Sv = fmaf(C.uf[k], X[1 + k], Sv);
+    Sa = fmaf(fabsf(C.uf[k]), Xa[1 + k], Sa);
+  }
+  const float A = fmaf(C.hb2f, X[0], -C.hb1f * Sv);
+  const float Aa = fmaf(fabsf(C.hb2f), Xa[0], fabsf(C.hb1f) * Sa);
+  const float B = fmaf(C.uf[DIR], X[0], -X[1 + DIR]) * C.hicf;
+  const float Ba = fmaf(fabsf(C.uf[DIR]), Xa[0], Xa[1 + DIR]) * fabsf(C.hicf);
+  float w[NVAR], wa[NVAR];
+  w[0] = A + B;
+  wa[0] = Aa + Ba;
+  w[1] = fmaf(-2.0f, A, X[0]);
+  wa[1] = fmaf(2.0f, Aa, Xa[0]);
+  {
+    int f = 2;
+#pragma unroll
+    for (int t = 0; t < NDIM; ++t) {
+      if (t == DIR) continue;
+      w[f] = fmaf(-C.uf[t], X[0], X[1 + t]);
+      wa[f] = fmaf(fabsf(C.uf[t]), Xa[0], Xa[1 + t]);
+      ++f;
+    }
+  }
+  w[NVAR - 1] = A - B;
+  wa[NVAR - 1] = Aa + Ba;
+  const float huf = hi_float(unj), hpf = hi_float(pnj);
+  const float az = hpf * (C.b1f * (huf - C.hudf));
+  const float aza = fabsf(hpf) * (fabsf(C.b1f) * (fabsf(huf) + fabsf(C.hudf)));
+  const float bz = hpf * C.hicf, bza = fabsf(hpf) * fabsf(C.hicf);
+#pragma unroll
+  for (int f = 0; f < NVAR; ++f) {
+    const float t = (f == 0) ? az - bz : (f == NVAR - 1) ? az + bz : (f == 1) ? -2.0f * az : 0.0f;
+    const float ta = (f == 0 || f == NVAR - 1) ? aza + bza : (f == 1) ? 2.0f * aza : 0.0f;
+    C.vp32[j][f] = fmaf(huf + C.haf[f], w[f], t);
+    C.vm32[j][f] = fmaf(-2.0f * C.haf[f], w[f], C.vp32[j][f]);
+    const float pa = fmaf(fabsf(huf) + C.haf[f], wa[f], ta);
+    const float ma = fmaf(2.0f * C.haf[f], wa[f], pa);
+    if (j <= 4) C.mp[f] = fmaxf(C.mp[f], pa);
+    if (j >= 1) C.mm[f] = fmaxf(C.mm[f], ma);
+    C.vmax = fmaxf(C.vmax, fmaxf(fabsf(C.vp32[j][f]), fabsf(C.vm32[j][f])));
+  }
+}
+
+template <int NDIM>
+__device__ __forceinline__ bool cert_keep(const CertIfc<NDIM>& C, const Scheme& S) {
+  constexpr int NVAR = NDIM + 2;
+  // |v32 - v| <= 8 * 2^-20 * (absolute evaluation) + 8 u max|v|: the
+  // inputs are 20-bit truncations, each FP32 operation adds 2^-24
+  const float kd = 8.0f * 0x1p-20f, ku = 8.0f * 0x1p-24f * C.vmax;
+  bool keep = true;
+#pragma unroll
+  for (int f = 0; f < NVAR; ++f) {
+    keep = keep && certify_keep(C.vp32[0][f], C.vp32[1][f], C.vp32[2][f], C.vp32[3][f], C.vp32[4][f],
+                                fmaf(kd, C.mp[f], ku), S);
+    keep = keep && certify_keep(C.vm32[5][f], C.vm32[4][f], C.vm32[3][f], C.vm32[2][f], C.vm32[1][f],
+                                fmaf(kd, C.mm[f], ku), S);
+  }
+  return keep;
+}
+
+// ---------------------------------------------------------------------------
+// Every stencil kept at every field and side: closed form.  With fixed linear
+// weights the characteristic reconstruction is
+//   F^ = R [ L sum_j P_j F_j + diag(alpha) L sum_j M_j U_j ]
+// with P = (1,-8,37,37,-8,1)/60 (central) and M = (1,-5,10,-10,5,-1)/60;
+// R L = I and alpha takes three values, so
+//   F^ = F~ + a_mid U~ + (a_0 - a_mid)(l_0.U~) r_0 + (a_E - a_mid)(l_E.U~) r_E.
+// closed_point adds point j to F~ and U~ (sums start at zero);
+// closed_out forms F^.
+// ---------------------------------------------------------------------------
+template <int NDIM, int DIR>
+__device__ __forceinline__ void closed_point(int j, const double (&Uj)[NDIM + 2], double unj, double pnj,
+                                             double (&Ft)[NDIM + 2], double (&Ut)[NDIM + 2]) {
+  constexpr int NVAR = NDIM + 2;
+  const double P2[6] = {1.0 / 30.0, -8.0 / 30.0, 37.0 / 30.0, 37.0 / 30.0, -8.0 / 30.0, 1.0 / 30.0};
+  const double Mw[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+  // F_j / 2 = (u_d/2) U_j + (p/2) (0, e_d, u_d)
+  const double cu = P2[j] * unj;
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    Ft[v] = fma(cu, Uj[v], Ft[v]);
+    Ut[v] = fma(Mw[j], Uj[v], Ut[v]);
+  }
+  Ft[1 + DIR] = fma(P2[j], pnj, Ft[1 + DIR]);
+  Ft[NVAR - 1] = fma(cu + cu, pnj, Ft[NVAR - 1]);
+}
+
+template <int NDIM, int DIR>
+__device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const double (&Ut)[NDIM + 2],
+                                           const RoeIfc<NDIM>& R, const double (&nal)[NDIM + 2],
+                                           double (&out)[NDIM + 2]) {
+  constexpr int NVAR = NDIM + 2;
+  double wt[NVAR];
+  project<NDIM, DIR>(Ut, R.u, R.hb1, R.hb2, R.hic, wt);
+  const double amid = -nal[1];
+  const double g0 = (nal[1] - nal[0]) * wt[0];
+  const double gE = (nal[1] - nal[NVAR - 1]) * wt[NVAR - 1];
+  const double gs = g0 + gE, gd = gE - g0;
+  out[0] = fma(amid, Ut[0], Ft[0]) + gs;
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) {
+    double o = fma(R.u[k], gs, fma(amid, Ut[1 + k], Ft[1 + k]));
+    if (k == DIR) o = fma(R.cs, gd, o);
+    out[1 + k] = o;
+  }
+  out[NVAR - 1] = fma(R.H, gs, fma(R.u[DIR] * R.cs, gd, fma(amid, Ut[NVAR - 1], Ft[NVAR - 1])));
+}
+
+// ---------------------------------------------------------------------------
+// The certified closed form alone, one stencil point at a time (each
+// point's state is dead once it has entered F~, U~ and the FP32 test, which
+// keeps the register footprint small).  Returns false, with `out`
+// unwritten, when the test does not keep every stencil; otherwise `out`
+// equals interface_flux's.
+// ---------------------------------------------------------------------------
+template <int NDIM, int DIR>
+__device__ __forceinline__ bool interface_flux_closed(const double* __restrict__ U,
+                                                      const double* __restrict__ aux, int64_t ncell,
+                                                      const int64_t (&cells)[6],
+                                                      const double (&alpha)[NDIM + 2],
+                                                      const double (&nal)[NDIM + 2], const Scheme& S,
+                                                      double (&out)[NDIM + 2], int* __restrict__ status) {
+  constexpr int NVAR = NDIM + 2;
+  if (S.keep_idx < 0) return false;
+  RoeIfc<NDIM> R;
+  {
+    double uu2[NDIM], uu3[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+      uu2[k] = aux[k * ncell + cells[2]];
+      uu3[k] = aux[k * ncell + cells[3]];
+    }
+    roe_interface<NDIM, DIR>(aux[(NDIM + 1) * ncell + cells[2]], aux[(NDIM + 1) * ncell + cells[3]],
+                             aux[(NDIM + 2) * ncell + cells[2]], aux[(NDIM + 2) * ncell + cells[3]], uu2, uu3,
+                             S, R, status);
+  }
+  CertIfc<NDIM> C;
+  cert_begin<NDIM>(R, alpha, C);
+  double Ft[NVAR], Ut[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) Ft[v] = Ut[v] = 0.0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int64_t c = cells[j];
+    double Uj[NVAR];
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) Uj[v] = U[v * ncell + c];
+    const double unj = aux[DIR * ncell + c], pnj = aux[NDIM * ncell + c];
+    closed_point<NDIM, DIR>(j, Uj, unj, pnj, Ft, Ut);
+    cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
+  }
+  if (!cert_keep<NDIM>(C, S)) return false;
+  closed_out<NDIM, DIR>(Ft, Ut, R, nal, out);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Interface flux F^_{i+1/2} in direction DIR from the six cells i-2..i+3
 // (`cells`, linear indices into arrays of `ncell` entries per variable):
 // Roe-averaged eigensystem of cells i, i+1, characteristic projection, global
@@ -83,8 +319,11 @@ __device__ __forceinline__ bool certify_keep(float v0, float v1, float v2, float
 // it returns without the flux when the certified test keeps every stencil.
 // kFluxCertify stops after the certified test: fl = 7 everywhere if it keeps
 // every stencil, else fl[0][0] = kUndecided and nothing else is written.
+// kFluxChar skips the certified test and takes the characteristic path (for
+// interfaces the test has already left undecided: the flux equals
+// kFluxFull's).
 // ---------------------------------------------------------------------------
-constexpr int kFluxFull = 0, kFluxSelect = 1, kFluxCertify = 2;
+constexpr int kFluxFull = 0, kFluxSelect = 1, kFluxCertify = 2, kFluxChar = 4;
 constexpr unsigned kUndecided = 0xffu;
 
 // the certify-only instantiation ends early: its remaining code is unreachable
@@ -123,146 +362,31 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
         }
       }
     }
-    // Roe average of cells i and i+1 (uu2, uu3 hold half velocities)
-    const double inv2 = 2.0 / (sr2 + sr3);
-    double u[NDIM];
-    double q2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < NDIM; ++k) {
-      u[k] = fma(sr2, uu2[k], sr3 * uu3[k]) * inv2;
-      q2 = fma(u[k], u[k], q2);
-    }
-    const double H = (sh2 + sh3) * (0.5 * inv2);
-    const double c2 = S.gm1 * fma(-0.5, q2, H);
-    if (!(c2 > 0.0)) atomicOr(status, kStatusNonphysical);
-    const double ic = rsqrt(c2);
-    const double cs = c2 * ic;
-    const double b1 = S.gm1 * ic * ic;
-    const double b2 = 0.5 * b1 * q2;
-    const double hb1 = 0.5 * b1, hb2 = 0.5 * b2, hic = 0.5 * ic;
-    const double hud = 0.5 * u[DIR];
+    RoeIfc<NDIM> R;
+    roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, uu2, uu3, S, R, status);
+    const double (&u)[NDIM] = R.u;
+    const double q2 = R.q2, H = R.H, cs = R.cs, b1 = R.b1;
+    const double hb1 = R.hb1, hb2 = R.hb2, hic = R.hic, hud = R.hud;
 
-    if (!WITH_FLAGS && S.keep_idx >= 0) {
-      // ---- certification in FP32 (split characteristic values and bounds) ----
-      float uf[NDIM];
+    if (!WITH_FLAGS && MODE != kFluxChar && S.keep_idx >= 0) {
+      CertIfc<NDIM> C;
+      cert_begin<NDIM>(R, alpha, C);
 #pragma unroll
-      for (int k = 0; k < NDIM; ++k) uf[k] = hi_float(u[k]);
-      const float hb1f = hi_float(hb1), hb2f = hi_float(hb2), hicf = hi_float(hic);
-      const float b1f = hi_float(b1), hudf = hi_float(hud);
-      float haf[NVAR];
-#pragma unroll
-      for (int f = 0; f < NVAR; ++f) haf[f] = hi_float(alpha[f]);
-      float vp32[6][NVAR], vm32[6][NVAR], mp[NVAR], mm[NVAR], vmax = 0.0f;
-#pragma unroll
-      for (int f = 0; f < NVAR; ++f) mp[f] = mm[f] = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        float X[NVAR], Xa[NVAR];
-#pragma unroll
-        for (int v = 0; v < NVAR; ++v) {
-          X[v] = hi_float(Ux[j][v]);
-          Xa[v] = fabsf(X[v]);
-        }
-        // projection (same form as project()) and its absolute-value evaluation
-        float Sv = -X[NVAR - 1], Sa = Xa[NVAR - 1];
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-          Sv = fmaf(uf[k], X[1 + k], Sv);
-          Sa = fmaf(fabsf(uf[k]), Xa[1 + k], Sa);
-        }
-        const float A = fmaf(hb2f, X[0], -hb1f * Sv);
-        const float Aa = fmaf(fabsf(hb2f), Xa[0], fabsf(hb1f) * Sa);
-        const float B = fmaf(uf[DIR], X[0], -X[1 + DIR]) * hicf;
-        const float Ba = fmaf(fabsf(uf[DIR]), Xa[0], Xa[1 + DIR]) * fabsf(hicf);
-        float w[NVAR], wa[NVAR];
-        w[0] = A + B;
-        wa[0] = Aa + Ba;
-        w[1] = fmaf(-2.0f, A, X[0]);
-        wa[1] = fmaf(2.0f, Aa, Xa[0]);
-        {
-          int f = 2;
-#pragma unroll
-          for (int t = 0; t < NDIM; ++t) {
-            if (t == DIR) continue;
-            w[f] = fmaf(-uf[t], X[0], X[1 + t]);
-            wa[f] = fmaf(fabsf(uf[t]), Xa[0], Xa[1 + t]);
-            ++f;
-          }
-        }
-        w[NVAR - 1] = A - B;
-        wa[NVAR - 1] = Aa + Ba;
-        const float huf = hi_float(un[j]), hpf = hi_float(pn[j]);
-        const float az = hpf * (b1f * (huf - hudf));
-        const float aza = fabsf(hpf) * (fabsf(b1f) * (fabsf(huf) + fabsf(hudf)));
-        const float bz = hpf * hicf, bza = fabsf(hpf) * fabsf(hicf);
-#pragma unroll
-        for (int f = 0; f < NVAR; ++f) {
-          const float t = (f == 0) ? az - bz : (f == NVAR - 1) ? az + bz : (f == 1) ? -2.0f * az : 0.0f;
-          const float ta = (f == 0 || f == NVAR - 1) ? aza + bza : (f == 1) ? 2.0f * aza : 0.0f;
-          vp32[j][f] = fmaf(huf + haf[f], w[f], t);
-          vm32[j][f] = fmaf(-2.0f * haf[f], w[f], vp32[j][f]);
-          const float pa = fmaf(fabsf(huf) + haf[f], wa[f], ta);
-          const float ma = fmaf(2.0f * haf[f], wa[f], pa);
-          if (j <= 4) mp[f] = fmaxf(mp[f], pa);
-          if (j >= 1) mm[f] = fmaxf(mm[f], ma);
-          vmax = fmaxf(vmax, fmaxf(fabsf(vp32[j][f]), fabsf(vm32[j][f])));
-        }
-      }
-      // |v32 - v| <= 8 * 2^-20 * (absolute evaluation) + 8 u max|v|: the
-      // inputs are 20-bit truncations, each FP32 operation adds 2^-24
-      const float kd = 8.0f * 0x1p-20f, ku = 8.0f * 0x1p-24f * vmax;
-      bool keep = true;
-#pragma unroll
-      for (int f = 0; f < NVAR; ++f) {
-        keep = keep && certify_keep(vp32[0][f], vp32[1][f], vp32[2][f], vp32[3][f], vp32[4][f],
-                                    fmaf(kd, mp[f], ku), S);
-        keep = keep && certify_keep(vm32[5][f], vm32[4][f], vm32[3][f], vm32[2][f], vm32[1][f],
-                                    fmaf(kd, mm[f], ku), S);
-      }
-      if (MODE != kFluxFull && keep) {
+      for (int j = 0; j < 6; ++j) cert_point<NDIM, DIR>(j, Ux[j], un[j], pn[j], C);
+      const bool keep = cert_keep<NDIM>(C, S);
+      if ((MODE == kFluxSelect || MODE == kFluxCertify) && keep) {
         // only the selections are wanted: every stencil kept
 #pragma unroll
         for (int f = 0; f < NVAR; ++f) fl[f][0] = fl[f][1] = 7u;
         return;
       }
       if (keep) {
-        // ---- every stencil kept at every field and side: closed form --------
-        // With fixed linear weights the characteristic reconstruction is
-        // F^ = R [ L sum_j P_j F_j + diag(alpha) L sum_j M_j U_j ] with
-        // P = (1,-8,37,37,-8,1)/60 (central) and M = (1,-5,10,-10,5,-1)/60;
-        // R L = I and alpha takes three values, so
-        // F^ = F~ + a_mid U~ + (a_0 - a_mid)(l_0.U~) r_0 + (a_E - a_mid)(l_E.U~) r_E.
-        const double P2[6] = {1.0 / 30.0, -8.0 / 30.0, 37.0 / 30.0, 37.0 / 30.0, -8.0 / 30.0, 1.0 / 30.0};
-        const double Mw[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
         double Ft[NVAR], Ut[NVAR];
 #pragma unroll
         for (int v = 0; v < NVAR; ++v) Ft[v] = Ut[v] = 0.0;
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          // F_j / 2 = (u_d/2) U_j + (p/2) (0, e_d, u_d)
-          const double cu = P2[j] * un[j];
-#pragma unroll
-          for (int v = 0; v < NVAR; ++v) {
-            Ft[v] = fma(cu, Ux[j][v], Ft[v]);
-            Ut[v] = fma(Mw[j], Ux[j][v], Ut[v]);
-          }
-          Ft[1 + DIR] = fma(P2[j], pn[j], Ft[1 + DIR]);
-          Ft[NVAR - 1] = fma(cu + cu, pn[j], Ft[NVAR - 1]);
-        }
-        double wt[NVAR];
-        project<NDIM, DIR>(Ut, u, hb1, hb2, hic, wt);
-        const double amid = -nal[1];
-        const double g0 = (nal[1] - nal[0]) * wt[0];
-        const double gE = (nal[1] - nal[NVAR - 1]) * wt[NVAR - 1];
-        const double gs = g0 + gE, gd = gE - g0;
-        out[0] = fma(amid, Ut[0], Ft[0]) + gs;
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-          double o = fma(u[k], gs, fma(amid, Ut[1 + k], Ft[1 + k]));
-          if (k == DIR) o = fma(cs, gd, o);
-          out[1 + k] = o;
-        }
-        out[NVAR - 1] = fma(H, gs, fma(u[DIR] * cs, gd, fma(amid, Ut[NVAR - 1], Ft[NVAR - 1])));
+        for (int j = 0; j < 6; ++j) closed_point<NDIM, DIR>(j, Ux[j], un[j], pn[j], Ft, Ut);
+        closed_out<NDIM, DIR>(Ft, Ut, R, nal, out);
 #pragma unroll
         for (int f = 0; f < NVAR; ++f) fl[f][0] = fl[f][1] = 7u;
         return;

@@ -147,6 +147,108 @@ __global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// The same fluxes in two passes (no flags).  flux_closed_kernel evaluates the
+// certified closed form -- every interface whose FP32 test keeps all ten
+// stencils -- and appends the others to `list` (one atomic per warp);
+// flux_pending_kernel then takes the listed interfaces through the
+// characteristic path.  Each interface gets the arithmetic of the one-pass
+// kernel, so Fhat is identical; the closed-form pass stays small (registers,
+// instruction cache) and its warps do not diverge into the rare slow path.
+// ---------------------------------------------------------------------------
+#ifndef TENO_CLOSED_MINBLOCKS
+#define TENO_CLOSED_MINBLOCKS 4
+#endif
+
+template <int NDIM, int DIR>
+__device__ __forceinline__ void interface_cells(int64_t q, const Grid& G, int64_t (&cells)[6]) {
+  const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
+  const int64_t stride_d = (DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1]);
+  const int64_t i0 = q % m0;
+  const int64_t r = q / m0;
+  const int64_t i1 = r % m1;
+  const int64_t i2 = r / m1;
+  const int64_t id = (DIR == 0) ? i0 : (DIR == 1 ? i1 : i2);
+  const int64_t base = (DIR == 0) ? (i2 * G.n[1] + i1) * G.n[0]
+                     : (DIR == 1) ? i2 * G.n[1] * G.n[0] + i0
+                                  : i1 * G.n[0] + i0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) cells[j] = base + ghost(id - 3 + j, G.n[DIR], G.bc[DIR]) * stride_d;
+}
+
+template <int NDIM, int DIR>
+__device__ __forceinline__ void half_speeds(const unsigned long long* __restrict__ alpha_bits,
+                                            double (&alpha)[NDIM + 2], double (&nal)[NDIM + 2]) {
+  constexpr int NVAR = NDIM + 2;
+  const double am = __longlong_as_double((long long)alpha_bits[DIR * 3 + 0]);
+  const double a0 = __longlong_as_double((long long)alpha_bits[DIR * 3 + 1]);
+  const double ap = __longlong_as_double((long long)alpha_bits[DIR * 3 + 2]);
+  alpha[0] = 0.5 * am;
+#pragma unroll
+  for (int f = 1; f < NVAR - 1; ++f) alpha[f] = 0.5 * a0;
+  alpha[NVAR - 1] = 0.5 * ap;
+#pragma unroll
+  for (int f = 0; f < NVAR; ++f) nal[f] = -2.0 * alpha[f];
+}
+
+template <int NDIM, int DIR>
+__global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel(
+    const double* __restrict__ U, const double* __restrict__ aux,
+    const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
+    uint32_t* __restrict__ list, unsigned* __restrict__ count, int* __restrict__ status, Grid G,
+    Scheme S) {
+  constexpr int NVAR = NDIM + 2;
+  const int64_t nifc = (G.n[0] + (DIR == 0)) * (G.n[1] + (DIR == 1)) * (G.n[2] + (DIR == 2));
+  double alpha[NVAR], nal[NVAR];
+  half_speeds<NDIM, DIR>(alpha_bits, alpha, nal);
+  const unsigned lane = threadIdx.x & 31u;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nifc;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t cells[6];
+    interface_cells<NDIM, DIR>(q, G, cells);
+    double out[NVAR];
+    const bool done = interface_flux_closed<NDIM, DIR>(U, aux, G.ncell, cells, alpha, nal, S, out, status);
+    if (done) {
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
+    }
+    // append the undecided interfaces of the lanes converged here
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, !done);
+    if (m) {
+      const unsigned leader = __ffs(act) - 1;
+      unsigned at = 0;
+      if (lane == leader) at = atomicAdd(count, __popc(m));
+      at = __shfl_sync(act, at, leader);
+      if (!done) list[at + __popc(m & ((1u << lane) - 1u))] = static_cast<uint32_t>(q);
+    }
+  }
+}
+
+template <int NDIM, int DIR>
+__global__ void __launch_bounds__(128) flux_pending_kernel(
+    const double* __restrict__ U, const double* __restrict__ aux,
+    const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
+    const uint32_t* __restrict__ list, const unsigned* __restrict__ count, int* __restrict__ status,
+    Grid G, Scheme S) {
+  constexpr int NVAR = NDIM + 2;
+  const int64_t nifc = (G.n[0] + (DIR == 0)) * (G.n[1] + (DIR == 1)) * (G.n[2] + (DIR == 2));
+  const int64_t n = *count;
+  if (blockIdx.x * (int64_t)blockDim.x >= n) return;
+  double alpha[NVAR], nal[NVAR];
+  half_speeds<NDIM, DIR>(alpha_bits, alpha, nal);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = list[i];
+    int64_t cells[6];
+    interface_cells<NDIM, DIR>(q, G, cells);
+    double out[NVAR];
+    unsigned fl[NVAR][2];
+    interface_flux<NDIM, DIR, false, kFluxChar>(U, aux, G.ncell, cells, alpha, nal, S, out, fl, status);
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Conservative difference (eq. 2.2) and SSP-RK3 stage update (eq. 4.1-4.3).
 // mode: 0 R = d; 1 R += d; 2 U1 = Un + dt (R + d); 3 U2 = 3/4 Un + 1/4 U1 +
 // 1/4 dt (R + d); 4 Un <- 1/3 Un + 2/3 U2 + 2/3 dt (R + d).  `acc` selects
@@ -304,33 +406,45 @@ cudaError_t launch_cell(int ndim, const double* U, double* aux,
 }
 
 template <int NDIM, int DIR>
-static void flux_launch(int blocks, int threads, cudaStream_t st, const double* U,
-                        const double* aux, const unsigned long long* alpha,
-                        double* Fhat, uint8_t* flags, int* status, const Grid& G,
-                        const Scheme& S) {
-  if (flags)
+static int flux_launch(int blocks, int threads, int pblocks, cudaStream_t st, const double* U,
+                       const double* aux, const unsigned long long* alpha, double* Fhat, uint8_t* flags,
+                       uint32_t* list, unsigned* count, int* status, const Grid& G, const Scheme& S) {
+  if (flags) {
     flux_kernel<NDIM, DIR, true><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
-  else
+    return 1;
+  }
+  if (!list) {
     flux_kernel<NDIM, DIR, false><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
+    return 1;
+  }
+  flux_closed_kernel<NDIM, DIR><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
+  flux_pending_kernel<NDIM, DIR><<<pblocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
+  return 2;
 }
 
 cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux,
                         const unsigned long long* alpha, double* Fhat,
-                        uint8_t* flags, int* status, const Grid& G,
-                        const Scheme& S, int nsm, cudaStream_t st) {
+                        uint8_t* flags, uint32_t* list, unsigned* count, int* status,
+                        const Grid& G, const Scheme& S, int nsm, cudaStream_t st,
+                        int* launches) {
   int64_t nifc = 1;
   for (int k = 0; k < 3; ++k) nifc *= G.n[k] + (k == dir ? 1 : 0);
+  if (nifc > int64_t(UINT32_MAX)) list = nullptr;   // list entries are 32-bit
+  if (!count) list = nullptr;
   const int threads = 128;
   const int blocks = blocks_for(nifc, threads, nsm * 64);
-  if (ndim == 1) flux_launch<1, 0>(blocks, threads, st, U, aux, alpha, Fhat, flags, status, G, S);
+  const int pblocks = blocks_for(nifc, threads, nsm * 16);
+  int n = 0;
+  if (ndim == 1) n = flux_launch<1, 0>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
   else if (ndim == 2) {
-    if (dir == 0) flux_launch<2, 0>(blocks, threads, st, U, aux, alpha, Fhat, flags, status, G, S);
-    else flux_launch<2, 1>(blocks, threads, st, U, aux, alpha, Fhat, flags, status, G, S);
+    if (dir == 0) n = flux_launch<2, 0>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
+    else n = flux_launch<2, 1>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
   } else {
-    if (dir == 0) flux_launch<3, 0>(blocks, threads, st, U, aux, alpha, Fhat, flags, status, G, S);
-    else if (dir == 1) flux_launch<3, 1>(blocks, threads, st, U, aux, alpha, Fhat, flags, status, G, S);
-    else flux_launch<3, 2>(blocks, threads, st, U, aux, alpha, Fhat, flags, status, G, S);
+    if (dir == 0) n = flux_launch<3, 0>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
+    else if (dir == 1) n = flux_launch<3, 1>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
+    else n = flux_launch<3, 2>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
   }
+  if (launches) *launches = n;
   return cudaGetLastError();
 }
 
@@ -371,9 +485,9 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 }
 
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
-                          size_t alpha_off, size_t aux_off, size_t fhat_off, const double* U,
-                          double* R, int mode, const double* Un, const double* Uk, double* Uout,
-                          cudaStream_t st) {
+                          size_t alpha_off, size_t aux_off, size_t fhat_off, size_t list_off,
+                          const double* U, double* R, int mode, const double* Un, const double* Uk,
+                          double* Uout, cudaStream_t st) {
   Grid G;
   for (int k = 0; k < 3; ++k) {
     G.n[k] = g->n[k];
@@ -392,11 +506,14 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
   auto* alpha = reinterpret_cast<unsigned long long*>(ws + alpha_off);
   double* aux = reinterpret_cast<double*>(ws + aux_off);
   double* Fhat = reinterpret_cast<double*>(ws + fhat_off);
-  if (cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
+  uint32_t* list = list_off ? reinterpret_cast<uint32_t*>(ws + list_off) : nullptr;
+  unsigned* count = reinterpret_cast<unsigned*>(ws + alpha_off + kPendingCountOffset);
+  if (cudaMemsetAsync(alpha, 0, kAlphaAndCountBytes, st) != cudaSuccess) return TENO_ERR_CUDA;
   if (launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
     return TENO_ERR_CUDA;
   for (int d = 0; d < g->ndim; ++d) {
-    if (launch_flux(g->ndim, d, U, aux, alpha, Fhat, nullptr, status, G, S, nsm, st) != cudaSuccess)
+    if (launch_flux(g->ndim, d, U, aux, alpha, Fhat, nullptr, list, count + d, status, G, S, nsm, st,
+                    nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
     const bool last = (d == g->ndim - 1);
     const int m = last ? mode : (d == 0 ? 0 : 1);

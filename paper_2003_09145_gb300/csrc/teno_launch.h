@@ -17,10 +17,22 @@ cudaError_t launch_cell(int ndim, const double* U, double* aux,
                         unsigned long long* alpha, int* status, int64_t ncell,
                         double gamma, int nsm, cudaStream_t st);
 
+// The interface fluxes of direction `dir` into Fhat.  With `flags`, or
+// without a pending list, one pass; with `list` (room for one 32-bit entry
+// per interface) and its counter `count` (zero on entry), the closed-form
+// pass and the pass over the interfaces it leaves pending.  `launches`
+// (optional) receives the number of kernels launched.
 cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux,
                         const unsigned long long* alpha, double* Fhat,
-                        uint8_t* flags, int* status, const Grid& G,
-                        const Scheme& S, int nsm, cudaStream_t st);
+                        uint8_t* flags, uint32_t* list, unsigned* count, int* status,
+                        const Grid& G, const Scheme& S, int nsm, cudaStream_t st,
+                        int* launches);
+
+// The workspace header holds the nine LF speeds (as bit patterns) and, right
+// after them, one pending-list counter per direction; one memset of
+// kAlphaAndCountBytes from the speeds clears both.
+constexpr size_t kPendingCountOffset = 9 * sizeof(unsigned long long);
+constexpr size_t kAlphaAndCountBytes = kPendingCountOffset + 3 * sizeof(unsigned);
 
 cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
                         const double* Un, const double* Uk, double* Uout,
@@ -33,12 +45,13 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 
 // One right-hand-side evaluation of U fused with the SSP-RK3 stage `mode`
 // (2, 3 or 4; see diff_kernel) into Uout, with dt read from the workspace
-// word at dt_off.  `ws` offsets locate the status word, the LF speeds, the
-// per-cell primitives and the interface-flux buffer; R holds the partial sums
-// of the multi-dimensional difference.
+// word at dt_off.  `ws` offsets locate the status word, the LF speeds (and
+// the pending counters after them), the per-cell primitives, the
+// interface-flux buffer and the pending list (0: none, one-pass fluxes); R
+// holds the partial sums of the multi-dimensional difference.
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
-                          size_t alpha_off, size_t aux_off, size_t fhat_off, const double* U,
-                          double* R, int mode, const double* Un, const double* Uk, double* Uout,
-                          cudaStream_t st);
+                          size_t alpha_off, size_t aux_off, size_t fhat_off, size_t list_off,
+                          const double* U, double* R, int mode, const double* Un, const double* Uk,
+                          double* Uout, cudaStream_t st);
 
 }  // namespace teno
