@@ -3,8 +3,8 @@
 Rounding-order differences can flip a selector that sits on a rounding
 boundary.  Such flips are counted, not failed, when (i) delta_k differs and the
 oracle's chi_k lies within 1e-10 relative of its C_T, or (ii) m differs and the
-oracle's 6 theta lies within 1e-12 of an integer (delta flips that only follow
-from that m flip are allowed as well).  The right-hand side is then compared
+oracle's K theta (K = B_u - B_l, 6 by default) lies within 1e-12 of an integer
+(delta flips that only follow from that m flip are allowed as well).  The right-hand side is then compared
 with the oracle evaluated with the GPU's selections forced.
 """
 from __future__ import annotations
@@ -54,8 +54,10 @@ def classify_flags(U, n, dx, bc, gpu_flags, oracle_flags, oracle, params=None,
         dg = oracle.euler_interface_diag(U, n, dx, bc, d, ifc, s, side, params)
         g, o = int(gpu_flags[flat]), int(oracle_flags[flat])
         if (g >> 3) != (o >> 3):
-            six_theta = 6.0 * dg["theta"]
-            if abs(six_theta - round(six_theta)) <= 1e-12 * max(1.0, six_theta):
+            # m = B_l + floor(theta (B_u - B_l)) (eq. 3.2): a flip needs K theta on an integer
+            K = (params.b_u - params.b_l) if params is not None else 6
+            k_theta = K * dg["theta"]
+            if abs(k_theta - round(k_theta)) <= 1e-12 * max(1.0, k_theta):
                 rep.allowed_m += 1
                 continue
             rep.unexplained.append((d, s, side, ifc, g, o, dg))

@@ -187,6 +187,29 @@ def test_flag_free_path(api, oracle, case):
     assert err <= RHS_RTOL, err
 
 
+@pytest.mark.parametrize("case", ["rand2d", "smooth3d"])
+def test_every_interface_pending(api, oracle, case):
+    """A scheme without a keep-all magnitude (B_l = 1, B_u = 2, H = 1e16:
+    3 (1 + max chi~)^6 C_T >= 1 at m = 2) sends every interface of the
+    flag-free path through the pending list: the list fills completely and the
+    result still matches the flag path and the oracle."""
+    sch = dict(H=1e16, b_l=1, b_u=2)
+    P = {"rand2d": lambda: inputs.Problem("r2", inputs.random_discontinuous_state(2, (33, 20), seed=15),
+                                          (33, 20), (0.02, 0.03), (1, 0), 0.0),
+         "smooth3d": lambda: inputs.Problem("s3", inputs.random_smooth_state(3, (17, 12, 9), seed=17, amp=0.03),
+                                            (17, 12, 9), (0.1, 0.1, 0.1), (0, 1, 0), 0.0)}[case]()
+    grid = api.EulerGrid(P.n, P.dx, P.bc, api.Scheme(**sch))
+    U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
+    a, fl = api.rhs(grid, U, want_flags=True)
+    b = api.rhs(grid, U, want_flags=False)
+    torch.cuda.synchronize()
+    a, fl, b = a.cpu().numpy(), fl.cpu().numpy(), b.cpu().numpy()
+    assert rel_max_err(b, a, flux_scale(P.U0, P.n, P.dx)) <= 1e-13
+    err, rep = compare_rhs(P.U0, P.n, P.dx, P.bc, b, fl, oracle, oracle.Params(**sch))
+    assert not rep.unexplained
+    assert err <= RHS_RTOL, err
+
+
 def test_cuda_graph_replay_matches_eager(api):
     """Steps captured in a CUDA graph give the same state as eager steps."""
     P = inputs.shu_osher(1024)
