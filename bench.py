@@ -37,12 +37,14 @@ FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
 # divide / rsqrt = 1).
 # * Every stencil kept at all ten reconstructions (certified in FP32): the
 #   closed form F~ + a_mid U~ + acoustic corrections -- Roe 34, per point
-#   26 (F~ and U~ sums), projection of U~ 20, corrections and output 30: 240.
+#   20 (the P-weighted sum of the cell pass's F/2 and the M-weighted sum of
+#   U), projection of U~ 20, corrections and output 30: 204.  (Forming
+#   F_d/2 costs 9 flops per cell and direction in the cell pass.)
 # * Otherwise the characteristic path: Roe 34, projection 6 x 20, split 6 x 28,
 #   sum 5, back-projection 21 (= 348), plus per scalar reconstruction 9 when
 #   its own FP32 pre-test keeps every stencil, else 38 for the binary64
 #   indicators, m and weights plus 21 for the cutoff test.
-ALG_CLOSED_3D = 240
+ALG_CLOSED_3D = 204
 ALG_FIXED_3D = 348
 ALG_PER_RECON_KEEP = 9
 ALG_PER_RECON = 38

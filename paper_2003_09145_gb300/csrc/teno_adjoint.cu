@@ -473,7 +473,7 @@ struct AdjLayout {
   // header: [0] status, [8] dt, [64] alpha bits (9 x 8), [136] pending-list counters of the
   // recomputed forward stages (3 x 4), [160] arg-max (9 x 8)
   size_t status = 0, dt = 8, alpha = 64, argidx = 160;
-  size_t aux = 0, kb = 0, contrib = 0, pending = 0, list = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0, total = 0;
+  size_t aux = 0, fh = 0, kb = 0, contrib = 0, pending = 0, list = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0, total = 0;
 };
 
 AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
@@ -496,6 +496,9 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   L.apart = off;
   off += round_up(sizeof(double) * 3 * 2 * size_t(adj_blocks(nsm)));
   if (op == TENO_OP_RK3_ADJOINT) {
+    // half fluxes of the recomputed forward stages (two-pass fluxes)
+    L.fh = off;
+    off += round_up(sizeof(double) * g->ndim * nvar * ncell);
     // forward recomputation (R, U1, U2) and the stage adjoints (B1, B2)
     L.R = off;
     off += round_up(sizeof(double) * nvar * ncell);
@@ -577,7 +580,7 @@ teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, c
   auto* pending = reinterpret_cast<unsigned char*>(ws + L.pending);
   if (cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
   if (cudaMemsetAsync(argidx, 0xff, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
-  if (teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
+  if (teno::launch_cell(g->ndim, U, aux, nullptr, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
     return TENO_ERR_CUDA;
   int64_t cb = (G.ncell + 255) / 256;
   if (cb > int64_t(nsm) * 16) cb = int64_t(nsm) * 16;
@@ -649,11 +652,11 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double 
   // forward stages of the step (eq. 4.1-4.2) with the given dt
   set_value_kernel<<<1, 1, 0, st>>>(dtp, dt);
   if (cudaGetLastError() != cudaSuccess) return TENO_ERR_CUDA;
-  teno_status s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.contrib, L.list, U_n, R, 2,
-                                      U_n, nullptr, U1, st);
+  teno_status s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.fh, L.contrib, L.list, U_n, R,
+                                      2, U_n, nullptr, U1, st);
   if (s != TENO_OK) return s;
-  s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.contrib, L.list, U1, R, 3, U_n, U1, U2,
-                          st);
+  s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.fh, L.contrib, L.list, U1, R, 3, U_n, U1,
+                          U2, st);
   if (s != TENO_OK) return s;
 
   // reverse of eq. 4.3: B2 = 2/3 Ubar' + 2/3 dt J(U2)^T Ubar';  Ubar_n = 1/3 Ubar'

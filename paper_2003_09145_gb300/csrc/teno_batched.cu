@@ -6,12 +6,14 @@
 // array U[3][sum N].  A persistent grid of CTAs pulls whole problems from a
 // device work queue (largest first, the order prepared by
 // teno_batch_prepare).  For its problem a CTA
-//   (A) evaluates the primitive variables and the problem's LF speeds
-//       (block reduction) and, in stage 1, the CFL step and the new time;
+//   (A) evaluates the primitive variables, the half physical fluxes F/2 and
+//       the problem's LF speeds (block reduction) and, in stage 1, the CFL
+//       step and the new time;
 //   (B) sweeps the problem in tiles of BLOCK - 1 cells: one thread per
-//       interface flux (the same device code as teno_rhs), the fluxes of a
-//       tile in shared memory, then the conservative difference fused with
-//       the stage update.
+//       interface flux (the same device code as teno_rhs: the certified
+//       closed form, else the characteristic path), the fluxes of a tile in
+//       shared memory, then the conservative difference fused with the
+//       stage update.
 // No grid-wide synchronisation is needed: every dependency is inside a
 // problem, and a problem never spans two CTAs.  The arithmetic is exactly
 // that of teno_rk3_step on each problem alone, so results agree bit for bit.
@@ -39,6 +41,7 @@ struct BatchArgs {
   const double* Uk;    // U1 (stage 2) or U2 (stage 3)
   double* Uout;        // U1, U2 or U^{n+1}
   double* aux;         // [4][ncell]
+  double* fh;          // [3][ncell]: F/2 of every cell (eq. 4.7)
   const int64_t* offsets;
   const double* dx;
   double* t;
@@ -79,7 +82,13 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
     bool bad = false;
     for (int64_t i = tid; i < n; i += BLOCK) {
       double u[1], cs;
-      if (!teno::cell_primitives<1>(A.Uin, A.ncell, off + i, A.gamma, A.aux, u, cs)) bad = true;
+      const int64_t c = off + i;
+      if (!teno::cell_primitives<1>(A.Uin, A.ncell, c, A.gamma, A.aux, u, cs)) bad = true;
+      const double Uc[3] = {A.Uin[c], A.Uin[A.ncell + c], A.Uin[2 * A.ncell + c]};
+      double Fh[3];
+      teno::cell_flux_half<1, 0>(Uc, A.aux[c], A.aux[A.ncell + c], Fh);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) A.fh[v * A.ncell + c] = Fh[v];
       l0 = fmax(l0, fabs(__dsub_rn(u[0], cs)));
       l1 = fmax(l1, fabs(u[0]));
       l2 = fmax(l2, fabs(__dadd_rn(u[0], cs)));
@@ -142,9 +151,14 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
         int64_t cells[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) cells[j] = off + teno::ghost(face - 3 + j, n, A.bc);
+        // the certified closed form, else the characteristic path (the grid
+        // path's two passes, in one thread)
         double out[3];
-        unsigned fl[3][2];
-        teno::interface_flux<1, 0, false>(A.Uin, A.aux, A.ncell, cells, alpha, nal, S, out, fl, A.status);
+        if (!teno::interface_flux_closed<1, 0>(A.Uin, A.aux, A.fh, A.ncell, cells, alpha, nal, S, out, A.status)) {
+          unsigned fl[3][2];
+          teno::interface_flux<1, 0, false, teno::kFluxChar>(A.Uin, A.aux, A.ncell, cells, alpha, nal, S, out, fl,
+                                                             A.status);
+        }
         s_F[tid][0] = out[0];
         s_F[tid][1] = out[1];
         s_F[tid][2] = out[2];
@@ -168,7 +182,7 @@ constexpr size_t kAlign = 256;
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct BatchLayout {
-  size_t status = 0, queue = 64, order = 0, dt = 0, aux = 0, U1 = 0, U2 = 0, total = 0;
+  size_t status = 0, queue = 64, order = 0, dt = 0, aux = 0, fh = 0, U1 = 0, U2 = 0, total = 0;
 };
 
 bool batch_ok(const teno_batch* b) {
@@ -189,6 +203,8 @@ BatchLayout batch_layout(const teno_batch* b) {
   off += round_up(sizeof(double) * size_t(b->nprob));
   L.aux = off;
   off += round_up(sizeof(double) * 4 * size_t(b->ncell));
+  L.fh = off;
+  off += round_up(sizeof(double) * 3 * size_t(b->ncell));
   L.U1 = off;
   off += round_up(sizeof(double) * 3 * size_t(b->ncell));
   L.U2 = off;
@@ -270,6 +286,7 @@ teno_status teno_rk3_step_batched(const teno_batch* b, const int64_t* offsets, c
   char* w = static_cast<char*>(ws);
   BatchArgs A;
   A.aux = reinterpret_cast<double*>(w + L.aux);
+  A.fh = reinterpret_cast<double*>(w + L.fh);
   A.offsets = offsets;
   A.dx = dx;
   A.t = t_dev;

@@ -52,7 +52,7 @@ struct Layout {
   // header: [0] status, [8] dt, [64] LF speeds (9 x 8) then the pending-list
   // counters (3 x 4)
   size_t status = 0, dt = 8, alpha = 64;
-  size_t aux = 0, fhat = 0, list = 0, R = 0, U1 = 0, U2 = 0, total = 0;
+  size_t aux = 0, fh = 0, fhat = 0, list = 0, R = 0, U1 = 0, U2 = 0, total = 0;
 };
 
 Layout layout_of(const teno_grid* g, int op) {
@@ -64,6 +64,8 @@ Layout layout_of(const teno_grid* g, int op) {
   size_t off = kHeader;
   L.aux = off;
   off += round_up(sizeof(double) * (g->ndim + 3) * ncell);
+  L.fh = off;   // half physical fluxes F_d/2 per cell and direction
+  off += round_up(sizeof(double) * g->ndim * nvar * ncell);
   L.fhat = off;
   off += round_up(sizeof(double) * nvar * size_t(maxifc));
   L.list = off;
@@ -178,11 +180,12 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
   double* aux = reinterpret_cast<double*>(ws + L.aux);
   double* Fhat = reinterpret_cast<double*>(ws + L.fhat);
   uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
+  double* fh = flags ? nullptr : reinterpret_cast<double*>(ws + L.fh);   // the flag path is one-pass
   unsigned* count = reinterpret_cast<unsigned*>(ws + L.alpha + teno::kPendingCountOffset);
   TENO_CUDA(cudaMemsetAsync(alpha, 0, teno::kAlphaAndCountBytes, st));
   {
     TimerScope ts(st, TENO_KERNEL_CELL);
-    TENO_CUDA(teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st));
+    TENO_CUDA(teno::launch_cell(g->ndim, U, aux, fh, alpha, status, G.ncell, g->gamma, nsm, st));
   }
   if (with_dt) {
     TimerScope ts(st, TENO_KERNEL_DT);
@@ -194,7 +197,7 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
     {
       TimerScope ts(st, TENO_KERNEL_FLUX);
       int nl = 1;
-      TENO_CUDA(teno::launch_flux(g->ndim, d, U, aux, alpha, Fhat, fl, list, count + d, status, G, S, nsm, st,
+      TENO_CUDA(teno::launch_flux(g->ndim, d, U, aux, fh, alpha, Fhat, fl, list, count + d, status, G, S, nsm, st,
                                   &nl));
       ts.launches(nl);
     }

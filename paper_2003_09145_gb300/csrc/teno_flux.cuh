@@ -218,24 +218,33 @@ __device__ __forceinline__ bool cert_keep(const CertIfc<NDIM>& C, const Scheme& 
 // with P = (1,-8,37,37,-8,1)/60 (central) and M = (1,-5,10,-10,5,-1)/60;
 // R L = I and alpha takes three values, so
 //   F^ = F~ + a_mid U~ + (a_0 - a_mid)(l_0.U~) r_0 + (a_E - a_mid)(l_E.U~) r_E.
-// closed_point adds point j to F~ and U~ (sums start at zero);
-// closed_out forms F^.
+// cell_flux_half gives F_d(U)/2 of one cell (eq. 4.7) from its half u_d and
+// half p -- the grid path stores it per cell and direction, the one-pass
+// path forms it per stencil point, with the same rounding; closed_point adds
+// point j to F~ and U~ (sums start at zero); closed_out forms F^.
 // ---------------------------------------------------------------------------
 template <int NDIM, int DIR>
-__device__ __forceinline__ void closed_point(int j, const double (&Uj)[NDIM + 2], double unj, double pnj,
+__device__ __forceinline__ void cell_flux_half(const double (&Uc)[NDIM + 2], double un, double pn,
+                                               double (&Fh)[NDIM + 2]) {
+  constexpr int NVAR = NDIM + 2;
+  // F/2 = (u_d/2) U + (p/2) (0, e_d, u_d)
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) Fh[v] = un * Uc[v];
+  Fh[1 + DIR] += pn;
+  Fh[NVAR - 1] = fma(pn, un + un, Fh[NVAR - 1]);
+}
+
+template <int NDIM>
+__device__ __forceinline__ void closed_point(int j, const double (&Uj)[NDIM + 2], const double (&Fhj)[NDIM + 2],
                                              double (&Ft)[NDIM + 2], double (&Ut)[NDIM + 2]) {
   constexpr int NVAR = NDIM + 2;
   const double P2[6] = {1.0 / 30.0, -8.0 / 30.0, 37.0 / 30.0, 37.0 / 30.0, -8.0 / 30.0, 1.0 / 30.0};
   const double Mw[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
-  // F_j / 2 = (u_d/2) U_j + (p/2) (0, e_d, u_d)
-  const double cu = P2[j] * unj;
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) {
-    Ft[v] = fma(cu, Uj[v], Ft[v]);
+    Ft[v] = fma(P2[j], Fhj[v], Ft[v]);
     Ut[v] = fma(Mw[j], Uj[v], Ut[v]);
   }
-  Ft[1 + DIR] = fma(P2[j], pnj, Ft[1 + DIR]);
-  Ft[NVAR - 1] = fma(cu + cu, pnj, Ft[NVAR - 1]);
 }
 
 template <int NDIM, int DIR>
@@ -262,13 +271,14 @@ __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const d
 // ---------------------------------------------------------------------------
 // The certified closed form alone, one stencil point at a time (each
 // point's state is dead once it has entered F~, U~ and the FP32 test, which
-// keeps the register footprint small).  Returns false, with `out`
-// unwritten, when the test does not keep every stencil; otherwise `out`
-// equals interface_flux's.
+// keeps the register footprint small), with the per-cell F_DIR/2 of the cell
+// pass (`fh`, [nvar][ncell]).  Returns false, with `out` unwritten, when the
+// test does not keep every stencil; otherwise `out` equals interface_flux's.
 // ---------------------------------------------------------------------------
 template <int NDIM, int DIR>
 __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__ U,
-                                                      const double* __restrict__ aux, int64_t ncell,
+                                                      const double* __restrict__ aux,
+                                                      const double* __restrict__ fh, int64_t ncell,
                                                       const int64_t (&cells)[6],
                                                       const double (&alpha)[NDIM + 2],
                                                       const double (&nal)[NDIM + 2], const Scheme& S,
@@ -295,11 +305,14 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     const int64_t c = cells[j];
-    double Uj[NVAR];
+    double Uj[NVAR], Fhj[NVAR];
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) Uj[v] = U[v * ncell + c];
+    for (int v = 0; v < NVAR; ++v) {
+      Uj[v] = U[v * ncell + c];
+      Fhj[v] = fh[v * ncell + c];
+    }
     const double unj = aux[DIR * ncell + c], pnj = aux[NDIM * ncell + c];
-    closed_point<NDIM, DIR>(j, Uj, unj, pnj, Ft, Ut);
+    closed_point<NDIM>(j, Uj, Fhj, Ft, Ut);
     cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
   }
   if (!cert_keep<NDIM>(C, S)) return false;
@@ -385,7 +398,11 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
 #pragma unroll
         for (int v = 0; v < NVAR; ++v) Ft[v] = Ut[v] = 0.0;
 #pragma unroll
-        for (int j = 0; j < 6; ++j) closed_point<NDIM, DIR>(j, Ux[j], un[j], pn[j], Ft, Ut);
+        for (int j = 0; j < 6; ++j) {
+          double Fhj[NVAR];
+          cell_flux_half<NDIM, DIR>(Ux[j], un[j], pn[j], Fhj);
+          closed_point<NDIM>(j, Ux[j], Fhj, Ft, Ut);
+        }
         closed_out<NDIM, DIR>(Ft, Ut, R, nal, out);
 #pragma unroll
         for (int f = 0; f < NVAR; ++f) fl[f][0] = fl[f][1] = 7u;

@@ -29,16 +29,33 @@ namespace teno {
 // (cell_primitives); the wave speeds |u_d - c|, |u_d|, |u_d + c| are reduced
 // to their maxima over all cells.
 // aux layout: [ndim + 3][ncell]: u_0/2..u_{ndim-1}/2, p/2, sqrt(rho),
-// (E+p)/sqrt(rho).
+// (E+p)/sqrt(rho).  With `fh`, also the half physical fluxes F_d/2 (eq. 4.7)
+// of every direction, [ndim][nvar][ncell], for the closed-form flux pass.
 // alpha layout (bit patterns of non-negative doubles): [ndim][3] =
 // max|u_d - c|, max|u_d|, max|u_d + c|.
 // ---------------------------------------------------------------------------
+// F_d/2 of cell c for d = D..NDIM-1 into fh[d][v][c].
+template <int NDIM, int D>
+__device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], const double* __restrict__ aux,
+                                                double pn, double* __restrict__ fh, int64_t ncell, int64_t c) {
+  if constexpr (D < NDIM) {
+    constexpr int NVAR = NDIM + 2;
+    double Fh[NVAR];
+    cell_flux_half<NDIM, D>(Uc, aux[D * ncell + c], pn, Fh);
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) fh[(int64_t)(D * NVAR + v) * ncell + c] = Fh[v];
+    store_flux_half<NDIM, D + 1>(Uc, aux, pn, fh, ncell, c);
+  }
+}
+
 template <int NDIM>
 __global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
                                                    double* __restrict__ aux,
+                                                   double* __restrict__ fh,
                                                    unsigned long long* __restrict__ alpha,
                                                    int* __restrict__ status,
                                                    int64_t ncell, double gamma) {
+  constexpr int NVAR = NDIM + 2;
   double lam[NDIM][3];
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) lam[d][0] = lam[d][1] = lam[d][2] = 0.0;
@@ -47,6 +64,13 @@ __global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
        c += (int64_t)gridDim.x * blockDim.x) {
     double u[NDIM], cs;
     if (!cell_primitives<NDIM>(U, ncell, c, gamma, aux, u, cs)) bad = true;
+    if (fh) {
+      double Uc[NVAR];
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) Uc[v] = U[v * ncell + c];
+      const double pn = aux[NDIM * ncell + c];
+      store_flux_half<NDIM, 0>(Uc, aux, pn, fh, ncell, c);
+    }
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       lam[d][0] = fmax(lam[d][0], fabs(__dsub_rn(u[d], cs)));
@@ -192,7 +216,7 @@ __device__ __forceinline__ void half_speeds(const unsigned long long* __restrict
 
 template <int NDIM, int DIR>
 __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel(
-    const double* __restrict__ U, const double* __restrict__ aux,
+    const double* __restrict__ U, const double* __restrict__ aux, const double* __restrict__ fh,
     const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
     uint32_t* __restrict__ list, unsigned* __restrict__ count, int* __restrict__ status, Grid G,
     Scheme S) {
@@ -206,7 +230,8 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
     int64_t cells[6];
     interface_cells<NDIM, DIR>(q, G, cells);
     double out[NVAR];
-    const bool done = interface_flux_closed<NDIM, DIR>(U, aux, G.ncell, cells, alpha, nal, S, out, status);
+    const bool done = interface_flux_closed<NDIM, DIR>(U, aux, fh + (int64_t)DIR * NVAR * G.ncell, G.ncell, cells,
+                                                       alpha, nal, S, out, status);
     if (done) {
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
@@ -392,23 +417,24 @@ static inline int blocks_for(int64_t n, int threads, int cap) {
   return static_cast<int>(b);
 }
 
-cudaError_t launch_cell(int ndim, const double* U, double* aux,
+cudaError_t launch_cell(int ndim, const double* U, double* aux, double* fh,
                         unsigned long long* alpha, int* status, int64_t ncell,
                         double gamma, int nsm, cudaStream_t st) {
   const int threads = 256;
   const int blocks = blocks_for(ncell, threads, nsm * 8);
   switch (ndim) {
-    case 1: cell_kernel<1><<<blocks, threads, 0, st>>>(U, aux, alpha, status, ncell, gamma); break;
-    case 2: cell_kernel<2><<<blocks, threads, 0, st>>>(U, aux, alpha, status, ncell, gamma); break;
-    default: cell_kernel<3><<<blocks, threads, 0, st>>>(U, aux, alpha, status, ncell, gamma); break;
+    case 1: cell_kernel<1><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma); break;
+    case 2: cell_kernel<2><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma); break;
+    default: cell_kernel<3><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma); break;
   }
   return cudaGetLastError();
 }
 
 template <int NDIM, int DIR>
 static int flux_launch(int blocks, int threads, int pblocks, cudaStream_t st, const double* U,
-                       const double* aux, const unsigned long long* alpha, double* Fhat, uint8_t* flags,
-                       uint32_t* list, unsigned* count, int* status, const Grid& G, const Scheme& S) {
+                       const double* aux, const double* fh, const unsigned long long* alpha, double* Fhat,
+                       uint8_t* flags, uint32_t* list, unsigned* count, int* status, const Grid& G,
+                       const Scheme& S) {
   if (flags) {
     flux_kernel<NDIM, DIR, true><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
     return 1;
@@ -417,12 +443,12 @@ static int flux_launch(int blocks, int threads, int pblocks, cudaStream_t st, co
     flux_kernel<NDIM, DIR, false><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
     return 1;
   }
-  flux_closed_kernel<NDIM, DIR><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
+  flux_closed_kernel<NDIM, DIR><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
   flux_pending_kernel<NDIM, DIR><<<pblocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
   return 2;
 }
 
-cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux,
+cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, const double* fh,
                         const unsigned long long* alpha, double* Fhat,
                         uint8_t* flags, uint32_t* list, unsigned* count, int* status,
                         const Grid& G, const Scheme& S, int nsm, cudaStream_t st,
@@ -430,19 +456,19 @@ cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux,
   int64_t nifc = 1;
   for (int k = 0; k < 3; ++k) nifc *= G.n[k] + (k == dir ? 1 : 0);
   if (nifc > int64_t(UINT32_MAX)) list = nullptr;   // list entries are 32-bit
-  if (!count) list = nullptr;
+  if (!count || !fh) list = nullptr;
   const int threads = 128;
   const int blocks = blocks_for(nifc, threads, nsm * 64);
   const int pblocks = blocks_for(nifc, threads, nsm * 16);
   int n = 0;
-  if (ndim == 1) n = flux_launch<1, 0>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
+  if (ndim == 1) n = flux_launch<1, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
   else if (ndim == 2) {
-    if (dir == 0) n = flux_launch<2, 0>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
-    else n = flux_launch<2, 1>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
+    if (dir == 0) n = flux_launch<2, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
+    else n = flux_launch<2, 1>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
   } else {
-    if (dir == 0) n = flux_launch<3, 0>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
-    else if (dir == 1) n = flux_launch<3, 1>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
-    else n = flux_launch<3, 2>(blocks, threads, pblocks, st, U, aux, alpha, Fhat, flags, list, count, status, G, S);
+    if (dir == 0) n = flux_launch<3, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
+    else if (dir == 1) n = flux_launch<3, 1>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
+    else n = flux_launch<3, 2>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
   }
   if (launches) *launches = n;
   return cudaGetLastError();
@@ -485,7 +511,7 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 }
 
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
-                          size_t alpha_off, size_t aux_off, size_t fhat_off, size_t list_off,
+                          size_t alpha_off, size_t aux_off, size_t fh_off, size_t fhat_off, size_t list_off,
                           const double* U, double* R, int mode, const double* Un, const double* Uk,
                           double* Uout, cudaStream_t st) {
   Grid G;
@@ -507,12 +533,13 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
   double* aux = reinterpret_cast<double*>(ws + aux_off);
   double* Fhat = reinterpret_cast<double*>(ws + fhat_off);
   uint32_t* list = list_off ? reinterpret_cast<uint32_t*>(ws + list_off) : nullptr;
+  double* fh = fh_off ? reinterpret_cast<double*>(ws + fh_off) : nullptr;
   unsigned* count = reinterpret_cast<unsigned*>(ws + alpha_off + kPendingCountOffset);
   if (cudaMemsetAsync(alpha, 0, kAlphaAndCountBytes, st) != cudaSuccess) return TENO_ERR_CUDA;
-  if (launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
+  if (launch_cell(g->ndim, U, aux, fh, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
     return TENO_ERR_CUDA;
   for (int d = 0; d < g->ndim; ++d) {
-    if (launch_flux(g->ndim, d, U, aux, alpha, Fhat, nullptr, list, count + d, status, G, S, nsm, st,
+    if (launch_flux(g->ndim, d, U, aux, fh, alpha, Fhat, nullptr, list, count + d, status, G, S, nsm, st,
                     nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
     const bool last = (d == g->ndim - 1);

@@ -13,16 +13,19 @@ namespace teno {
 // Scheme constants for the given gas and LAD parameters (eq. 3.1-3.2, 2.8).
 Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u);
 
-cudaError_t launch_cell(int ndim, const double* U, double* aux,
+// Primitives (aux) and LF speeds of every cell; with `fh` (nullable) also
+// the half physical fluxes F_d/2, [ndim][nvar][ncell].
+cudaError_t launch_cell(int ndim, const double* U, double* aux, double* fh,
                         unsigned long long* alpha, int* status, int64_t ncell,
                         double gamma, int nsm, cudaStream_t st);
 
 // The interface fluxes of direction `dir` into Fhat.  With `flags`, or
-// without a pending list, one pass; with `list` (room for one 32-bit entry
-// per interface) and its counter `count` (zero on entry), the closed-form
-// pass and the pass over the interfaces it leaves pending.  `launches`
-// (optional) receives the number of kernels launched.
-cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux,
+// without a pending list or the cell pass's half fluxes `fh`, one pass; with
+// `list` (room for one 32-bit entry per interface), its counter `count`
+// (zero on entry) and `fh`, the closed-form pass and the pass over the
+// interfaces it leaves pending.  `launches` (optional) receives the number
+// of kernels launched.
+cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, const double* fh,
                         const unsigned long long* alpha, double* Fhat,
                         uint8_t* flags, uint32_t* list, unsigned* count, int* status,
                         const Grid& G, const Scheme& S, int nsm, cudaStream_t st,
@@ -46,11 +49,12 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 // One right-hand-side evaluation of U fused with the SSP-RK3 stage `mode`
 // (2, 3 or 4; see diff_kernel) into Uout, with dt read from the workspace
 // word at dt_off.  `ws` offsets locate the status word, the LF speeds (and
-// the pending counters after them), the per-cell primitives, the
-// interface-flux buffer and the pending list (0: none, one-pass fluxes); R
-// holds the partial sums of the multi-dimensional difference.
+// the pending counters after them), the per-cell primitives, the half
+// fluxes, the interface-flux buffer and the pending list (fh_off or list_off
+// 0: one-pass fluxes); R holds the partial sums of the multi-dimensional
+// difference.
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
-                          size_t alpha_off, size_t aux_off, size_t fhat_off, size_t list_off,
+                          size_t alpha_off, size_t aux_off, size_t fh_off, size_t fhat_off, size_t list_off,
                           const double* U, double* R, int mode, const double* Un, const double* Uk,
                           double* Uout, cudaStream_t st);
 

@@ -132,10 +132,10 @@ extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, dou
   // wave-speed maxima must start from zero.
   if (cudaMemsetAsync(status, 0, 64 + sizeof(unsigned long long) * 9, st) != cudaSuccess)
     return TENO_ERR_CUDA;
-  if (teno::launch_cell(g->ndim, U, aux, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
+  if (teno::launch_cell(g->ndim, U, aux, nullptr, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
     return TENO_ERR_CUDA;
   for (int d = 0; d < g->ndim; ++d) {
-    if (teno::launch_flux(g->ndim, d, U, aux, alpha, Fhat, nullptr, nullptr, nullptr, status, G, S, nsm, st,
+    if (teno::launch_flux(g->ndim, d, U, aux, nullptr, alpha, Fhat, nullptr, nullptr, nullptr, status, G, S, nsm, st,
                           nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
     if (teno::launch_diff(g->ndim, d, Fhat, dUdt, nullptr, nullptr, nullptr, nullptr, G,
