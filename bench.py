@@ -55,15 +55,32 @@ SURVEY_FLOPS_PER_IFACE_3D = 1495
 STATE_BYTES_PER_CELL = 5 * 8
 
 
-def _dist():
+def _dist(backend: str = "nccl"):
+    """One process per GPU under torchrun (RANK / WORLD_SIZE / MASTER_* from the
+    environment); (None, 0, 1) without it."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return None, 0, 1
     import torch.distributed as dist
     rank = int(os.environ["RANK"])
-    backend = "nccl"
     dist.init_process_group(backend=backend)
     return dist, rank, ws
+
+
+def max_over_ranks(dist, ms: float, device) -> float:
+    """The slowest rank's time (every rank gets it); ms itself without ranks."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, cells: int, steps: int, ms: float) -> float:
+    """Gcell-updates/s of the whole job: every replica advances `cells` cells by
+    `steps` steps in the max-over-ranks time `ms` (weak scaling)."""
+    return world * cells * steps / (ms * 1e-3) / 1e9
 
 
 def _peaks():
@@ -382,12 +399,9 @@ def main() -> None:
     _lib.check(lib.teno_timer_end(kms, kcount), "teno_timer_end")
     clk = clocks.stop()
     assert solver.status() == 0, "non-physical state in the timed region"
-    if dist:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, ms, device)
     cells = grid.ncell
-    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+    value = whole_job_rate(world, cells, args.steps, ms)
 
     # ---- roofline of the dominant kernel (interface fluxes) ----------------
     kinds = dict(zip(_lib.KERNEL_KINDS, zip(list(kms), list(kcount))))
@@ -434,12 +448,9 @@ def main() -> None:
     f1.record()
     torch.cuda.synchronize()
     ems = f0.elapsed_time(f1)
-    if dist:
-        t = torch.tensor([ems], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
+    ems = max_over_ranks(dist, ems, device)
     nbytes = U0.numel() * 8
-    e2e = {"value": world * cells * args.steps / (ems * 1e-3) / 1e9, "unit": UNIT,
+    e2e = {"value": whole_job_rate(world, cells, args.steps, ems), "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     forms = {}

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
     if (A.mode != 2 && !(A.dtv[p] > 0.0)) continue;  // finished problem
 
     // (A) primitive variables and LF speeds of this problem
-    double l0 = 0.0, l1 = 0.0, l2 = 0.0;
+    unsigned long long b0 = 0ull, b1 = 0ull, b2 = 0ull;   // bit patterns of the maxima
     bool bad = false;
     for (int64_t i = tid; i < n; i += BLOCK) {
       double u[1], cs;
@@ -89,11 +89,10 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
       teno::cell_flux_half<1, 0>(Uc, A.aux[c], A.aux[A.ncell + c], Fh);
 #pragma unroll
       for (int v = 0; v < 3; ++v) A.fh[v * A.ncell + c] = Fh[v];
-      l0 = fmax(l0, fabs(__dsub_rn(u[0], cs)));
-      l1 = fmax(l1, fabs(u[0]));
-      l2 = fmax(l2, fabs(__dadd_rn(u[0], cs)));
+      b0 = teno::max_abs_bits(b0, __dsub_rn(u[0], cs));
+      b1 = teno::max_abs_bits(b1, u[0]);
+      b2 = teno::max_abs_bits(b2, __dadd_rn(u[0], cs));
     }
-    unsigned long long b0 = teno::dbits(l0), b1 = teno::dbits(l1), b2 = teno::dbits(l2);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long w0 = __shfl_xor_sync(0xffffffffu, b0, o);

@@ -122,6 +122,24 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
   return static_cast<unsigned long long>(__double_as_longlong(x));
 }
 
+// Integer-pipe tests and maxima on binary64 bit patterns (GB300's FP64 pipe
+// is the scarce unit):
+//   max_abs_bits(m, x) = bits of max(value(m), |x|) for m >= 0, skipping a NaN
+//                        x as fmax does (non-negative doubles order as
+//                        their bit patterns);
+//   pos_finite(x)      = 0 < x < inf;
+//   is_finite(x)       = x is neither inf nor NaN.
+constexpr unsigned long long kExpMask = 0x7FF0000000000000ull;
+__device__ __forceinline__ unsigned long long max_abs_bits(unsigned long long m, double x) {
+  const unsigned long long b = dbits(x) & 0x7FFFFFFFFFFFFFFFull;
+  return (b <= kExpMask && b > m) ? b : m;
+}
+__device__ __forceinline__ bool pos_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < static_cast<long long>(kExpMask);
+}
+__device__ __forceinline__ bool is_finite(double x) { return (dbits(x) & kExpMask) != kExpMask; }
+
 // binary32 approximation of a double built on the integer pipe from its high
 // word: exponent rebiased, mantissa truncated to 20 bits (|f - x| < 2^-20 |x|),
 // magnitudes clamped to [2^-126, 2^128).

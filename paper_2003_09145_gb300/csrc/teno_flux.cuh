@@ -507,7 +507,7 @@ __device__ __forceinline__ bool cell_primitives(const double* __restrict__ U, in
   aux[NDIM * ncell + c] = 0.5 * p;
   aux[(NDIM + 1) * ncell + c] = sr;
   aux[(NDIM + 2) * ncell + c] = (E + p) * isr;
-  return (rho > 0.0) && (p > 0.0) && isfinite(E) && isfinite(q2) && (gpr > 0.0);
+  return pos_finite(rho) && pos_finite(p) && is_finite(E) && is_finite(q2) && pos_finite(gpr);
 }
 
 // SSP-RK3 stage value (eq. 4.1-4.3) of element e from d = L(U^(k))_e:

@@ -49,16 +49,16 @@ __device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], co
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
+__global__ void __launch_bounds__(256, 3) cell_kernel(const double* __restrict__ U,
                                                    double* __restrict__ aux,
                                                    double* __restrict__ fh,
                                                    unsigned long long* __restrict__ alpha,
                                                    int* __restrict__ status,
                                                    int64_t ncell, double gamma) {
   constexpr int NVAR = NDIM + 2;
-  double lam[NDIM][3];
+  unsigned long long lam[NDIM][3];   // bit patterns of the running maxima (>= 0)
 #pragma unroll
-  for (int d = 0; d < NDIM; ++d) lam[d][0] = lam[d][1] = lam[d][2] = 0.0;
+  for (int d = 0; d < NDIM; ++d) lam[d][0] = lam[d][1] = lam[d][2] = 0ull;
   bool bad = false;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
     }
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      lam[d][0] = fmax(lam[d][0], fabs(__dsub_rn(u[d], cs)));
-      lam[d][1] = fmax(lam[d][1], fabs(u[d]));
-      lam[d][2] = fmax(lam[d][2], fabs(__dadd_rn(u[d], cs)));
+      lam[d][0] = max_abs_bits(lam[d][0], __dsub_rn(u[d], cs));
+      lam[d][1] = max_abs_bits(lam[d][1], u[d]);
+      lam[d][2] = max_abs_bits(lam[d][2], __dadd_rn(u[d], cs));
     }
   }
   // warp max on bit patterns (all values are >= 0)
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const double* __restrict__ U,
   for (int d = 0; d < NDIM; ++d)
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      unsigned long long v = dbits(lam[d][s]);
+      unsigned long long v = lam[d][s];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
