@@ -73,6 +73,20 @@ def shock_tube(n: int = 200, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1),
                    x0=(a,), extra={"left": tuple(left), "right": tuple(right), "x_jump": x_jump})
 
 
+def sod_paper(n: int = 400, t_end: float = 0.14) -> Problem:
+    """Sod's tube as in Sec. 4.2 (eq. 4.8): [-0.5, 0.5], left state where x <= 0,
+    zero-gradient ends; the paper's figures use N = 400 at t = 0.14."""
+    return shock_tube(n, a=-0.5, b=0.5, x_jump=0.0, t_end=t_end, name="sod_paper")
+
+
+def lax_tube(n: int = 400, t_end: float = 0.13) -> Problem:
+    """Lax's tube (eq. 4.9): (0.445, 0.698, 3.528) where x <= 0, else
+    (0.5, 0, 0.571), on [-5, 5] with zero-gradient ends; the paper's figures
+    use N = 400 at t = 0.13."""
+    return shock_tube(n, left=(0.445, 0.698, 3.528), right=(0.5, 0.0, 0.571), a=-5.0, b=5.0,
+                      x_jump=0.0, t_end=t_end, name="lax")
+
+
 def shu_osher(n: int = 4096, t_end: float = 1.8) -> Problem:
     """Shock / entropy-wave interaction on [-5, 5] (eq. 4.10), with the post-shock
     state given to six digits: (3.857143, 2.629369, 10.3333) for x < -4, else
@@ -108,6 +122,15 @@ QUADRANTS_LAX_LIU_3 = {
 }
 
 
+# configuration 12 of the same family (eq. 4.13)
+QUADRANTS_CONFIG_12 = {
+    "NE": (0.5313, 0.0, 0.0, 0.4),
+    "NW": (1.0, 0.7276, 0.0, 1.0),
+    "SW": (0.8, 0.0, 0.0, 1.0),
+    "SE": (1.0, 0.0, 0.7276, 1.0),
+}
+
+
 def riemann_2d(n: int = 2048, split=(0.8, 0.8), states=QUADRANTS_LAX_LIU_3,
                t_end: float = 0.8, ny: int | None = None) -> Problem:
     """Four-quadrant 2D Riemann problem on [0,1]^2 (eq. 4.14 layout), quadrants split
@@ -129,6 +152,22 @@ def riemann_2d(n: int = 2048, split=(0.8, 0.8), states=QUADRANTS_LAX_LIU_3,
     U = prim_to_cons(prim[0], [prim[1], prim[2]], prim[3])
     return Problem("riemann2d", U, (nx, ny), (dx, dy), (TRANSMISSIVE, TRANSMISSIVE), t_end,
                    x0=(0.0, 0.0))
+
+
+def riemann_2d_config3(n: int = 1024, t_end: float = 0.3) -> Problem:
+    """Sec. 4.3.1's first case (eq. 4.14): the states of QUADRANTS_LAX_LIU_3 split
+    at (0.5, 0.5), integrated to t = 0.3 on 1024^2 in the paper."""
+    P = riemann_2d(n, split=(0.5, 0.5), states=QUADRANTS_LAX_LIU_3, t_end=t_end)
+    P.name = "riemann2d_config3"
+    return P
+
+
+def riemann_2d_config12(n: int = 1024, t_end: float = 0.25) -> Problem:
+    """Sec. 4.3.1's second case (eq. 4.13): split at (0.5, 0.5), integrated to
+    t = 0.25 on 1024^2 and 2048^2 in the paper."""
+    P = riemann_2d(n, split=(0.5, 0.5), states=QUADRANTS_CONFIG_12, t_end=t_end)
+    P.name = "riemann2d_config12"
+    return P
 
 
 @dataclass
