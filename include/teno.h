@@ -229,6 +229,44 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n,
  */
 teno_status teno_get_device_status(void* ws, void* stream, int* status);
 
+/* ------------------------------------------------------------------------ */
+/* Scalar mode: linear advection, the paper's scalar test problems.          */
+/* ------------------------------------------------------------------------ */
+
+/* Reconstruction used by the scalar mode. */
+enum {
+  TENO_SCALAR_LAD = 0,      /* TENO5-LAD (eq. 2.4-2.15, 3.1-3.4)               */
+  TENO_SCALAR_UPWIND5 = 1   /* the fixed linear weights of eq. 2.3           */
+};
+
+/* Bytes of workspace the scalar mode needs for grid g (0 if g is not a valid
+ * periodic 1D grid). */
+size_t teno_scalar_workspace_bytes(const teno_grid* g);
+
+/*
+ * teno_scalar_rhs -- right-hand side of u_t + a u_x = 0 (eq. 4.4) on a
+ * periodic 1D grid: the flux f = a u is split by global Lax-Friedrichs
+ * (alpha = |a|), f^+ = (a + |a|) u / 2 is reconstructed from u_{i-2..i+2}
+ * and f^- = (a - |a|) u / 2 from u_{i+3..i-1} with `mode` (TENO_SCALAR_*),
+ * and dudt_i = -(f^_{i+1/2} - f^_{i-1/2}) / dx (eq. 2.2).
+ *   g      : ndim = 1, bc[0] = TENO_BC_PERIODIC (else TENO_ERR_UNSUPPORTED);
+ *            H, b_l, b_u, eps as for the Euler path; gamma is unused.
+ *   a      : advection speed (finite).
+ *   u      : [in]  device, n[0] doubles.
+ *   dudt   : [out] device, n[0] doubles; must not alias u.
+ *   ws     : >= teno_scalar_workspace_bytes(g).
+ */
+teno_status teno_scalar_rhs(const teno_grid* g, double a, int mode, const double* u,
+                            double* dudt, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * teno_scalar_rk3_step -- one SSP-RK3 step (eq. 4.1-4.3) of fixed dt > 0 of
+ * the same problem, u in place (the caller clips the last step to its final
+ * time).
+ */
+teno_status teno_scalar_rk3_step(const teno_grid* g, double a, int mode, double* u, double dt,
+                                 void* ws, size_t ws_bytes, void* stream);
+
 /*
  * teno_rhs_noalloc -- teno_rhs for callers that cannot allocate device memory.
  * The paper has no counterpart; this is a deployment aid.

@@ -85,6 +85,10 @@ SIGNATURES = [
                                              ctypes.c_double, ctypes.c_double,
                                              ctypes.POINTER(TenoBatchTuning), _VP, ctypes.c_size_t, _VP]),
     ("teno_rhs_noalloc", ctypes.c_int, [_GP, _VP, _VP, _VP]),
+    ("teno_scalar_workspace_bytes", ctypes.c_size_t, [_GP]),
+    ("teno_scalar_rhs", ctypes.c_int, [_GP, ctypes.c_double, ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("teno_scalar_rk3_step", ctypes.c_int, [_GP, ctypes.c_double, ctypes.c_int, _VP, ctypes.c_double, _VP,
+                                            ctypes.c_size_t, _VP]),
     ("teno_timer_begin", ctypes.c_int, []),
     ("teno_timer_end", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     ("teno_probe_fp64", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP]),

@@ -251,6 +251,56 @@ class BatchSolver:
         return device_status(self.ws)
 
 
+SCALAR_MODES = {"lad": 0, "upwind5": 1}
+
+
+class ScalarAdvection:
+    """Linear advection u_t + a u_x = 0 (eq. 4.4) on a periodic 1D grid of n
+    cells: the scalar form of the same TENO5-LAD reconstruction (``mode``
+    "lad") or the linear weights of eq. 2.3 ("upwind5"); owns its workspace."""
+
+    def __init__(self, n: int, dx: float, a: float = 1.0, mode: str = "lad", scheme: Scheme | None = None,
+                 device="cuda"):
+        self.grid = EulerGrid((n,), (dx,), (_lib.BC_PERIODIC,), scheme)
+        self.a = float(a)
+        self.mode = SCALAR_MODES[mode]
+        self.n = int(n)
+        nb = self.grid.lib.teno_scalar_workspace_bytes(ctypes.byref(self.grid.c))
+        if nb == 0:
+            raise ValueError("invalid scalar grid")
+        self.ws = alloc_workspace(nb, torch.device(device))
+
+    def _check(self, u: torch.Tensor) -> None:
+        if u.dtype != torch.float64 or not u.is_cuda or not u.is_contiguous() or u.numel() != self.n:
+            raise ValueError(f"u must be a contiguous CUDA float64 tensor of {self.n} values")
+
+    def rhs(self, u: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """du/dt = -(f^_{i+1/2} - f^_{i-1/2}) / dx on the current stream."""
+        self._check(u)
+        dudt = out if out is not None else torch.empty_like(u)
+        st = self.grid.lib.teno_scalar_rhs(ctypes.byref(self.grid.c), self.a, self.mode, _ptr(u), _ptr(dudt),
+                                           _ptr(self.ws), self.ws.numel(), _stream_ptr())
+        _lib.check(st, "teno_scalar_rhs")
+        return dudt
+
+    def step(self, u: torch.Tensor, dt: float) -> None:
+        """One SSP-RK3 step (eq. 4.1-4.3) of dt, u in place."""
+        self._check(u)
+        st = self.grid.lib.teno_scalar_rk3_step(ctypes.byref(self.grid.c), self.a, self.mode, _ptr(u), float(dt),
+                                                _ptr(self.ws), self.ws.numel(), _stream_ptr())
+        _lib.check(st, "teno_scalar_rk3_step")
+
+    def run(self, u: torch.Tensor, t_end: float, dt: float) -> int:
+        """Steps of dt from t = 0 to t_end, the last one clipped; returns the count."""
+        t, k = 0.0, 0
+        while t < t_end:
+            h = dt if t_end - t >= dt else t_end - t
+            self.step(u, h)
+            t += h
+            k += 1
+        return k
+
+
 def rhs_adjoint(grid: EulerGrid, U: torch.Tensor, dUdt_bar: torch.Tensor, U_bar: torch.Tensor | None = None,
                 ws: torch.Tensor | None = None) -> torch.Tensor:
     """U_bar (+)= J(U)^T dUdt_bar with the stencil selections held at their values

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libteno_gb300.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["teno_kernels.cu", "teno_capi.cu", "teno_probe.cu", "teno_noalloc.cu", "teno_batched.cu", "teno_adjoint.cu"]
+SOURCES = ["teno_kernels.cu", "teno_capi.cu", "teno_probe.cu", "teno_noalloc.cu", "teno_batched.cu", "teno_adjoint.cu",
+           "teno_scalar.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]

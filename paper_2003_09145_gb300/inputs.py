@@ -113,6 +113,45 @@ def entropy_wave(n: int, t_end: float = 2.0, amp: float = 0.2) -> Problem:
                    (PERIODIC,), t_end, x0=(a,))
 
 
+# Scalar linear advection u_t + u_x = 0 on [-1, 1], periodic (Sec. 4.1), on
+# the points x_i = -1 + i dx, dx = 2/n.
+def scalar_points(n: int) -> np.ndarray:
+    return -1.0 + np.arange(n) * (2.0 / n)
+
+
+def scalar_smooth(n: int) -> np.ndarray:
+    """u0 = sin(pi x - sin(pi x) / pi) (eq. 4.5), with two critical points where
+    the first derivative vanishes and the third does not: Tab. 1's test."""
+    x = scalar_points(n)
+    return np.sin(np.pi * x - np.sin(np.pi * x) / np.pi)
+
+
+def scalar_composite(n: int) -> np.ndarray:
+    """The composite profile of eq. 4.6: Gaussians on [-0.8, -0.6), a square
+    wave on [-0.4, -0.2), a triangle on [0, 0.2), a half ellipse on
+    [0.4, 0.6), 0 elsewhere (a = 0.5, z = -0.7, delta = 0.005, alpha = 10,
+    beta = log 2 / (36 delta^2))."""
+    x = scalar_points(n)
+    a, z, delta, alpha = 0.5, -0.7, 0.005, 10.0
+    beta = np.log(2.0) / (36.0 * delta * delta)
+
+    def G(c):
+        return np.exp(-beta * (x - c) ** 2)
+
+    def F(c):
+        return np.sqrt(np.maximum(1.0 - alpha * alpha * (x - c) ** 2, 0.0))
+
+    u = np.zeros(n)
+    m = (x >= -0.8) & (x < -0.6)
+    u[m] = ((G(z - delta) + G(z + delta) + 4.0 * G(z)) / 6.0)[m]
+    u[(x >= -0.4) & (x < -0.2)] = 1.0
+    m = (x >= 0.0) & (x < 0.2)
+    u[m] = (1.0 - np.abs(10.0 * (x - 0.1)))[m]
+    m = (x >= 0.4) & (x < 0.6)
+    u[m] = ((F(a - delta) + F(a + delta) + 4.0 * F(a)) / 6.0)[m]
+    return u
+
+
 # 2D four-quadrant Riemann problem: quadrant states as (rho, u, v, p)
 QUADRANTS_LAX_LIU_3 = {
     "NE": (1.5, 0.0, 0.0, 1.5),

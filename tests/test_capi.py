@@ -77,3 +77,26 @@ def test_status_strings(lib):
     assert lib.teno_status_string(4) == b"TENO_ERR_NONPHYSICAL"
     assert lib.teno_status_string(99) == b"TENO_UNKNOWN_STATUS"
     assert lib.teno_abi_version() == 1
+
+
+def test_scalar_mode_validation(lib):
+    """Scalar mode: periodic 1D grids only; bad arguments are rejected on the host."""
+    from paper_2003_09145_gb300 import _lib
+    import numpy as np
+    good = _lib.make_grid((40,), (0.05,), 0)
+    nb = lib.teno_scalar_workspace_bytes(ctypes.byref(good))
+    assert nb >= 8 * (41 + 2 * 40)
+    assert lib.teno_scalar_workspace_bytes(ctypes.byref(_lib.make_grid((40,), (0.05,), 1))) == 0
+    assert lib.teno_scalar_workspace_bytes(ctypes.byref(_lib.make_grid((8, 8), (0.1, 0.1), 0))) == 0
+    u = np.ones(40)
+    ws = np.zeros(nb, dtype=np.uint8)
+    # transmissive: unsupported; bad mode, non-finite speed, host memory: invalid
+    assert lib.teno_scalar_rhs(ctypes.byref(_lib.make_grid((40,), (0.05,), 1)), 1.0, 0, None, None, None, 0,
+                               None) == 2   # TENO_ERR_UNSUPPORTED
+    assert lib.teno_scalar_rhs(ctypes.byref(good), 1.0, 7, u.ctypes.data, u.ctypes.data, ws.ctypes.data, nb,
+                               None) == 1
+    assert lib.teno_scalar_rhs(ctypes.byref(good), float("nan"), 0, u.ctypes.data, None, ws.ctypes.data, nb,
+                               None) == 1
+    assert lib.teno_scalar_rhs(ctypes.byref(good), 1.0, 0, u.ctypes.data, None, ws.ctypes.data, nb, None) == 1
+    assert lib.teno_scalar_rk3_step(ctypes.byref(good), 1.0, 0, u.ctypes.data, 0.01, ws.ctypes.data, nb,
+                                    None) == 1
