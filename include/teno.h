@@ -56,7 +56,12 @@ typedef enum {
 
 typedef enum {
   TENO_BC_PERIODIC = 0,      /* wrap-around                                   */
-  TENO_BC_TRANSMISSIVE = 1   /* zero gradient: the boundary cell is copied    */
+  TENO_BC_TRANSMISSIVE = 1,  /* zero gradient: the boundary cell is copied    */
+  TENO_BC_REFLECTIVE = 2     /* solid wall: cells mirrored about the wall with */
+                             /* the normal velocity reversed (Sec. 4.2's blast */
+                             /* waves); teno_rhs, teno_rk3_step and            */
+                             /* teno_rhs_noalloc only (the adjoint and batched */
+                             /* entry points return TENO_ERR_UNSUPPORTED)      */
 } teno_bc;
 
 /* Grid and scheme parameters (problem statement: eq. 2.1-2.2, eq. 4.7,

@@ -31,7 +31,9 @@
  * taken per characteristic field and per direction, as a maximum over all
  * cells, recomputed at every right-hand-side evaluation; the cutoff keeps a
  * stencil when chi_k >= C_T; transmissive boundaries copy the boundary cell
- * into three ghost cells, periodic ones wrap.
+ * into three ghost cells, periodic ones wrap, reflecting ones (the blast-wave
+ * test of Sec. 4.2) mirror the cells about the wall with the normal velocity
+ * reversed; the LF speeds and the time step use the interior cells only.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no FMA contraction,
  * so every product and sum is rounded separately as written).
@@ -295,15 +297,32 @@ int or_roe_eigensystem(int ndim, int d, const double* Ua, const double* Ub,
 
 /* Cell index after the boundary treatment: bc 0 = periodic (wrap),
  * bc 1 = transmissive / zero gradient (the boundary cell is copied into the
- * three ghost cells). */
+ * three ghost cells), bc 2 = reflecting (ghost cell -1-k is the mirror image
+ * of cell k about the wall; see ghost_reflects for the velocity). */
 static int64_t ghost_index(int64_t i, int64_t n, int bc) {
   if (bc == 0) {
     int64_t r = i % n;
     return r < 0 ? r + n : r;
   }
+  if (bc == 2) {
+    while (i < 0 || i >= n) i = (i < 0) ? -1 - i : 2 * n - 1 - i;
+    return i;
+  }
   if (i < 0) return 0;
   if (i >= n) return n - 1;
   return i;
+}
+
+/* 1 if the point i of a reflecting direction is a mirror image with the
+ * normal velocity reversed (an odd number of reflections), else 0. */
+static int ghost_reflects(int64_t i, int64_t n, int bc) {
+  int odd = 0;
+  if (bc != 2) return 0;
+  while (i < 0 || i >= n) {
+    i = (i < 0) ? -1 - i : 2 * n - 1 - i;
+    odd ^= 1;
+  }
+  return odd;
 }
 
 typedef struct {
@@ -395,6 +414,8 @@ static int interface_flux(const or_shape* s, int d, const int64_t ifc[3],
     int64_t idx[3] = {ifc[0], ifc[1], ifc[2]};
     idx[d] = ghost_index(base - 2 + j, s->n[d], bc[d]);
     load_cell(s, U, cell_linear(s, idx), Upt[j]);
+    /* reflecting wall: the ghost state has the normal momentum reversed */
+    if (ghost_reflects(base - 2 + j, s->n[d], bc[d])) Upt[j][1 + d] = -Upt[j][1 + d];
     physical_flux(ndim, d, Upt[j], P->gamma, Fpt[j]);
   }
   double L[OR_MAXVAR * OR_MAXVAR], R[OR_MAXVAR * OR_MAXVAR];

@@ -19,7 +19,7 @@ STATUS_NAMES = {
     7: "TENO_ERR_UNIMPLEMENTED",
 }
 OP_RHS, OP_RK3, OP_RHS_ADJOINT, OP_RK3_ADJOINT = 0, 1, 2, 3
-BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
 KERNEL_KINDS = ("cell", "flux", "diff", "dt")
 
 

@@ -53,7 +53,7 @@ class Scheme:
 
 class EulerGrid:
     """A uniform ndim grid of ``n`` cells (x first) with spacing ``dx`` and
-    boundary types ``bc`` (0 periodic, 1 transmissive)."""
+    boundary types ``bc`` (0 periodic, 1 transmissive, 2 reflecting)."""
 
     def __init__(self, n, dx, bc, scheme: Scheme | None = None):
         self.n = tuple(int(v) for v in n)

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     I.locate(q, G, id, base, cells);
     double fout[NVAR];
     unsigned fl[NVAR][2];
-    teno::interface_flux<NDIM, DIR, false, teno::kFluxCertify>(U, aux, I.ncell, cells, ha, nfa, S, fout, fl,
+    teno::interface_flux<NDIM, DIR, false, teno::kFluxCertify>(U, aux, I.ncell, cells, 0u, ha, nfa, S, fout, fl,
                                                                status);
     const bool kept = fl[0][0] != teno::kUndecided;
     pending[q] = kept ? 0 : 1;
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
       I.locate(q, G, id, base, cells);
       double fout[NVAR];
       unsigned fl[NVAR][2];
-      teno::interface_flux<NDIM, DIR, false, teno::kFluxSelect>(U, aux, I.ncell, cells, ha, nfa, S, fout, fl,
+      teno::interface_flux<NDIM, DIR, false, teno::kFluxSelect>(U, aux, I.ncell, cells, 0u, ha, nfa, S, fout, fl,
                                                                 status);
       unsigned sel[NVAR][2];
       bool all_kept = true;
@@ -461,6 +461,15 @@ bool grid_valid(const teno_grid* g) {
   return true;
 }
 
+// Reflecting walls are not differentiated here (the adjoint supports
+// periodic and transmissive boundaries).
+bool has_reflective(const teno_grid* g) {
+  if (!g || g->ndim < 1 || g->ndim > 3) return false;
+  for (int k = 0; k < g->ndim; ++k)
+    if (g->bc[k] == TENO_BC_REFLECTIVE) return true;
+  return false;
+}
+
 int64_t nifc_of(const teno_grid* g, int d) {
   int64_t m = 1;
   for (int k = 0; k < 3; ++k) m *= g->n[k] + (k == d ? 1 : 0);
@@ -621,6 +630,7 @@ size_t teno_adjoint_workspace_bytes(const teno_grid* g, int op) {
 
 teno_status teno_rhs_adjoint(const teno_grid* g, const double* U, const double* dUdt_bar, double* U_bar,
                              void* ws, size_t ws_bytes, void* stream) {
+  if (has_reflective(g)) return TENO_ERR_UNSUPPORTED;
   if (!grid_valid(g) || !U || !dUdt_bar || !U_bar) return TENO_ERR_INVALID_ARG;
   if (!al(U, 16) || !al(dUdt_bar, 16) || !al(U_bar, 16)) return TENO_ERR_INVALID_ARG;
   if (U_bar == U || U_bar == dUdt_bar) return TENO_ERR_INVALID_ARG;
@@ -633,6 +643,7 @@ teno_status teno_rhs_adjoint(const teno_grid* g, const double* U, const double* 
 
 teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double dt, const double* Ubar_next,
                                   double* Ubar_n, void* ws, size_t ws_bytes, void* stream) {
+  if (has_reflective(g)) return TENO_ERR_UNSUPPORTED;
   if (!grid_valid(g) || !U_n || !Ubar_next || !Ubar_n || !(dt >= 0.0) || !std::isfinite(dt))
     return TENO_ERR_INVALID_ARG;
   if (!al(U_n, 16) || !al(Ubar_next, 16) || !al(Ubar_n, 16) || Ubar_n == U_n) return TENO_ERR_INVALID_ARG;

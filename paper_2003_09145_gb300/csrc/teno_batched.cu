@@ -153,10 +153,12 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
         // the certified closed form, else the characteristic path (the grid
         // path's two passes, in one thread)
         double out[3];
-        if (!teno::interface_flux_closed<1, 0>(A.Uin, A.aux, A.fh, A.ncell, cells, alpha, nal, S, out, A.status)) {
+        // (periodic or transmissive ends only: no mirrored points)
+        if (!teno::interface_flux_closed<1, 0>(A.Uin, A.aux, A.fh, A.ncell, cells, 0u, alpha, nal, S, out,
+                                               A.status)) {
           unsigned fl[3][2];
-          teno::interface_flux<1, 0, false, teno::kFluxChar>(A.Uin, A.aux, A.ncell, cells, alpha, nal, S, out, fl,
-                                                             A.status);
+          teno::interface_flux<1, 0, false, teno::kFluxChar>(A.Uin, A.aux, A.ncell, cells, 0u, alpha, nal, S, out,
+                                                             fl, A.status);
         }
         s_F[tid][0] = out[0];
         s_F[tid][1] = out[1];
@@ -234,6 +236,7 @@ size_t teno_batch_workspace_bytes(const teno_batch* b) {
 
 teno_status teno_batch_prepare(const teno_batch* b, const int64_t* offsets_host, void* ws,
                                size_t ws_bytes, void* stream) {
+  if (b && b->bc == TENO_BC_REFLECTIVE) return TENO_ERR_UNSUPPORTED;
   if (!batch_ok(b) || !offsets_host) return TENO_ERR_INVALID_ARG;
   const BatchLayout L = batch_layout(b);
   if (!ws || !al(ws, kAlign) || ws_bytes < L.total || !is_dev(ws)) return TENO_ERR_WORKSPACE;
@@ -261,6 +264,7 @@ teno_status teno_rk3_step_batched(const teno_batch* b, const int64_t* offsets, c
                                   double* U, double* t_dev, const double* t_end_dev, double cfl,
                                   double dt_fixed, const teno_batch_tuning* tuning, void* ws,
                                   size_t ws_bytes, void* stream) {
+  if (b && b->bc == TENO_BC_REFLECTIVE) return TENO_ERR_UNSUPPORTED;
   if (!batch_ok(b) || !offsets || !dx || !U || !t_dev || !t_end_dev) return TENO_ERR_INVALID_ARG;
   if (!al(U, 16) || !al(offsets, 8) || !al(dx, 8) || !al(t_dev, 8) || !al(t_end_dev, 8))
     return TENO_ERR_INVALID_ARG;

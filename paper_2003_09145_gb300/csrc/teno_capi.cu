@@ -27,7 +27,8 @@ bool grid_ok(const teno_grid* g) {
     if (k >= g->ndim && g->n[k] != 1) return false;
     if (k < g->ndim) {
       if (!(g->dx[k] > 0.0) || !std::isfinite(g->dx[k])) return false;
-      if (g->bc[k] != TENO_BC_PERIODIC && g->bc[k] != TENO_BC_TRANSMISSIVE) return false;
+      if (g->bc[k] != TENO_BC_PERIODIC && g->bc[k] != TENO_BC_TRANSMISSIVE && g->bc[k] != TENO_BC_REFLECTIVE)
+        return false;
     }
   }
   if (!(g->gamma > 1.0) || !std::isfinite(g->gamma)) return false;

@@ -102,9 +102,13 @@ struct Grid {
   double inv_dx[3];
 };
 
-// Index of a (possibly ghost) cell along an axis of n cells: periodic wrap or
-// zero-gradient copy of the boundary cell.
-__device__ __forceinline__ int64_t ghost(int64_t i, int64_t n, int bc) {
+// Index of a (possibly ghost) cell along an axis of n cells: periodic wrap,
+// zero-gradient copy of the boundary cell, or (bc 2, reflecting) the mirror
+// image about the wall, cell -1-k for ghost k; `flip` is set when the point is
+// a mirror image carrying the reversed normal velocity (an odd number of
+// reflections -- more than one only on grids narrower than the stencil).
+__device__ __forceinline__ int64_t ghost(int64_t i, int64_t n, int bc, bool& flip) {
+  flip = false;
   if (bc == 0) {
     if (i < 0) i += n;
     else if (i >= n) i -= n;
@@ -113,7 +117,25 @@ __device__ __forceinline__ int64_t ghost(int64_t i, int64_t n, int bc) {
     else if (i >= n) i = i % n;
     return i;
   }
+  if (bc == 2) {
+    // at most 3 cells outside: a few reflections at most
+    while (i < 0 || i >= n) {
+      i = (i < 0) ? -1 - i : 2 * n - 1 - i;
+      flip = !flip;
+    }
+    return i;
+  }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+__device__ __forceinline__ int64_t ghost(int64_t i, int64_t n, int bc) {
+  bool flip;
+  return ghost(i, n, bc, flip);
+}
+
+// x with its sign reversed when f (an integer-pipe sign-bit flip)
+__device__ __forceinline__ double flip_sign(double x, bool f) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (static_cast<long long>(f) << 63));
 }
 
 // Non-negative doubles order like their bit patterns; used for max / compare

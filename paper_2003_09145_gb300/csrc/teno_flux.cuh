@@ -279,7 +279,7 @@ template <int NDIM, int DIR>
 __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__ U,
                                                       const double* __restrict__ aux,
                                                       const double* __restrict__ fh, int64_t ncell,
-                                                      const int64_t (&cells)[6],
+                                                      const int64_t (&cells)[6], unsigned flips,
                                                       const double (&alpha)[NDIM + 2],
                                                       const double (&nal)[NDIM + 2], const Scheme& S,
                                                       double (&out)[NDIM + 2], int* __restrict__ status) {
@@ -293,6 +293,8 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
       uu2[k] = aux[k * ncell + cells[2]];
       uu3[k] = aux[k * ncell + cells[3]];
     }
+    uu2[DIR] = flip_sign(uu2[DIR], (flips >> 2) & 1u);
+    uu3[DIR] = flip_sign(uu3[DIR], (flips >> 3) & 1u);
     roe_interface<NDIM, DIR>(aux[(NDIM + 1) * ncell + cells[2]], aux[(NDIM + 1) * ncell + cells[3]],
                              aux[(NDIM + 2) * ncell + cells[2]], aux[(NDIM + 2) * ncell + cells[3]], uu2, uu3,
                              S, R, status);
@@ -305,13 +307,17 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     const int64_t c = cells[j];
+    // a mirrored wall point: U with the normal momentum reversed, so u_d and
+    // every component of F_d/2 but the normal-momentum one change sign
+    const bool fj = (flips >> j) & 1u;
     double Uj[NVAR], Fhj[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) {
       Uj[v] = U[v * ncell + c];
-      Fhj[v] = fh[v * ncell + c];
+      Fhj[v] = flip_sign(fh[v * ncell + c], fj && v != 1 + DIR);
     }
-    const double unj = aux[DIR * ncell + c], pnj = aux[NDIM * ncell + c];
+    Uj[1 + DIR] = flip_sign(Uj[1 + DIR], fj);
+    const double unj = flip_sign(aux[DIR * ncell + c], fj), pnj = aux[NDIM * ncell + c];
     closed_point<NDIM>(j, Uj, Fhj, Ft, Ut);
     cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
   }
@@ -326,7 +332,9 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
 // Roe-averaged eigensystem of cells i, i+1, characteristic projection, global
 // Lax-Friedrichs split with the halved speeds `alpha` (nal = -2 alpha), TENO5-LAD
 // reconstruction of f^+ (cells i-2..i+2) and f^- (mirrored, i+3..i-1) for
-// every field, back-projection.  `fl` receives the flag bytes when WITH_FLAGS
+// every field, back-projection.  Bit j of `flips` marks stencil point j as a
+// mirrored wall point (reflecting boundary: normal velocity reversed).
+// `fl` receives the flag bytes when WITH_FLAGS
 // (without flags, bits 0..2 still hold the selections used).
 // MODE kFluxFull computes the flux.  kFluxSelect only wants the selections:
 // it returns without the flux when the certified test keeps every stencil.
@@ -344,7 +352,7 @@ constexpr unsigned kUndecided = 0xffu;
 template <int NDIM, int DIR, bool WITH_FLAGS, int MODE = kFluxFull>
 __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
                                                const double* __restrict__ aux,
-                                               int64_t ncell, const int64_t (&cells)[6],
+                                               int64_t ncell, const int64_t (&cells)[6], unsigned flips,
                                                const double (&alpha)[NDIM + 2],
                                                const double (&nal)[NDIM + 2],
                                                const Scheme& S, double (&out)[NDIM + 2],
@@ -358,9 +366,11 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const int64_t c = cells[j];
+      const bool fj = (flips >> j) & 1u;   // mirrored wall point
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Ux[j][v] = U[v * ncell + c];
-      un[j] = aux[DIR * ncell + c];
+      Ux[j][1 + DIR] = flip_sign(Ux[j][1 + DIR], fj);
+      un[j] = flip_sign(aux[DIR * ncell + c], fj);
       pn[j] = aux[NDIM * ncell + c];
       if (j == 2 || j == 3) {
         double* uu = (j == 2) ? uu2 : uu3;

@@ -152,11 +152,16 @@ __global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
                                     : i1 * G.n[0] + i0;
 
     int64_t cells[6];
+    unsigned flips = 0u;
 #pragma unroll
-    for (int j = 0; j < 6; ++j) cells[j] = base + ghost(id - 3 + j, nd, bcd) * stride_d;
+    for (int j = 0; j < 6; ++j) {
+      bool f;
+      cells[j] = base + ghost(id - 3 + j, nd, bcd, f) * stride_d;
+      flips |= unsigned(f) << j;
+    }
     double out[NVAR];
     unsigned fl[NVAR][2];
-    interface_flux<NDIM, DIR, WITH_FLAGS>(U, aux, ncell, cells, alpha, nal, S, out, fl, status);
+    interface_flux<NDIM, DIR, WITH_FLAGS>(U, aux, ncell, cells, flips, alpha, nal, S, out, fl, status);
     if (WITH_FLAGS) {
       // direction block offset is applied by the caller through `flags`
 #pragma unroll
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
 #endif
 
 template <int NDIM, int DIR>
-__device__ __forceinline__ void interface_cells(int64_t q, const Grid& G, int64_t (&cells)[6]) {
+__device__ __forceinline__ void interface_cells(int64_t q, const Grid& G, int64_t (&cells)[6], unsigned& flips) {
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
   const int64_t stride_d = (DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1]);
   const int64_t i0 = q % m0;
@@ -195,8 +200,13 @@ __device__ __forceinline__ void interface_cells(int64_t q, const Grid& G, int64_
   const int64_t base = (DIR == 0) ? (i2 * G.n[1] + i1) * G.n[0]
                      : (DIR == 1) ? i2 * G.n[1] * G.n[0] + i0
                                   : i1 * G.n[0] + i0;
+  flips = 0u;
 #pragma unroll
-  for (int j = 0; j < 6; ++j) cells[j] = base + ghost(id - 3 + j, G.n[DIR], G.bc[DIR]) * stride_d;
+  for (int j = 0; j < 6; ++j) {
+    bool f;
+    cells[j] = base + ghost(id - 3 + j, G.n[DIR], G.bc[DIR], f) * stride_d;
+    flips |= unsigned(f) << j;
+  }
 }
 
 template <int NDIM, int DIR>
@@ -228,10 +238,11 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nifc;
        q += (int64_t)gridDim.x * blockDim.x) {
     int64_t cells[6];
-    interface_cells<NDIM, DIR>(q, G, cells);
+    unsigned flips;
+    interface_cells<NDIM, DIR>(q, G, cells, flips);
     double out[NVAR];
     const bool done = interface_flux_closed<NDIM, DIR>(U, aux, fh + (int64_t)DIR * NVAR * G.ncell, G.ncell, cells,
-                                                       alpha, nal, S, out, status);
+                                                       flips, alpha, nal, S, out, status);
     if (done) {
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
@@ -264,10 +275,11 @@ __global__ void __launch_bounds__(128) flux_pending_kernel(
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = list[i];
     int64_t cells[6];
-    interface_cells<NDIM, DIR>(q, G, cells);
+    unsigned flips;
+    interface_cells<NDIM, DIR>(q, G, cells, flips);
     double out[NVAR];
     unsigned fl[NVAR][2];
-    interface_flux<NDIM, DIR, false, kFluxChar>(U, aux, G.ncell, cells, alpha, nal, S, out, fl, status);
+    interface_flux<NDIM, DIR, false, kFluxChar>(U, aux, G.ncell, cells, flips, alpha, nal, S, out, fl, status);
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
   }

@@ -60,7 +60,9 @@ bool grid_valid(const teno_grid* g) {
   for (int k = 0; k < 3; ++k) {
     if (g->n[k] < 1 || (k >= g->ndim && g->n[k] != 1)) return false;
     if (k < g->ndim && (!(g->dx[k] > 0.0) || !(g->dx[k] < 1e300))) return false;
-    if (k < g->ndim && g->bc[k] != TENO_BC_PERIODIC && g->bc[k] != TENO_BC_TRANSMISSIVE) return false;
+    if (k < g->ndim && g->bc[k] != TENO_BC_PERIODIC && g->bc[k] != TENO_BC_TRANSMISSIVE &&
+        g->bc[k] != TENO_BC_REFLECTIVE)
+      return false;
   }
   if (!(g->gamma > 1.0) || !(g->H > 0.0) || !(g->eps > 0.0)) return false;
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;

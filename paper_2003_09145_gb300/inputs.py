@@ -18,6 +18,7 @@ import numpy as np
 GAMMA = 1.4
 PERIODIC = 0
 TRANSMISSIVE = 1
+REFLECTIVE = 2
 
 
 def prim_to_cons(rho, vel, p, gamma: float = GAMMA) -> np.ndarray:
@@ -85,6 +86,18 @@ def lax_tube(n: int = 400, t_end: float = 0.13) -> Problem:
     use N = 400 at t = 0.13."""
     return shock_tube(n, left=(0.445, 0.698, 3.528), right=(0.5, 0.0, 0.571), a=-5.0, b=5.0,
                       x_jump=0.0, t_end=t_end, name="lax")
+
+
+def blast_waves(n: int = 400, t_end: float = 0.038) -> Problem:
+    """Two interacting blast waves (eq. 4.11) on [0, 1] with reflecting walls:
+    at rest, rho = 1, p = 1000 for x < 0.1, 0.01 for 0.1 <= x < 0.9 (the
+    printed middle range reads 0 <= x < 0.9), 100 for x >= 0.9; the paper's
+    figure uses N = 400 at t = 0.038."""
+    dx = 1.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+    return Problem("blast_waves", prim_to_cons(np.ones(n), [np.zeros(n)], p), (n,), (dx,), (REFLECTIVE,), t_end,
+                   x0=(0.0,))
 
 
 def shu_osher(n: int = 4096, t_end: float = 1.8) -> Problem:

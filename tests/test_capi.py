@@ -100,3 +100,16 @@ def test_scalar_mode_validation(lib):
     assert lib.teno_scalar_rhs(ctypes.byref(good), 1.0, 0, u.ctypes.data, None, ws.ctypes.data, nb, None) == 1
     assert lib.teno_scalar_rk3_step(ctypes.byref(good), 1.0, 0, u.ctypes.data, 0.01, ws.ctypes.data, nb,
                                     None) == 1
+
+
+def test_reflecting_walls_accepted_by_the_forward_path_only(lib):
+    """bc 2 (reflecting): the forward entry points size and accept it; the
+    adjoint and batched entry points answer TENO_ERR_UNSUPPORTED."""
+    from paper_2003_09145_gb300 import _lib
+    g = _lib.make_grid((32, 16), (0.1, 0.1), (2, 0))
+    assert lib.teno_workspace_bytes(ctypes.byref(g), _lib.OP_RK3) > 0
+    assert lib.teno_rhs_adjoint(ctypes.byref(g), None, None, None, None, 0, None) == 2
+    assert lib.teno_rk3_step_adjoint(ctypes.byref(g), None, 0.1, None, None, None, 0, None) == 2
+    b = _lib.TenoBatch(2, 10, 2, 1.4, 10.0, 4, 10, 1e-6)
+    off = (ctypes.c_int64 * 3)(0, 5, 10)
+    assert lib.teno_batch_prepare(ctypes.byref(b), off, None, 0, None) == 2

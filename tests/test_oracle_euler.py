@@ -249,3 +249,54 @@ def test_flags_layout_and_forced_replay(oracle):
     np.testing.assert_array_equal(R, R2)
     # alpha: acoustic speeds bound the convective one
     assert np.all(alpha[:, 0] >= 0) and np.all(alpha[:, -1] >= alpha[:, 1])
+
+
+# ---------------------------------------------------------------------------
+# Reflecting walls (bc 2; the two-blast-wave test of Sec. 4.2, eq. 4.11)
+# ---------------------------------------------------------------------------
+def _blast_prims(x):
+    """eq. 4.11 (middle range read as 0.1 <= x < 0.9): at rest, p = 1000 / 0.01 / 100."""
+    p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+    return np.ones_like(x), np.zeros_like(x), p
+
+
+def test_reflecting_constant_state_at_rest_is_steady(oracle):
+    n = 23
+    U = inputs.prim_to_cons(np.full(n, 1.3), [np.zeros(n)], np.full(n, 0.7))
+    R = oracle.euler_rhs(U, (n,), (1.0 / n,), (2,))
+    assert np.all(R == 0.0)
+
+
+@pytest.mark.parametrize("n", [5, 40])
+def test_reflecting_equals_mirrored_periodic(oracle, n):
+    """Data at rest on [0, 1] with reflecting walls, and the doubled periodic
+    domain [-1, 1] holding the data and its mirror image (velocity reversed):
+    every stencil sees the same values, and at rest the LF speeds agree, so the
+    right-hand sides on [0, 1] are equal bit for bit."""
+    x = (np.arange(n) + 0.5) / n
+    rho, u, p = _blast_prims(x)
+    p = p * (1.0 + 0.1 * np.sin(7.0 * x))            # break the piecewise constancy
+    U = inputs.prim_to_cons(rho, [u], p)
+    Ud = np.concatenate([U[:, ::-1] * np.array([[1.0], [-1.0], [1.0]]), U], axis=1)
+    R = oracle.euler_rhs(U, (n,), (1.0 / n,), (2,))
+    Rd = oracle.euler_rhs(np.ascontiguousarray(Ud), (2 * n,), (1.0 / n,), (0,))
+    np.testing.assert_array_equal(R, Rd[:, n:])
+
+
+def test_reflecting_in_x_periodic_in_y_equals_1d(oracle):
+    """A 2D grid varying along x only, reflecting in x and periodic in y, gives
+    the 1D reflecting right-hand side in every row (and zero y-momentum)."""
+    n, m = 30, 4
+    x = (np.arange(n) + 0.5) / n
+    rho, u, p = _blast_prims(x)
+    rho = rho + 0.2 * np.cos(3.0 * x)
+    u = 0.3 * np.sin(5.0 * x)
+    U1 = inputs.prim_to_cons(rho, [u], p)
+    U2 = inputs.prim_to_cons(np.tile(rho, (m, 1)), [np.tile(u, (m, 1)), np.zeros((m, n))], np.tile(p, (m, 1)))
+    R1 = oracle.euler_rhs(U1, (n,), (1.0 / n,), (2,))
+    R2 = oracle.euler_rhs(U2, (n, m), (1.0 / n, 0.25), (2, 0))
+    for j in range(m):
+        np.testing.assert_array_equal(R2[0][j], R1[0])
+        np.testing.assert_array_equal(R2[1][j], R1[1])
+        np.testing.assert_array_equal(R2[3][j], R1[2])
+    assert np.all(R2[2] == 0.0)
