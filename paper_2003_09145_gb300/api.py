@@ -177,6 +177,57 @@ class Solver:
         return device_status(self.ws)
 
 
+class HostPipeline:
+    """Advances states that live in pinned host memory, one SSP-RK3 step each:
+    item k is copied to the device on an H2D stream, stepped by ``solver`` on
+    the caller's current stream, and copied back on a D2H stream.  Two device
+    buffers let the copy-in of item k+1 and the copy-out of item k-1 overlap
+    the step of item k; CUDA events order the three streams, and no copy
+    starts before run() is called (an event on the current stream).  When
+    run() returns, the current stream waits for the last copy-out (nothing
+    synchronises the host)."""
+
+    def __init__(self, solver: "Solver", like: torch.Tensor):
+        self.solver = solver
+        dev = solver.device
+        self.buf = [torch.empty(like.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+        self.s_in = torch.cuda.Stream(dev)
+        self.s_out = torch.cuda.Stream(dev)
+        self.ev_in = [torch.cuda.Event() for _ in range(2)]
+        self.ev_step = [torch.cuda.Event() for _ in range(2)]
+        self.ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def run(self, host_in, host_out, t_end: float = float("inf"), dt_fixed: float = 0.0) -> None:
+        """host_in[k] -> one step -> host_out[k] for every k (pinned CPU float64
+        tensors shaped like the state; entries may repeat)."""
+        if len(host_in) != len(host_out):
+            raise ValueError("host_in and host_out differ in length")
+        comp = torch.cuda.current_stream(self.solver.device)
+        start = torch.cuda.Event()
+        start.record(comp)
+        self.s_in.wait_event(start)
+        self.s_out.wait_event(start)
+        used = [False, False]
+        for k, (hi, ho) in enumerate(zip(host_in, host_out)):
+            b = k % 2
+            with torch.cuda.stream(self.s_in):
+                if used[b]:
+                    self.s_in.wait_event(self.ev_out[b])     # buffer b has been copied out
+                self.buf[b].copy_(hi, non_blocking=True)
+                self.ev_in[b].record(self.s_in)
+            comp.wait_event(self.ev_in[b])
+            self.solver.step(self.buf[b], t_end, dt_fixed)
+            self.ev_step[b].record(comp)
+            with torch.cuda.stream(self.s_out):
+                self.s_out.wait_event(self.ev_step[b])
+                ho.copy_(self.buf[b], non_blocking=True)
+                self.ev_out[b].record(self.s_out)
+            used[b] = True
+        for b in range(2):
+            if used[b]:
+                comp.wait_event(self.ev_out[b])
+
+
 class BatchSolver:
     """Many independent 1D Euler problems of uneven length (one SoA state
     U[3][sum N]) advanced together by ``teno_rk3_step_batched``: one persistent

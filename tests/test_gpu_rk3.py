@@ -99,3 +99,26 @@ def test_nonphysical_state_is_reported(api):
     solver.step(U, 1.0, dt_fixed=1e-5)
     assert solver.status() == 4      # TENO_ERR_NONPHYSICAL
     assert solver.status() == 0      # cleared by the query
+
+
+def test_host_pipeline_equals_one_item_at_a_time(api):
+    """api.HostPipeline (copy-in, step and copy-out of neighbouring items
+    overlapped on three streams) gives, for every item, the state one step of
+    that item alone gives -- including items that repeat a host buffer."""
+    P = inputs.solenoidal_turbulence(n=20, t_end=10.0)
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    items = []
+    for k in range(5):
+        Uk = np.array(P.U0)
+        Uk[0] *= 1.0 + 0.01 * k
+        items.append(torch.from_numpy(np.ascontiguousarray(Uk)).pin_memory())
+    host_in = items + [items[1]]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    solver = api.Solver(grid)
+    pipe = api.HostPipeline(solver, torch.from_numpy(P.U0))
+    pipe.run(host_in, host_out)
+    torch.cuda.synchronize()
+    for hi, ho in zip(host_in, host_out):
+        U = hi.cuda()
+        api.Solver(grid).step(U)
+        assert torch.equal(U.cpu(), ho)
