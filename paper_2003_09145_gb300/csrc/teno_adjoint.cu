@@ -167,21 +167,6 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
        q += (int64_t)gridDim.x * blockDim.x) {
     int64_t id, base, cells[6];
     I.locate(q, G, id, base, cells);
-    double fout[NVAR];
-    unsigned fl[NVAR][2];
-    teno::interface_flux<NDIM, DIR, false, teno::kFluxCertify>(U, aux, I.ncell, cells, 0u, ha, nfa, S, fout, fl,
-                                                               status);
-    const bool kept = fl[0][0] != teno::kUndecided;
-    pending[q] = kept ? 0 : 1;
-    if (!kept) continue;
-    double Ut[NVAR];
-#pragma unroll
-    for (int v = 0; v < NVAR; ++v) {
-      double t = 0.0;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) t = fma(M[j], U[v * I.ncell + cells[j]], t);
-      Ut[v] = t;
-    }
     // Roe state from the cell pass's primitives (u/2, p/2, sqrt(rho), (E+p)/sqrt(rho))
     double ua[NDIM], ub[NDIM];
 #pragma unroll
@@ -193,6 +178,40 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     teno_adj::roe_from_primitives<NDIM>(aux[(NDIM + 1) * I.ncell + cells[2]], aux[(NDIM + 1) * I.ncell + cells[3]],
                                         aux[(NDIM + 2) * I.ncell + cells[2]], aux[(NDIM + 2) * I.ncell + cells[3]],
                                         ua, ub, S.gamma, R);
+    if (!(R.c2 > 0.0)) atomicOr(status, teno::kStatusNonphysical);
+    // The forward's certified FP32 test on this Roe state (it equals the
+    // forward's own to a few ulps, far inside the test's 2^-20 margins, so a
+    // pass proves the forward's binary64 selections keep every stencil), with
+    // U~ accumulated over the same stencil loads.
+    teno::RoeIfc<NDIM> Rf;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) Rf.u[k] = R.ut[k];
+    Rf.q2 = R.q2;
+    Rf.H = R.H;
+    Rf.cs = R.c;
+    Rf.b1 = R.b1;
+    Rf.hb1 = 0.5 * R.b1;
+    Rf.hb2 = 0.5 * R.b2;
+    Rf.hic = 0.5 * R.ic;
+    Rf.hud = 0.5 * R.ut[DIR];
+    teno::CertIfc<NDIM> C;
+    teno::cert_begin<NDIM>(Rf, ha, C);
+    double Ut[NVAR];
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) Ut[v] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      double Uj[NVAR];
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) {
+        Uj[v] = U[v * I.ncell + cells[j]];
+        Ut[v] = fma(M[j], Uj[v], Ut[v]);
+      }
+      teno::cert_point<NDIM, DIR>(j, Uj, aux[DIR * I.ncell + cells[j]], aux[NDIM * I.ncell + cells[j]], C);
+    }
+    const bool kept = S.keep_idx >= 0 && teno::cert_keep<NDIM>(C, S);
+    pending[q] = kept ? 0 : 1;
+    if (!kept) continue;
     double Fb[NVAR];
     interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
     double Utb[NVAR], roeA[NVAR], roeB[NVAR], ab[NVAR];
@@ -292,6 +311,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
 // for U~ = sum_j M_j U_j (indexed by a warp-uniform slot number).
 __constant__ double c_adjP[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
 __constant__ double c_adjM[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+// sum_j P_j (Rbar_{id+3-j} - Rbar_{id+2-j}) as one stencil on Rbar: the
+// weights of Rbar_{id+t} for t = -3, -2, -1, 1, 2, 3 (t = 0 cancels)
+__constant__ double c_adjW[6] = {-1.0 / 60.0, 9.0 / 60.0, -45.0 / 60.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
 
 // The share of interface q's slot j at the cell that slot maps to: the
 // pending interface's own contribution, or for a kept one M_j U~bar_q (plus
@@ -329,8 +351,11 @@ __device__ __forceinline__ void gather_slot(int j, int64_t q, int64_t qd, const 
 // (boundary ghost copies included): the pending interfaces' contributions,
 // M_j U~bar and the Roe terms of the kept ones, and A(U_c)^T applied once to
 // sum_j P_j Fbar of the kept ones.  Deterministic, no atomics.
+#ifndef TENO_ADJ_GATHER_MINBLOCKS
+#define TENO_ADJ_GATHER_MINBLOCKS 3   // 80 registers: measured fastest of 1-3
+#endif
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(256) adj_gather_kernel(const double* __restrict__ U,
+__global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_kernel(const double* __restrict__ U,
                                                          const double* __restrict__ Rbar, double scale,
                                                          const double* __restrict__ kb,
                                                          const double* __restrict__ contrib,
@@ -358,7 +383,31 @@ __global__ void __launch_bounds__(256) adj_gather_kernel(const double* __restric
     double acc[NVAR], Fsum[NVAR];
     for (int v = 0; v < NVAR; ++v) acc[v] = Fsum[v] = 0.0;
     const int idl = int(id), ndl = int(nd);
-    for (int j = 0; j < 6; ++j) {
+    // interior cell whose six interfaces (qd = id+3-j) are all kept: the
+    // P-weighted Fbar sum as one stencil on Rbar
+    bool fast = idl >= 3 && idl <= ndl - 4;
+    if (fast)
+      for (int j = 0; j < 6; ++j) fast = fast && pending[q0 + (int64_t)(idl + 3 - j) * sd] == 0;
+    if (fast) {
+      const int toff[6] = {-3, -2, -1, 1, 2, 3};
+      for (int v = 0; v < NVAR; ++v) {
+        const double* r = Rbar + v * ncell + c;
+        double f = 0.0;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) f = fma(c_adjW[t], r[toff[t] * cstride], f);
+        Fsum[v] = f;
+      }
+      for (int j = 0; j < 6; ++j) {
+        const int64_t q = q0 + (int64_t)(idl + 3 - j) * sd;
+        const double Mj = c_adjM[j];
+        for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
+        if (j == 2)
+          for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(NVAR + v) * nifc + q];
+        if (j == 3)
+          for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+      }
+    }
+    for (int j = 0; j < 6 && !fast; ++j) {
       // interfaces qd in [0, nd] whose point j, ghost(qd - 3 + j), is cell id
       if (bc == 0) {
         // x = qd - 3 + j ranges over [j - 3, nd + j - 3]; x = id (mod nd)
