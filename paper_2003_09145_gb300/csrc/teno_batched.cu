@@ -10,10 +10,10 @@
 //       the problem's LF speeds (block reduction) and, in stage 1, the CFL
 //       step and the new time;
 //   (B) sweeps the problem in tiles of BLOCK - 1 cells: one thread per
-//       interface flux (the same device code as teno_rhs: the certified
-//       closed form, else the characteristic path), the fluxes of a tile in
-//       shared memory, then the conservative difference fused with the
-//       stage update.
+//       interface flux with the same device code as teno_rhs (the certified
+//       closed form; the faces it leaves pending are gathered into the first
+//       lanes for the characteristic path), the fluxes of a tile in shared
+//       memory, then the conservative difference fused with the stage update.
 // No grid-wide synchronisation is needed: every dependency is inside a
 // problem, and a problem never spans two CTAs.  The arithmetic is exactly
 // that of teno_rk3_step on each problem alone, so results agree bit for bit.
@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
   __shared__ double s_alpha[3];
   __shared__ double s_dt, s_idx;
   __shared__ double s_F[BLOCK][3];
+  __shared__ int s_pend[BLOCK];   // tile faces the certified test leaves pending
+  __shared__ int s_npend;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (;;) {
@@ -145,24 +147,41 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
 
     // (B) fluxes tile by tile, difference fused with the stage update
     for (int64_t i0 = 0; i0 < n; i0 += BLOCK - 1) {
+      // the grid path's two passes inside the tile: the certified closed form
+      // for every face, then the faces it leaves pending, gathered into the
+      // first lanes so that only ceil(pending / 32) warps take the
+      // characteristic path (periodic or transmissive ends: no mirrored points)
+      if (tid == 0) s_npend = 0;
+      __syncthreads();
       const int64_t face = i0 + tid;
       if (face <= n) {
         int64_t cells[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) cells[j] = off + teno::ghost(face - 3 + j, n, A.bc);
-        // the certified closed form, else the characteristic path (the grid
-        // path's two passes, in one thread)
         double out[3];
-        // (periodic or transmissive ends only: no mirrored points)
-        if (!teno::interface_flux_closed<1, 0>(A.Uin, A.aux, A.fh, A.ncell, cells, 0u, alpha, nal, S, out,
-                                               A.status)) {
-          unsigned fl[3][2];
-          teno::interface_flux<1, 0, false, teno::kFluxChar>(A.Uin, A.aux, A.ncell, cells, 0u, alpha, nal, S, out,
-                                                             fl, A.status);
+        if (teno::interface_flux_closed<1, 0>(A.Uin, A.aux, A.fh, A.ncell, cells, 0u, alpha, nal, S, out,
+                                              A.status)) {
+          s_F[tid][0] = out[0];
+          s_F[tid][1] = out[1];
+          s_F[tid][2] = out[2];
+        } else {
+          s_pend[atomicAdd(&s_npend, 1)] = tid;
         }
-        s_F[tid][0] = out[0];
-        s_F[tid][1] = out[1];
-        s_F[tid][2] = out[2];
+      }
+      __syncthreads();
+      if (tid < s_npend) {
+        const int t = s_pend[tid];
+        const int64_t f2 = i0 + t;
+        int64_t cells[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) cells[j] = off + teno::ghost(f2 - 3 + j, n, A.bc);
+        double out[3];
+        unsigned fl[3][2];
+        teno::interface_flux<1, 0, false, teno::kFluxChar>(A.Uin, A.aux, A.ncell, cells, 0u, alpha, nal, S, out, fl,
+                                                           A.status);
+        s_F[t][0] = out[0];
+        s_F[t][1] = out[1];
+        s_F[t][2] = out[2];
       }
       __syncthreads();
       const int64_t cell = i0 + tid;
