@@ -224,7 +224,10 @@ __device__ __forceinline__ void half_speeds(const unsigned long long* __restrict
   for (int f = 0; f < NVAR; ++f) nal[f] = -2.0 * alpha[f];
 }
 
-template <int NDIM, int DIR>
+// REFLECT: the sweep direction has a reflecting wall, so stencil points may be
+// mirrored; without one the mirror flags are the constant 0 and their sign
+// flips fold away.
+template <int NDIM, int DIR, bool REFLECT>
 __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel(
     const double* __restrict__ U, const double* __restrict__ aux, const double* __restrict__ fh,
     const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
     interface_cells<NDIM, DIR>(q, G, cells, flips);
     double out[NVAR];
     const bool done = interface_flux_closed<NDIM, DIR>(U, aux, fh + (int64_t)DIR * NVAR * G.ncell, G.ncell, cells,
-                                                       flips, alpha, nal, S, out, status);
+                                                       REFLECT ? flips : 0u, alpha, nal, S, out, status);
     if (done) {
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
@@ -455,7 +458,11 @@ static int flux_launch(int blocks, int threads, int pblocks, cudaStream_t st, co
     flux_kernel<NDIM, DIR, false><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
     return 1;
   }
-  flux_closed_kernel<NDIM, DIR><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
+  if (G.bc[DIR] == TENO_BC_REFLECTIVE)
+    flux_closed_kernel<NDIM, DIR, true><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
+  else
+    flux_closed_kernel<NDIM, DIR, false><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G,
+                                                                     S);
   flux_pending_kernel<NDIM, DIR><<<pblocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
   return 2;
 }
