@@ -39,7 +39,8 @@ FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
 #   closed form F~ + a_mid U~ + acoustic corrections -- Roe 34, per point
 #   20 (the P-weighted sum of the cell pass's F/2 and the M-weighted sum of
 #   U), projection of U~ 20, corrections and output 30: 204.  (Forming
-#   F_d/2 costs 9 flops per cell and direction in the cell pass.)
+#   F_d/2 costs 8 flops per cell and direction in the cell pass; its mass
+#   component m_d/2 is not formed: the P-weighted sum takes m_d itself.)
 # * Otherwise the characteristic path: Roe 34, projection 6 x 20, split 6 x 28,
 #   sum 5, back-projection 21 (= 348), plus per scalar reconstruction 9 when
 #   its own FP32 pre-test keeps every stencil, else 38 for the binary64

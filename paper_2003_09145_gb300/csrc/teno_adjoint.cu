@@ -556,7 +556,7 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   if (op == TENO_OP_RK3_ADJOINT) {
     // half fluxes of the recomputed forward stages (two-pass fluxes)
     L.fh = off;
-    off += round_up(sizeof(double) * g->ndim * nvar * ncell);
+    off += round_up(sizeof(double) * g->ndim * (nvar - 1) * ncell);
     // forward recomputation (R, U1, U2) and the stage adjoints (B1, B2)
     L.R = off;
     off += round_up(sizeof(double) * nvar * ncell);

@@ -41,7 +41,7 @@ struct BatchArgs {
   const double* Uk;    // U1 (stage 2) or U2 (stage 3)
   double* Uout;        // U1, U2 or U^{n+1}
   double* aux;         // [4][ncell]
-  double* fh;          // [3][ncell]: F/2 of every cell (eq. 4.7)
+  double* fh;          // [2][ncell]: F/2 of every cell (eq. 4.7), momentum and energy
   const int64_t* offsets;
   const double* dx;
   double* t;
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
       double Fh[3];
       teno::cell_flux_half<1, 0>(Uc, A.aux[c], A.aux[A.ncell + c], Fh);
 #pragma unroll
-      for (int v = 0; v < 3; ++v) A.fh[v * A.ncell + c] = Fh[v];
+      for (int v = 1; v < 3; ++v) A.fh[(v - 1) * A.ncell + c] = Fh[v];
       b0 = teno::max_abs_bits(b0, __dsub_rn(u[0], cs));
       b1 = teno::max_abs_bits(b1, u[0]);
       b2 = teno::max_abs_bits(b2, __dadd_rn(u[0], cs));
@@ -224,7 +224,7 @@ BatchLayout batch_layout(const teno_batch* b) {
   L.aux = off;
   off += round_up(sizeof(double) * 4 * size_t(b->ncell));
   L.fh = off;
-  off += round_up(sizeof(double) * 3 * size_t(b->ncell));
+  off += round_up(sizeof(double) * 2 * size_t(b->ncell));
   L.U1 = off;
   off += round_up(sizeof(double) * 3 * size_t(b->ncell));
   L.U2 = off;

@@ -65,8 +65,8 @@ Layout layout_of(const teno_grid* g, int op) {
   size_t off = kHeader;
   L.aux = off;
   off += round_up(sizeof(double) * (g->ndim + 3) * ncell);
-  L.fh = off;   // half physical fluxes F_d/2 per cell and direction
-  off += round_up(sizeof(double) * g->ndim * nvar * ncell);
+  L.fh = off;   // half physical fluxes F_d/2 per cell and direction (no mass component)
+  off += round_up(sizeof(double) * g->ndim * (nvar - 1) * ncell);
   L.fhat = off;
   off += round_up(sizeof(double) * nvar * size_t(maxifc));
   L.list = off;

@@ -221,28 +221,34 @@ __device__ __forceinline__ bool cert_keep(const CertIfc<NDIM>& C, const Scheme& 
 // cell_flux_half gives F_d(U)/2 of one cell (eq. 4.7) from its half u_d and
 // half p -- the grid path stores it per cell and direction, the one-pass
 // path forms it per stencil point, with the same rounding; closed_point adds
-// point j to F~ and U~ (sums start at zero); closed_out forms F^.
+// point j to F~ and U~ (sums start at zero); closed_out forms F^.  The mass
+// component of F_d/2 is m_d/2: closed_point takes it as m_d with the weights
+// P/2 (the same products, since halving is exact), so the half fluxes need
+// only the momentum and energy components (v = 1..nvar-1).
 // ---------------------------------------------------------------------------
 template <int NDIM, int DIR>
 __device__ __forceinline__ void cell_flux_half(const double (&Uc)[NDIM + 2], double un, double pn,
                                                double (&Fh)[NDIM + 2]) {
   constexpr int NVAR = NDIM + 2;
-  // F/2 = (u_d/2) U + (p/2) (0, e_d, u_d)
+  // F/2 = (u_d/2) U + (p/2) (0, e_d, u_d); the mass component m_d/2
+  Fh[0] = 0.5 * Uc[1 + DIR];
 #pragma unroll
-  for (int v = 0; v < NVAR; ++v) Fh[v] = un * Uc[v];
+  for (int v = 1; v < NVAR; ++v) Fh[v] = un * Uc[v];
   Fh[1 + DIR] += pn;
   Fh[NVAR - 1] = fma(pn, un + un, Fh[NVAR - 1]);
 }
 
-template <int NDIM>
+// (Fhj[0] is not read: the mass term is P[j] m_d = (P2[j]/2) m_d.)
+template <int NDIM, int DIR>
 __device__ __forceinline__ void closed_point(int j, const double (&Uj)[NDIM + 2], const double (&Fhj)[NDIM + 2],
                                              double (&Ft)[NDIM + 2], double (&Ut)[NDIM + 2]) {
   constexpr int NVAR = NDIM + 2;
   const double P2[6] = {1.0 / 30.0, -8.0 / 30.0, 37.0 / 30.0, 37.0 / 30.0, -8.0 / 30.0, 1.0 / 30.0};
+  const double P1[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
   const double Mw[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) {
-    Ft[v] = fma(P2[j], Fhj[v], Ft[v]);
+    Ft[v] = v == 0 ? fma(P1[j], Uj[1 + DIR], Ft[0]) : fma(P2[j], Fhj[v], Ft[v]);
     Ut[v] = fma(Mw[j], Uj[v], Ut[v]);
   }
 }
@@ -272,8 +278,9 @@ __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const d
 // The certified closed form alone, one stencil point at a time (each
 // point's state is dead once it has entered F~, U~ and the FP32 test, which
 // keeps the register footprint small), with the per-cell F_DIR/2 of the cell
-// pass (`fh`, [nvar][ncell]).  Returns false, with `out` unwritten, when the
-// test does not keep every stencil; otherwise `out` equals interface_flux's.
+// pass (`fh`, momentum and energy components only: [nvar - 1][ncell]).
+// Returns false, with `out` unwritten, when the test does not keep every
+// stencil; otherwise `out` equals interface_flux's.
 // ---------------------------------------------------------------------------
 template <int NDIM, int DIR>
 __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__ U,
@@ -312,13 +319,13 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
     const bool fj = (flips >> j) & 1u;
     double Uj[NVAR], Fhj[NVAR];
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) {
-      Uj[v] = U[v * ncell + c];
-      Fhj[v] = flip_sign(fh[v * ncell + c], fj && v != 1 + DIR);
-    }
+    for (int v = 0; v < NVAR; ++v) Uj[v] = U[v * ncell + c];
+    Fhj[0] = 0.0;   // unused: the mass term comes from m_d
+#pragma unroll
+    for (int v = 1; v < NVAR; ++v) Fhj[v] = flip_sign(fh[(v - 1) * ncell + c], fj && v != 1 + DIR);
     Uj[1 + DIR] = flip_sign(Uj[1 + DIR], fj);
     const double unj = flip_sign(aux[DIR * ncell + c], fj), pnj = aux[NDIM * ncell + c];
-    closed_point<NDIM>(j, Uj, Fhj, Ft, Ut);
+    closed_point<NDIM, DIR>(j, Uj, Fhj, Ft, Ut);
     cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
   }
   if (!cert_keep<NDIM>(C, S)) return false;
@@ -411,7 +418,7 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
         for (int j = 0; j < 6; ++j) {
           double Fhj[NVAR];
           cell_flux_half<NDIM, DIR>(Ux[j], un[j], pn[j], Fhj);
-          closed_point<NDIM>(j, Ux[j], Fhj, Ft, Ut);
+          closed_point<NDIM, DIR>(j, Ux[j], Fhj, Ft, Ut);
         }
         closed_out<NDIM, DIR>(Ft, Ut, R, nal, out);
 #pragma unroll

@@ -30,11 +30,12 @@ namespace teno {
 // to their maxima over all cells.
 // aux layout: [ndim + 3][ncell]: u_0/2..u_{ndim-1}/2, p/2, sqrt(rho),
 // (E+p)/sqrt(rho).  With `fh`, also the half physical fluxes F_d/2 (eq. 4.7)
-// of every direction, [ndim][nvar][ncell], for the closed-form flux pass.
+// of every direction, momentum and energy components only (the mass one is
+// m_d/2), [ndim][nvar - 1][ncell], for the closed-form flux pass.
 // alpha layout (bit patterns of non-negative doubles): [ndim][3] =
 // max|u_d - c|, max|u_d|, max|u_d + c|.
 // ---------------------------------------------------------------------------
-// F_d/2 of cell c for d = D..NDIM-1 into fh[d][v][c].
+// F_d/2 of cell c for d = D..NDIM-1 into fh[d][v - 1][c], v = 1..nvar-1.
 template <int NDIM, int D>
 __device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], const double* __restrict__ aux,
                                                 double pn, double* __restrict__ fh, int64_t ncell, int64_t c) {
@@ -43,7 +44,7 @@ __device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], co
     double Fh[NVAR];
     cell_flux_half<NDIM, D>(Uc, aux[D * ncell + c], pn, Fh);
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) fh[(int64_t)(D * NVAR + v) * ncell + c] = Fh[v];
+    for (int v = 1; v < NVAR; ++v) fh[(int64_t)(D * (NVAR - 1) + v - 1) * ncell + c] = Fh[v];
     store_flux_half<NDIM, D + 1>(Uc, aux, pn, fh, ncell, c);
   }
 }
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
     unsigned flips;
     interface_cells<NDIM, DIR>(q, G, cells, flips);
     double out[NVAR];
-    const bool done = interface_flux_closed<NDIM, DIR>(U, aux, fh + (int64_t)DIR * NVAR * G.ncell, G.ncell, cells,
+    const bool done = interface_flux_closed<NDIM, DIR>(U, aux, fh + (int64_t)DIR * (NVAR - 1) * G.ncell, G.ncell, cells,
                                                        REFLECT ? flips : 0u, alpha, nal, S, out, status);
     if (done) {
 #pragma unroll
@@ -308,7 +309,15 @@ __global__ void __launch_bounds__(256) diff_kernel(
   double dt = 0.0;
   if (mode >= 2) {
     dt = *dt_ptr;
-    if (!(dt > 0.0)) return;  // t >= t_end: the state is left unchanged
+    if (!(dt > 0.0)) {
+      // t >= t_end: the state is left unchanged.  The stage buffers U1, U2
+      // take U^n, so that the stages after this one read defined values.
+      if (mode <= 3)
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < NVAR * ncell;
+             e += (int64_t)gridDim.x * blockDim.x)
+          Uout[e] = Un[e];
+      return;
+    }
   }
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {

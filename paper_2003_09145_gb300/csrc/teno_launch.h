@@ -14,7 +14,8 @@ namespace teno {
 Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u);
 
 // Primitives (aux) and LF speeds of every cell; with `fh` (nullable) also
-// the half physical fluxes F_d/2, [ndim][nvar][ncell].
+// the half physical fluxes F_d/2 without their mass component,
+// [ndim][nvar - 1][ncell].
 cudaError_t launch_cell(int ndim, const double* U, double* aux, double* fh,
                         unsigned long long* alpha, int* status, int64_t ncell,
                         double gamma, int nsm, cudaStream_t st);

@@ -87,6 +87,22 @@ def test_clip_and_no_op_after_t_end(api):
     solver.step(U, t_end)
     assert solver.dt.item() == 0.0
     assert torch.equal(before, U)
+    assert solver.status() == 0
+
+
+def test_no_op_first_step_reports_no_error(api):
+    """A first step already at t_end (dt = 0) leaves U unchanged and raises
+    no status: the stages that follow a skipped stage read U^n, not the
+    uninitialised stage buffers of a fresh workspace."""
+    P = inputs.shock_tube(64)
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    solver = api.Solver(grid, cfl=0.5)
+    U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
+    before = U.clone()
+    solver.step(U, 0.0)
+    assert solver.dt.item() == 0.0
+    assert torch.equal(before, U)
+    assert solver.status() == 0
 
 
 def test_nonphysical_state_is_reported(api):
