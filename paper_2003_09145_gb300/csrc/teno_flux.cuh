@@ -230,12 +230,13 @@ template <int NDIM, int DIR>
 __device__ __forceinline__ void cell_flux_half(const double (&Uc)[NDIM + 2], double un, double pn,
                                                double (&Fh)[NDIM + 2]) {
   constexpr int NVAR = NDIM + 2;
-  // F/2 = (u_d/2) U + (p/2) (0, e_d, u_d); the mass component m_d/2
+  // F/2 = (u_d/2) U + (p/2) (0, e_d, u_d), per component: mass m_d/2,
+  // momentum (u_d/2) m_k (+ p/2 for k = d), energy (u_d/2)(E + p); E + p
+  // is formed as E + 2 (p/2), which doubles exactly
   Fh[0] = 0.5 * Uc[1 + DIR];
 #pragma unroll
-  for (int v = 1; v < NVAR; ++v) Fh[v] = un * Uc[v];
-  Fh[1 + DIR] += pn;
-  Fh[NVAR - 1] = fma(pn, un + un, Fh[NVAR - 1]);
+  for (int k = 0; k < NDIM; ++k) Fh[1 + k] = k == DIR ? fma(un, Uc[1 + k], pn) : un * Uc[1 + k];
+  Fh[NVAR - 1] = un * fma(2.0, pn, Uc[NVAR - 1]);
 }
 
 // (Fhj[0] is not read: the mass term is P[j] m_d = (P2[j]/2) m_d.)

@@ -293,14 +293,18 @@ __global__ void __launch_bounds__(128) flux_pending_kernel(
 // Conservative difference (eq. 2.2) and SSP-RK3 stage update (eq. 4.1-4.3).
 // mode: 0 R = d; 1 R += d; 2 U1 = Un + dt (R + d); 3 U2 = 3/4 Un + 1/4 U1 +
 // 1/4 dt (R + d); 4 Un <- 1/3 Un + 2/3 U2 + 2/3 dt (R + d).  `acc` selects
-// whether R already holds the contributions of earlier directions.
+// whether R already holds the contributions of earlier directions; it does
+// exactly for the directions after the first (DIR > 0).  MODE is a template
+// argument (0 and 1 share one form) so that every load of a cell is issued
+// before its stores.
 // ---------------------------------------------------------------------------
-template <int NDIM, int DIR>
+template <int NDIM, int DIR, int MODE>
 __global__ void __launch_bounds__(256) diff_kernel(
     const double* __restrict__ Fhat, double* __restrict__ R,
     const double* __restrict__ Un, const double* __restrict__ Uk,
-    double* __restrict__ Uout, const double* __restrict__ dt_ptr, Grid G,
-    int mode, int acc) {
+    double* __restrict__ Uout, const double* __restrict__ dt_ptr, Grid G) {
+  constexpr int mode = MODE;
+  constexpr bool acc = DIR > 0;
   constexpr int NVAR = NDIM + 2;
   const int64_t ncell = G.ncell;
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
@@ -319,21 +323,36 @@ __global__ void __launch_bounds__(256) diff_kernel(
       return;
     }
   }
+  // The interface left of cell c = (i2 n1 + i1) n0 + i0 is (i2 m1 + i1) m0 + i0:
+  // x: c plus the row index c / n0 (one more interface per row); y: c plus
+  // n0 times the plane index c / (n0 n1); z: c itself.
+  const int64_t span = DIR == 0 ? G.n[0] : G.n[0] * G.n[1];
+  const int64_t shift = DIR == 0 ? 1 : G.n[0];
+  const bool narrow = ncell <= int64_t(UINT32_MAX);   // 32-bit division suffices
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i0 = c % G.n[0];
-    const int64_t r = c / G.n[0];
-    const int64_t i1 = r % G.n[1];
-    const int64_t i2 = r / G.n[1];
-    const int64_t left = (i2 * m1 + i1) * m0 + i0;
+    int64_t left = c;
+    if (DIR < 2) {
+      const int64_t q = narrow ? int64_t(uint32_t(c) / uint32_t(span)) : c / span;
+      left += q * shift;
+    }
     const int64_t right = left + (DIR == 0 ? 1 : (DIR == 1 ? m0 : m0 * m1));
+    // all loads of the cell first (the branches on mode and acc are uniform)
+    double d[NVAR];
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) {
-      double d = (Fhat[v * nifc + left] - Fhat[v * nifc + right]) * idx;
-      const int64_t e = v * ncell + c;
-      if (acc) d += R[e];
-      if (mode <= 1) R[e] = d;
-      else Uout[e] = stage_value(mode, dt, d, Un, Uk, e);
+    for (int v = 0; v < NVAR; ++v) d[v] = (Fhat[v * nifc + left] - Fhat[v * nifc + right]) * idx;
+    if (acc)
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) d[v] += R[v * ncell + c];
+    if (mode <= 1) {
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) R[v * ncell + c] = d[v];
+    } else {
+      double o[NVAR];
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) o[v] = stage_value(mode, dt, d[v], Un, Uk, v * ncell + c);
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) Uout[v * ncell + c] = o[v];
     }
   }
 }
@@ -506,13 +525,21 @@ template <int NDIM, int DIR>
 static void diff_launch(int blocks, int threads, cudaStream_t st, const double* Fhat,
                         double* R, const double* Un, const double* Uk, double* Uout,
                         const double* dt, const Grid& G, int mode, int acc) {
-  diff_kernel<NDIM, DIR><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
+  (void)acc;   // acc == (DIR > 0), checked by launch_diff
+  switch (mode) {
+    case 0:
+    case 1: diff_kernel<NDIM, DIR, 1><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
+    case 2: diff_kernel<NDIM, DIR, 2><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
+    case 3: diff_kernel<NDIM, DIR, 3><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
+    default: diff_kernel<NDIM, DIR, 4><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
+  }
 }
 
 cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
                         const double* Un, const double* Uk, double* Uout,
                         const double* dt, const Grid& G, int mode, int acc,
                         int nsm, cudaStream_t st) {
+  if ((acc != 0) != (dir > 0) || mode < 0 || mode > 4) return cudaErrorInvalidValue;
   const int threads = 256;
   const int blocks = blocks_for(G.ncell, threads, nsm * 16);
   if (ndim == 1) diff_launch<1, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
