@@ -334,6 +334,16 @@ teno_status teno_timer_end(double* ms, int64_t* launches);
 teno_status teno_probe_fp64(double* out_dev, int64_t blocks, int64_t iters,
                             void* stream);
 
+/*
+ * teno_probe_recip -- test aid (no counterpart in the paper): for the n
+ * doubles x_dev (device) writes, to out_dev (device, 2 n doubles), the
+ * library's seeded reciprocal (the one the Roe average uses), then CUDA's
+ * 1.0 / x, n entries each.  TENO_ERR_INVALID_ARG for null pointers or n
+ * outside 1..2^32.
+ */
+teno_status teno_probe_recip(const double* x_dev, double* out_dev, int64_t n,
+                             void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* teno_status_string(teno_status s);
 

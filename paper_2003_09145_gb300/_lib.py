@@ -92,6 +92,7 @@ SIGNATURES = [
     ("teno_timer_begin", ctypes.c_int, []),
     ("teno_timer_end", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     ("teno_probe_fp64", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP]),
+    ("teno_probe_recip", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
     ("teno_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("teno_abi_version", ctypes.c_int, []),
 ]

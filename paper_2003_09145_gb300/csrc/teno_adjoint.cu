@@ -49,11 +49,11 @@ __global__ void argmax_kernel(const double* __restrict__ U, const unsigned long 
                               double* __restrict__ scratch_aux) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
-    double u[NDIM], cs;
-    teno::cell_primitives<NDIM>(U, ncell, c, gamma, scratch_aux, u, cs);
+    double uh[NDIM], cs;
+    teno::cell_primitives<NDIM>(U, ncell, c, gamma, scratch_aux, uh, cs);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      const double lam[3] = {fabs(__dsub_rn(u[d], cs)), fabs(u[d]), fabs(__dadd_rn(u[d], cs))};
+      const double lam[3] = {fabs(fma(2.0, uh[d], -cs)), fabs(2.0 * uh[d]), fabs(fma(2.0, uh[d], cs))};
 #pragma unroll
       for (int k = 0; k < 3; ++k)
         if (teno::dbits(lam[k]) == alpha[d * 3 + k]) atomicMin(&argidx[d * 3 + k], (unsigned long long)c);

@@ -83,18 +83,20 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
     unsigned long long b0 = 0ull, b1 = 0ull, b2 = 0ull;   // bit patterns of the maxima
     bool bad = false;
     for (int64_t i = tid; i < n; i += BLOCK) {
-      double u[1], cs;
+      double uh[1], cs;
       const int64_t c = off + i;
-      if (!teno::cell_primitives<1>(A.Uin, A.ncell, c, A.gamma, A.aux, u, cs)) bad = true;
+      if (!teno::cell_primitives<1>(A.Uin, A.ncell, c, A.gamma, A.aux, uh, cs)) bad = true;
       const double Uc[3] = {A.Uin[c], A.Uin[A.ncell + c], A.Uin[2 * A.ncell + c]};
       double Fh[3];
       teno::cell_flux_half<1, 0>(Uc, A.aux[c], A.aux[A.ncell + c], Fh);
 #pragma unroll
       for (int v = 1; v < 3; ++v) A.fh[(v - 1) * A.ncell + c] = Fh[v];
-      b0 = teno::max_abs_bits(b0, __dsub_rn(u[0], cs));
-      b1 = teno::max_abs_bits(b1, u[0]);
-      b2 = teno::max_abs_bits(b2, __dadd_rn(u[0], cs));
+      // u -+ c from u/2 with one rounding; max|u| kept as max|u/2|
+      b0 = teno::max_abs_bits(b0, fma(2.0, uh[0], -cs));
+      b1 = teno::max_abs_bits(b1, uh[0]);
+      b2 = teno::max_abs_bits(b2, fma(2.0, uh[0], cs));
     }
+    b1 = teno::dbits(2.0 * __longlong_as_double(static_cast<long long>(b1)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long w0 = __shfl_xor_sync(0xffffffffu, b0, o);

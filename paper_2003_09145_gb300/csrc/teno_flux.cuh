@@ -86,7 +86,7 @@ template <int NDIM, int DIR>
 __device__ __forceinline__ void roe_interface(double sr2, double sr3, double sh2, double sh3,
                                               const double (&uu2)[NDIM], const double (&uu3)[NDIM],
                                               const Scheme& S, RoeIfc<NDIM>& R, int* __restrict__ status) {
-  const double inv2 = 2.0 / (sr2 + sr3);
+  const double inv2 = 2.0 * recip_pos(sr2 + sr3);
   R.q2 = 0.0;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
@@ -495,37 +495,40 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
 
 // ---------------------------------------------------------------------------
 // Primitive variables of cell c from one reciprocal square root:
-// 1/sqrt(rho), sqrt(rho) = rho/sqrt(rho), 1/rho = (1/sqrt(rho))^2, u = m/rho,
-// p = (gamma-1)(E - rho |u|^2 / 2) (eq. 4.7), c = sqrt(gamma p / rho).  Writes
-// the aux entries (u_k/2, p/2, sqrt(rho), (E+p)/sqrt(rho)) and returns u and c;
-// false if the state is not physical (rho <= 0, p <= 0 or non-finite).
+// 1/sqrt(rho), sqrt(rho) = rho/sqrt(rho), 1/(2 rho) = (1/sqrt(rho))^2 / 2,
+// u/2 = m/(2 rho), p = (gamma-1)(E - 2 rho |u/2|^2) (eq. 4.7),
+// c = sqrt(gamma p / rho).  Writes the aux entries (u_k/2, p/2, sqrt(rho),
+// (E+p)/sqrt(rho)) and returns uh = u/2 and c; false if the state is not
+// physical (rho <= 0, p <= 0 or non-finite).  Working with u/2 saves the
+// halving multiplies; every value equals the u-based evaluation's bit for
+// bit, since the factors of 2 are exact.
 // ---------------------------------------------------------------------------
 template <int NDIM>
 __device__ __forceinline__ bool cell_primitives(const double* __restrict__ U, int64_t ncell,
                                                 int64_t c, double gamma,
                                                 double* __restrict__ aux,
-                                                double (&u)[NDIM], double& cs) {
+                                                double (&uh)[NDIM], double& cs) {
   constexpr int NVAR = NDIM + 2;
   const double rho = U[c];
   const double E = U[(NVAR - 1) * ncell + c];
   const double isr = rsqrt(rho);
   const double sr = rho * isr;
-  const double r = isr * isr;
-  double q2 = 0.0;
+  const double hr = (0.5 * isr) * isr;
+  double q2h = 0.0;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
-    u[k] = U[(1 + k) * ncell + c] * r;
-    q2 = fma(u[k], u[k], q2);
+    uh[k] = U[(1 + k) * ncell + c] * hr;
+    q2h = fma(uh[k], uh[k], q2h);
   }
-  const double p = (gamma - 1.0) * fma(-0.5 * rho, q2, E);
-  const double gpr = gamma * p * r;
+  const double p = (gamma - 1.0) * fma(-2.0 * rho, q2h, E);
+  const double gpr = (2.0 * gamma) * p * hr;
   cs = gpr * rsqrt(gpr);
 #pragma unroll
-  for (int k = 0; k < NDIM; ++k) aux[k * ncell + c] = 0.5 * u[k];
+  for (int k = 0; k < NDIM; ++k) aux[k * ncell + c] = uh[k];
   aux[NDIM * ncell + c] = 0.5 * p;
   aux[(NDIM + 1) * ncell + c] = sr;
   aux[(NDIM + 2) * ncell + c] = (E + p) * isr;
-  return pos_finite(rho) && pos_finite(p) && is_finite(E) && is_finite(q2) && pos_finite(gpr);
+  return pos_finite(rho) && pos_finite(p) && is_finite(E) && is_finite(q2h) && pos_finite(gpr);
 }
 
 // SSP-RK3 stage value (eq. 4.1-4.3) of element e from d = L(U^(k))_e:

@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(256, 3) cell_kernel(const double* __restrict__
   bool bad = false;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
-    double u[NDIM], cs;
-    if (!cell_primitives<NDIM>(U, ncell, c, gamma, aux, u, cs)) bad = true;
+    double uh[NDIM], cs;
+    if (!cell_primitives<NDIM>(U, ncell, c, gamma, aux, uh, cs)) bad = true;
     if (fh) {
       double Uc[NVAR];
 #pragma unroll
@@ -72,13 +72,17 @@ __global__ void __launch_bounds__(256, 3) cell_kernel(const double* __restrict__
       const double pn = aux[NDIM * ncell + c];
       store_flux_half<NDIM, 0>(Uc, aux, pn, fh, ncell, c);
     }
+    // u -+ c = 2 (u/2) -+ c with one rounding, as a subtraction of u would;
+    // max|u| is kept as max|u/2| and doubled (exactly) below
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      lam[d][0] = max_abs_bits(lam[d][0], __dsub_rn(u[d], cs));
-      lam[d][1] = max_abs_bits(lam[d][1], u[d]);
-      lam[d][2] = max_abs_bits(lam[d][2], __dadd_rn(u[d], cs));
+      lam[d][0] = max_abs_bits(lam[d][0], fma(2.0, uh[d], -cs));
+      lam[d][1] = max_abs_bits(lam[d][1], uh[d]);
+      lam[d][2] = max_abs_bits(lam[d][2], fma(2.0, uh[d], cs));
     }
   }
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) lam[d][1] = dbits(2.0 * __longlong_as_double(static_cast<long long>(lam[d][1])));
   // warp max on bit patterns (all values are >= 0)
   __shared__ unsigned long long red[8][NDIM * 3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
