@@ -21,11 +21,22 @@
 
 #ifdef __CUDACC__
 #define TENO_HD __host__ __device__
+#include "teno_device.cuh"
 #else
 #define TENO_HD
 #endif
 
 namespace teno_adj {
+
+// 1/x for x > 0: on the device the seeded reciprocal of the forward pass
+// (teno::recip_pos, within one ulp), on the host the division.
+TENO_HD inline double recip(double x) {
+#ifdef __CUDA_ARCH__
+  return teno::recip_pos(x);
+#else
+  return 1.0 / x;
+#endif
+}
 
 // Linear weights of the reconstruction with selection `sel` (delta bits):
 // f^ = sum_k a[k] v_k over v = (f_{i-2}, ..., f_{i+2}), from the TENO weights
@@ -286,7 +297,7 @@ TENO_HD inline void flux_vjp(const double (&U)[NDIM + 2], double gamma, const do
   constexpr int NV = NDIM + 2;
   constexpr int E = NDIM + 1;
   const double gm1 = gamma - 1.0;
-  const double ir = 1.0 / U[0];
+  const double ir = recip(U[0]);
   double u[NDIM], q = 0.0;
   for (int k = 0; k < NDIM; ++k) {
     u[k] = U[1 + k] * ir;
@@ -316,14 +327,14 @@ template <int NDIM>
 TENO_HD inline void roe_from_primitives(double sa, double sb, double sha, double shb, const double (&ua)[NDIM],
                                         const double (&ub)[NDIM], double gamma, RoeState<NDIM>& R) {
   const double gm1 = gamma - 1.0;
-  const double rsa = 1.0 / sa, rsb = 1.0 / sb;
+  const double rsa = recip(sa), rsb = recip(sb);
   R.sa = sa;
   R.sb = sb;
   R.ira = rsa * rsa;
   R.irb = rsb * rsb;
   R.Ha = sha * rsa;
   R.Hb = shb * rsb;
-  R.iS = 1.0 / (sa + sb);
+  R.iS = recip(sa + sb);
   R.qa = R.qb = R.q2 = 0.0;
   for (int k = 0; k < NDIM; ++k) {
     R.ua[k] = ua[k];
