@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     Rf.hic = 0.5 * R.ic;
     Rf.hud = 0.5 * R.ut[DIR];
     teno::CertIfc<NDIM> C;
-    teno::cert_begin<NDIM>(Rf, ha, C);
+    teno::cert_begin<NDIM, DIR>(Rf, ha, C);
     double Ut[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) Ut[v] = 0.0;

@@ -86,22 +86,24 @@ template <int NDIM, int DIR>
 __device__ __forceinline__ void roe_interface(double sr2, double sr3, double sh2, double sh3,
                                               const double (&uu2)[NDIM], const double (&uu3)[NDIM],
                                               const Scheme& S, RoeIfc<NDIM>& R, int* __restrict__ status) {
-  const double inv2 = 2.0 * recip_pos(sr2 + sr3);
+  const double y = recip_pos(sr2 + sr3);
+  const double inv2 = 2.0 * y;
   R.q2 = 0.0;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
     R.u[k] = fma(sr2, uu2[k], sr3 * uu3[k]) * inv2;
     R.q2 = fma(R.u[k], R.u[k], R.q2);
   }
-  R.H = (sh2 + sh3) * (0.5 * inv2);
+  R.H = (sh2 + sh3) * y;
   const double c2 = S.gm1 * fma(-0.5, R.q2, R.H);
   if (!(c2 > 0.0)) atomicOr(status, kStatusNonphysical);
   const double ic = rsqrt(c2);
   R.cs = c2 * ic;
-  R.b1 = S.gm1 * ic * ic;
-  const double b2 = 0.5 * R.b1 * R.q2;
-  R.hb1 = 0.5 * R.b1;
-  R.hb2 = 0.5 * b2;
+  // the halved coefficients directly (the factors 1/2 are exact); b1 and
+  // hud only for the characteristic path, which reads them
+  R.hb1 = (0.5 * S.gm1) * ic * ic;
+  R.b1 = R.hb1 + R.hb1;
+  R.hb2 = 0.5 * (R.hb1 * R.q2);
   R.hic = 0.5 * ic;
   R.hud = 0.5 * R.u[DIR];
 }
@@ -119,7 +121,7 @@ struct CertIfc {
   float vp32[6][NDIM + 2], vm32[6][NDIM + 2], mp[NDIM + 2], mm[NDIM + 2], vmax;
 };
 
-template <int NDIM>
+template <int NDIM, int DIR>
 __device__ __forceinline__ void cert_begin(const RoeIfc<NDIM>& R, const double (&alpha)[NDIM + 2],
                                            CertIfc<NDIM>& C) {
   constexpr int NVAR = NDIM + 2;
@@ -128,8 +130,10 @@ __device__ __forceinline__ void cert_begin(const RoeIfc<NDIM>& R, const double (
   C.hb1f = hi_float(R.hb1);
   C.hb2f = hi_float(R.hb2);
   C.hicf = hi_float(R.hic);
-  C.b1f = hi_float(R.b1);
-  C.hudf = hi_float(R.hud);
+  // b1 = 2 hb1 and hud = u_d/2 from the truncated values (exact scalings:
+  // the same 2^-20 relative bound, no FP64 work)
+  C.b1f = 2.0f * C.hb1f;
+  C.hudf = 0.5f * C.uf[DIR];
 #pragma unroll
   for (int f = 0; f < NVAR; ++f) {
     C.haf[f] = hi_float(alpha[f]);
@@ -259,20 +263,29 @@ __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const d
                                            const RoeIfc<NDIM>& R, const double (&nal)[NDIM + 2],
                                            double (&out)[NDIM + 2]) {
   constexpr int NVAR = NDIM + 2;
-  double wt[NVAR];
-  project<NDIM, DIR>(Ut, R.u, R.hb1, R.hb2, R.hic, wt);
+  // l_0.U~ = A + B and l_E.U~ = A - B (as in project), so with the speed
+  // differences d0, dE of fields 0 and E against the middle ones the two
+  // corrections g0 = d0 l_0.U~, gE = dE l_E.U~ enter only as
+  //   gs = g0 + gE = (d0 + dE) A + (d0 - dE) B,
+  //   gd = gE - g0 = -((d0 - dE) A + (d0 + dE) B)      (ngd = -gd below).
+  double Sx = -Ut[NVAR - 1];
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) Sx = fma(R.u[k], Ut[1 + k], Sx);
+  const double A = fma(R.hb2, Ut[0], -R.hb1 * Sx);
+  const double B = fma(R.u[DIR], Ut[0], -Ut[1 + DIR]) * R.hic;
   const double amid = -nal[1];
-  const double g0 = (nal[1] - nal[0]) * wt[0];
-  const double gE = (nal[1] - nal[NVAR - 1]) * wt[NVAR - 1];
-  const double gs = g0 + gE, gd = gE - g0;
+  const double d0 = nal[1] - nal[0], dE = nal[1] - nal[NVAR - 1];
+  const double sg = d0 + dE, df = d0 - dE;
+  const double gs = fma(sg, A, df * B);
+  const double ngd = fma(df, A, sg * B);
   out[0] = fma(amid, Ut[0], Ft[0]) + gs;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
     double o = fma(R.u[k], gs, fma(amid, Ut[1 + k], Ft[1 + k]));
-    if (k == DIR) o = fma(R.cs, gd, o);
+    if (k == DIR) o = fma(-R.cs, ngd, o);
     out[1 + k] = o;
   }
-  out[NVAR - 1] = fma(R.H, gs, fma(R.u[DIR] * R.cs, gd, fma(amid, Ut[NVAR - 1], Ft[NVAR - 1])));
+  out[NVAR - 1] = fma(R.H, gs, fma(-(R.u[DIR] * R.cs), ngd, fma(amid, Ut[NVAR - 1], Ft[NVAR - 1])));
 }
 
 // ---------------------------------------------------------------------------
@@ -308,7 +321,7 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
                              S, R, status);
   }
   CertIfc<NDIM> C;
-  cert_begin<NDIM>(R, alpha, C);
+  cert_begin<NDIM, DIR>(R, alpha, C);
   double Ft[NVAR], Ut[NVAR];
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) Ft[v] = Ut[v] = 0.0;
@@ -401,7 +414,7 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
 
     if (!WITH_FLAGS && MODE != kFluxChar && S.keep_idx >= 0) {
       CertIfc<NDIM> C;
-      cert_begin<NDIM>(R, alpha, C);
+      cert_begin<NDIM, DIR>(R, alpha, C);
 #pragma unroll
       for (int j = 0; j < 6; ++j) cert_point<NDIM, DIR>(j, Ux[j], un[j], pn[j], C);
       const bool keep = cert_keep<NDIM>(C, S);
