@@ -286,10 +286,10 @@ teno_status teno_scalar_rk3_step(const teno_grid* g, double a, int mode, double*
  * which every GPU that loads the library holds until the process exits.
  *   U    : [in]  device, nvar * ncell doubles (layout above).
  *   dUdt : [out] device, nvar * ncell doubles; must not alias U.
- * Size limit: a call needs 256 + 8 (ndim + 3) ncell + 8 (ndim + 2) max_d
+ * Size limit: a call needs 256 + 8 (2 ndim + 3) ncell + 8 (ndim + 2) max_d
  * (#interfaces_d) bytes (each term rounded up to 256); larger grids are
  * rejected with TENO_ERR_WORKSPACE before anything is launched.  In 1D that is
- * up to about 149,000 cells; in 3D about 45^3.
+ * up to 131,065 cells; in 2D 308^2; in 3D 42^3.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before capturing
  * a stream into a CUDA graph.

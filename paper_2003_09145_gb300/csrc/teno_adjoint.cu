@@ -49,8 +49,8 @@ __global__ void argmax_kernel(const double* __restrict__ U, const unsigned long 
                               double* __restrict__ scratch_aux) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
-    double uh[NDIM], cs;
-    teno::cell_primitives<NDIM>(U, ncell, c, gamma, scratch_aux, uh, cs);
+    double uh[NDIM], cs, ep;
+    teno::cell_primitives<NDIM>(U, ncell, c, gamma, scratch_aux, uh, cs, ep);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       const double lam[3] = {fabs(fma(2.0, uh[d], -cs)), fabs(2.0 * uh[d]), fabs(fma(2.0, uh[d], cs))};
@@ -542,7 +542,7 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   for (int d = 0; d < g->ndim; ++d) maxifc = nifc_of(g, d) > maxifc ? nifc_of(g, d) : maxifc;
   size_t off = kAlign;
   L.aux = off;
-  off += round_up(sizeof(double) * (g->ndim + 3) * ncell);
+  off += round_up(sizeof(double) * teno::aux_fields(g->ndim) * ncell);
   L.kb = off;
   off += round_up(sizeof(double) * 3 * nvar * size_t(maxifc));
   L.contrib = off;

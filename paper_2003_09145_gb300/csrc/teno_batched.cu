@@ -83,12 +83,12 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
     unsigned long long b0 = 0ull, b1 = 0ull, b2 = 0ull;   // bit patterns of the maxima
     bool bad = false;
     for (int64_t i = tid; i < n; i += BLOCK) {
-      double uh[1], cs;
+      double uh[1], cs, ep;
       const int64_t c = off + i;
-      if (!teno::cell_primitives<1>(A.Uin, A.ncell, c, A.gamma, A.aux, uh, cs)) bad = true;
+      if (!teno::cell_primitives<1>(A.Uin, A.ncell, c, A.gamma, A.aux, uh, cs, ep)) bad = true;
       const double Uc[3] = {A.Uin[c], A.Uin[A.ncell + c], A.Uin[2 * A.ncell + c]};
       double Fh[3];
-      teno::cell_flux_half<1, 0>(Uc, A.aux[c], A.aux[A.ncell + c], Fh);
+      teno::cell_flux_half_ep<1, 0>(Uc, uh[0], A.aux[A.ncell + c], ep, Fh);
 #pragma unroll
       for (int v = 1; v < 3; ++v) A.fh[(v - 1) * A.ncell + c] = Fh[v];
       // u -+ c from u/2 with one rounding; max|u| kept as max|u/2|
@@ -224,7 +224,7 @@ BatchLayout batch_layout(const teno_batch* b) {
   L.dt = off;
   off += round_up(sizeof(double) * size_t(b->nprob));
   L.aux = off;
-  off += round_up(sizeof(double) * 4 * size_t(b->ncell));
+  off += round_up(sizeof(double) * teno::aux_fields(1) * size_t(b->ncell));
   L.fh = off;
   off += round_up(sizeof(double) * 2 * size_t(b->ncell));
   L.U1 = off;

@@ -37,7 +37,7 @@ bool grid_ok(const teno_grid* g) {
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
   // total cell count must stay addressable with 64-bit indices
   const double cells = double(g->n[0]) * double(g->n[1]) * double(g->n[2]);
-  if (cells * (g->ndim + 3) > 9.0e18 / 8.0) return false;
+  if (cells * teno::aux_fields(g->ndim) > 9.0e18 / 8.0) return false;
   return true;
 }
 
@@ -64,7 +64,7 @@ Layout layout_of(const teno_grid* g, int op) {
   for (int d = 0; d < g->ndim; ++d) maxifc = nifc_of(g, d) > maxifc ? nifc_of(g, d) : maxifc;
   size_t off = kHeader;
   L.aux = off;
-  off += round_up(sizeof(double) * (g->ndim + 3) * ncell);
+  off += round_up(sizeof(double) * teno::aux_fields(g->ndim) * ncell);
   L.fh = off;   // half physical fluxes F_d/2 per cell and direction (no mass component)
   off += round_up(sizeof(double) * g->ndim * (nvar - 1) * ncell);
   L.fhat = off;

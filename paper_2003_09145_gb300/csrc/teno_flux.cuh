@@ -73,7 +73,7 @@ __device__ __forceinline__ bool certify_keep(float v0, float v1, float v2, float
 
 // ---------------------------------------------------------------------------
 // Roe state of the interface i+1/2 from the per-cell primitives of cells i
-// and i+1 (sqrt(rho), (E+p)/sqrt(rho) and the half velocities uu = u/2):
+// and i+1 (sqrt(rho), (E+p)/sqrt(rho) and su = sqrt(rho) u/2):
 // u~ = (sr_a u_a + sr_b u_b)/(sr_a + sr_b), H~ = (sh_a + sh_b)/(sr_a + sr_b),
 // c~^2 = (gamma-1)(H~ - |u~|^2/2), b1 = (gamma-1)/c~^2, b2 = b1 |u~|^2/2.
 // ---------------------------------------------------------------------------
@@ -84,14 +84,14 @@ struct RoeIfc {
 
 template <int NDIM, int DIR>
 __device__ __forceinline__ void roe_interface(double sr2, double sr3, double sh2, double sh3,
-                                              const double (&uu2)[NDIM], const double (&uu3)[NDIM],
+                                              const double (&su2)[NDIM], const double (&su3)[NDIM],
                                               const Scheme& S, RoeIfc<NDIM>& R, int* __restrict__ status) {
   const double y = recip_pos(sr2 + sr3);
   const double inv2 = 2.0 * y;
   R.q2 = 0.0;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
-    R.u[k] = fma(sr2, uu2[k], sr3 * uu3[k]) * inv2;
+    R.u[k] = (su2[k] + su3[k]) * inv2;
     R.q2 = fma(R.u[k], R.u[k], R.q2);
   }
   R.H = (sh2 + sh3) * y;
@@ -230,6 +230,19 @@ __device__ __forceinline__ bool cert_keep(const CertIfc<NDIM>& C, const Scheme& 
 // P/2 (the same products, since halving is exact), so the half fluxes need
 // only the momentum and energy components (v = 1..nvar-1).
 // ---------------------------------------------------------------------------
+// cell_flux_half_ep takes E + p as given (the cell pass has it);
+// cell_flux_half forms it as E + 2 (p/2), the same value, since the
+// doubling is exact.
+template <int NDIM, int DIR>
+__device__ __forceinline__ void cell_flux_half_ep(const double (&Uc)[NDIM + 2], double un, double pn, double ep,
+                                                  double (&Fh)[NDIM + 2]) {
+  constexpr int NVAR = NDIM + 2;
+  Fh[0] = 0.5 * Uc[1 + DIR];
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) Fh[1 + k] = k == DIR ? fma(un, Uc[1 + k], pn) : un * Uc[1 + k];
+  Fh[NVAR - 1] = un * ep;
+}
+
 template <int NDIM, int DIR>
 __device__ __forceinline__ void cell_flux_half(const double (&Uc)[NDIM + 2], double un, double pn,
                                                double (&Fh)[NDIM + 2]) {
@@ -237,10 +250,7 @@ __device__ __forceinline__ void cell_flux_half(const double (&Uc)[NDIM + 2], dou
   // F/2 = (u_d/2) U + (p/2) (0, e_d, u_d), per component: mass m_d/2,
   // momentum (u_d/2) m_k (+ p/2 for k = d), energy (u_d/2)(E + p); E + p
   // is formed as E + 2 (p/2), which doubles exactly
-  Fh[0] = 0.5 * Uc[1 + DIR];
-#pragma unroll
-  for (int k = 0; k < NDIM; ++k) Fh[1 + k] = k == DIR ? fma(un, Uc[1 + k], pn) : un * Uc[1 + k];
-  Fh[NVAR - 1] = un * fma(2.0, pn, Uc[NVAR - 1]);
+  cell_flux_half_ep<NDIM, DIR>(Uc, un, pn, fma(2.0, pn, Uc[NVAR - 1]), Fh);
 }
 
 // (Fhj[0] is not read: the mass term is P[j] m_d = (P2[j]/2) m_d.)
@@ -308,16 +318,16 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
   if (S.keep_idx < 0) return false;
   RoeIfc<NDIM> R;
   {
-    double uu2[NDIM], uu3[NDIM];
+    double su2[NDIM], su3[NDIM];
 #pragma unroll
     for (int k = 0; k < NDIM; ++k) {
-      uu2[k] = aux[k * ncell + cells[2]];
-      uu3[k] = aux[k * ncell + cells[3]];
+      su2[k] = aux[(NDIM + 3 + k) * ncell + cells[2]];
+      su3[k] = aux[(NDIM + 3 + k) * ncell + cells[3]];
     }
-    uu2[DIR] = flip_sign(uu2[DIR], (flips >> 2) & 1u);
-    uu3[DIR] = flip_sign(uu3[DIR], (flips >> 3) & 1u);
+    su2[DIR] = flip_sign(su2[DIR], (flips >> 2) & 1u);
+    su3[DIR] = flip_sign(su3[DIR], (flips >> 3) & 1u);
     roe_interface<NDIM, DIR>(aux[(NDIM + 1) * ncell + cells[2]], aux[(NDIM + 1) * ncell + cells[3]],
-                             aux[(NDIM + 2) * ncell + cells[2]], aux[(NDIM + 2) * ncell + cells[3]], uu2, uu3,
+                             aux[(NDIM + 2) * ncell + cells[2]], aux[(NDIM + 2) * ncell + cells[3]], su2, su3,
                              S, R, status);
   }
   CertIfc<NDIM> C;
@@ -383,7 +393,7 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
   {
     // six-point stencil i-2..i+3 with i = id - 1
     double Ux[6][NVAR], un[6], pn[6];
-    double sr2, sr3, sh2, sh3, uu2[NDIM], uu3[NDIM];
+    double sr2, sr3, sh2, sh3, su2[NDIM], su3[NDIM];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const int64_t c = cells[j];
@@ -394,9 +404,10 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
       un[j] = flip_sign(aux[DIR * ncell + c], fj);
       pn[j] = aux[NDIM * ncell + c];
       if (j == 2 || j == 3) {
-        double* uu = (j == 2) ? uu2 : uu3;
+        double* su = (j == 2) ? su2 : su3;
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) uu[k] = (k == DIR) ? un[j] : aux[k * ncell + c];
+        for (int k = 0; k < NDIM; ++k) su[k] = aux[(NDIM + 3 + k) * ncell + c];
+        su[DIR] = flip_sign(su[DIR], fj);
         if (j == 2) {
           sr2 = aux[(NDIM + 1) * ncell + c];
           sh2 = aux[(NDIM + 2) * ncell + c];
@@ -407,7 +418,7 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
       }
     }
     RoeIfc<NDIM> R;
-    roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, uu2, uu3, S, R, status);
+    roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, su2, su3, S, R, status);
     const double (&u)[NDIM] = R.u;
     const double q2 = R.q2, H = R.H, cs = R.cs, b1 = R.b1;
     const double hb1 = R.hb1, hb2 = R.hb2, hic = R.hic, hud = R.hud;
@@ -511,16 +522,17 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
 // 1/sqrt(rho), sqrt(rho) = rho/sqrt(rho), 1/(2 rho) = (1/sqrt(rho))^2 / 2,
 // u/2 = m/(2 rho), p = (gamma-1)(E - 2 rho |u/2|^2) (eq. 4.7),
 // c = sqrt(gamma p / rho).  Writes the aux entries (u_k/2, p/2, sqrt(rho),
-// (E+p)/sqrt(rho)) and returns uh = u/2 and c; false if the state is not
-// physical (rho <= 0, p <= 0 or non-finite).  Working with u/2 saves the
-// halving multiplies; every value equals the u-based evaluation's bit for
-// bit, since the factors of 2 are exact.
+// (E+p)/sqrt(rho), sqrt(rho) u_k/2 -- the Roe average's weighted velocities)
+// and returns uh = u/2, c and E + p; false if the state is not physical
+// (rho <= 0, p <= 0 or non-finite).  Working with u/2 saves the halving
+// multiplies; every value equals the u-based evaluation's bit for bit,
+// since the factors of 2 are exact.
 // ---------------------------------------------------------------------------
 template <int NDIM>
 __device__ __forceinline__ bool cell_primitives(const double* __restrict__ U, int64_t ncell,
                                                 int64_t c, double gamma,
                                                 double* __restrict__ aux,
-                                                double (&uh)[NDIM], double& cs) {
+                                                double (&uh)[NDIM], double& cs, double& ep) {
   constexpr int NVAR = NDIM + 2;
   const double rho = U[c];
   const double E = U[(NVAR - 1) * ncell + c];
@@ -536,11 +548,14 @@ __device__ __forceinline__ bool cell_primitives(const double* __restrict__ U, in
   const double p = (gamma - 1.0) * fma(-2.0 * rho, q2h, E);
   const double gpr = (2.0 * gamma) * p * hr;
   cs = gpr * rsqrt(gpr);
+  ep = E + p;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) aux[k * ncell + c] = uh[k];
   aux[NDIM * ncell + c] = 0.5 * p;
   aux[(NDIM + 1) * ncell + c] = sr;
-  aux[(NDIM + 2) * ncell + c] = (E + p) * isr;
+  aux[(NDIM + 2) * ncell + c] = ep * isr;
+#pragma unroll
+  for (int k = 0; k < NDIM; ++k) aux[(NDIM + 3 + k) * ncell + c] = sr * uh[k];
   return pos_finite(rho) && pos_finite(p) && is_finite(E) && is_finite(q2h) && pos_finite(gpr);
 }
 

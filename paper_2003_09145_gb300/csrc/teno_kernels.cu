@@ -28,8 +28,9 @@ namespace teno {
 // The primitive variables come from one reciprocal square root per cell
 // (cell_primitives); the wave speeds |u_d - c|, |u_d|, |u_d + c| are reduced
 // to their maxima over all cells.
-// aux layout: [ndim + 3][ncell]: u_0/2..u_{ndim-1}/2, p/2, sqrt(rho),
-// (E+p)/sqrt(rho).  With `fh`, also the half physical fluxes F_d/2 (eq. 4.7)
+// aux layout: [aux_fields(ndim) = 2 ndim + 3][ncell]: u_0/2..u_{ndim-1}/2,
+// p/2, sqrt(rho), (E+p)/sqrt(rho), sqrt(rho) u_0/2..sqrt(rho) u_{ndim-1}/2.
+// With `fh`, also the half physical fluxes F_d/2 (eq. 4.7)
 // of every direction, momentum and energy components only (the mass one is
 // m_d/2), [ndim][nvar - 1][ncell], for the closed-form flux pass.
 // alpha layout (bit patterns of non-negative doubles): [ndim][3] =
@@ -37,15 +38,15 @@ namespace teno {
 // ---------------------------------------------------------------------------
 // F_d/2 of cell c for d = D..NDIM-1 into fh[d][v - 1][c], v = 1..nvar-1.
 template <int NDIM, int D>
-__device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], const double* __restrict__ aux,
-                                                double pn, double* __restrict__ fh, int64_t ncell, int64_t c) {
+__device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], const double (&uh)[NDIM], double pn,
+                                                double ep, double* __restrict__ fh, int64_t ncell, int64_t c) {
   if constexpr (D < NDIM) {
     constexpr int NVAR = NDIM + 2;
     double Fh[NVAR];
-    cell_flux_half<NDIM, D>(Uc, aux[D * ncell + c], pn, Fh);
+    cell_flux_half_ep<NDIM, D>(Uc, uh[D], pn, ep, Fh);
 #pragma unroll
     for (int v = 1; v < NVAR; ++v) fh[(int64_t)(D * (NVAR - 1) + v - 1) * ncell + c] = Fh[v];
-    store_flux_half<NDIM, D + 1>(Uc, aux, pn, fh, ncell, c);
+    store_flux_half<NDIM, D + 1>(Uc, uh, pn, ep, fh, ncell, c);
   }
 }
 
@@ -63,14 +64,14 @@ __global__ void __launch_bounds__(256, 3) cell_kernel(const double* __restrict__
   bool bad = false;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
-    double uh[NDIM], cs;
-    if (!cell_primitives<NDIM>(U, ncell, c, gamma, aux, uh, cs)) bad = true;
+    double uh[NDIM], cs, ep;
+    if (!cell_primitives<NDIM>(U, ncell, c, gamma, aux, uh, cs, ep)) bad = true;
     if (fh) {
       double Uc[NVAR];
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Uc[v] = U[v * ncell + c];
       const double pn = aux[NDIM * ncell + c];
-      store_flux_half<NDIM, 0>(Uc, aux, pn, fh, ncell, c);
+      store_flux_half<NDIM, 0>(Uc, uh, pn, ep, fh, ncell, c);
     }
     // u -+ c = 2 (u/2) -+ c with one rounding, as a subtraction of u would;
     // max|u| is kept as max|u/2| and doubled (exactly) below

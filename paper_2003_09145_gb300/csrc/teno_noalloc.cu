@@ -23,7 +23,7 @@ namespace {
 // The scratch array.  Every GPU that loads the library holds these bytes
 // until the process exits.  Layout (all offsets 256-byte aligned):
 //   [0, 256)        status word and the LF wave speeds (bit patterns)
-//   [256, ...)      per-cell primitive variables, (ndim + 3) * ncell doubles
+//   [256, ...)      per-cell primitive variables, aux_fields(ndim) * ncell doubles
 //   [..., end)      interface fluxes, nvar * max_d(#interfaces_d) doubles
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TENO_NOALLOC_SCRATCH_BYTES];
 
@@ -89,7 +89,7 @@ size_t scratch_needed(const teno_grid* g) {
     for (int k = 0; k < 3; ++k) m *= size_t(g->n[k] + (k == d ? 1 : 0));
     if (m > maxifc) maxifc = m;
   }
-  return kAlign + round_up(sizeof(double) * (g->ndim + 3) * ncell) +
+  return kAlign + round_up(sizeof(double) * teno::aux_fields(g->ndim) * ncell) +
          round_up(sizeof(double) * (g->ndim + 2) * maxifc);
 }
 
@@ -113,7 +113,7 @@ extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, dou
   auto* alpha = reinterpret_cast<unsigned long long*>(ws + 64);
   const size_t ncell = size_t(g->n[0] * g->n[1] * g->n[2]);
   double* aux = reinterpret_cast<double*>(ws + kAlign);
-  double* Fhat = reinterpret_cast<double*>(ws + kAlign + round_up(sizeof(double) * (g->ndim + 3) * ncell));
+  double* Fhat = reinterpret_cast<double*>(ws + kAlign + round_up(sizeof(double) * teno::aux_fields(g->ndim) * ncell));
 
   teno::Grid G;
   for (int k = 0; k < 3; ++k) {

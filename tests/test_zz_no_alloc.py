@@ -71,10 +71,10 @@ def test_noalloc_matches_teno_rhs_on_consecutive_calls():
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
     L, lib = _lib()
-    too_big = L.make_grid((200000,), (1e-5,), 1)        # 1D limit is about 149,000 cells
+    too_big = L.make_grid((200000,), (1e-5,), 1)        # 1D limit is 131,065 cells
     # aligned non-null stand-ins: the size check fails before any pointer is used
     st = lib.teno_rhs_noalloc(ctypes.byref(too_big), ctypes.c_void_p(256), ctypes.c_void_p(512), None)
     assert st == TENO_ERR_WORKSPACE
-    cube = L.make_grid((46, 46, 46), (0.1,) * 3, 0)      # 3D limit is 45^3
+    cube = L.make_grid((43, 43, 43), (0.1,) * 3, 0)      # 3D limit is 42^3
     st = lib.teno_rhs_noalloc(ctypes.byref(cube), ctypes.c_void_p(256), ctypes.c_void_p(512), None)
     assert st == TENO_ERR_WORKSPACE
