@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
     if (!(dt > 0.0)) continue;
     const double alpha[3] = {s_alpha[0], s_alpha[1], s_alpha[2]};
     const double nal[3] = {-2.0 * s_alpha[0], -2.0 * s_alpha[1], -2.0 * s_alpha[2]};
-    const double idx = s_idx;
+    const double cdt = dt * s_idx;   // dt / dx, as the grid path's stage coefficient
 
     // (B) fluxes tile by tile, difference fused with the stage update
     for (int64_t i0 = 0; i0 < n; i0 += BLOCK - 1) {
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
       if (tid < BLOCK - 1 && cell < n) {
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          const double d = (s_F[tid][v] - s_F[tid + 1][v]) * idx;
+          const double t = s_F[tid][v] - s_F[tid + 1][v];
           const int64_t e = v * A.ncell + off + cell;
-          A.Uout[e] = teno::stage_value(A.mode, dt, d, A.Un, A.Uk, e);
+          A.Uout[e] = teno::stage_value(A.mode, cdt, t, A.Un, A.Uk, e);
         }
       }
       __syncthreads();

@@ -203,12 +203,9 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
       ts.launches(nl);
     }
     foff += int64_t(g->ndim + 2) * 2 * nifc_of(g, d);
-    const bool last = (d == g->ndim - 1);
-    const int mode = last ? (mode_last == 0 ? (d == 0 ? 0 : 1) : mode_last) : (d == 0 ? 0 : 1);
-    const int acc = d > 0 ? 1 : 0;
     {
       TimerScope ts(st, TENO_KERNEL_DIFF);
-      TENO_CUDA(teno::launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt_ws, G, mode, acc, nsm, st));
+      TENO_CUDA(teno::launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt_ws, G, mode_last, nsm, st));
     }
   }
   return TENO_OK;

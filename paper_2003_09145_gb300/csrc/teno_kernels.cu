@@ -296,37 +296,48 @@ __global__ void __launch_bounds__(128) flux_pending_kernel(
 
 // ---------------------------------------------------------------------------
 // Conservative difference (eq. 2.2) and SSP-RK3 stage update (eq. 4.1-4.3).
-// mode: 0 R = d; 1 R += d; 2 U1 = Un + dt (R + d); 3 U2 = 3/4 Un + 1/4 U1 +
-// 1/4 dt (R + d); 4 Un <- 1/3 Un + 2/3 U2 + 2/3 dt (R + d).  `acc` selects
-// whether R already holds the contributions of earlier directions; it does
-// exactly for the directions after the first (DIR > 0).  MODE is a template
-// argument (0 and 1 share one form) so that every load of a cell is issued
-// before its stores.
+// With t_d = F^_{i-1/2} - F^_{i+1/2} of direction d and r_d = dx_0 / dx_d,
+// L(U) = (t_0 + r_1 t_1 + r_2 t_2) / dx_0: R carries the unscaled partial
+// sum and 1/dx_0 is applied once (in the stage's coefficient, or at the end
+// of a plain right-hand side), one FP64 instruction fewer per element than
+// scaling every direction -- the passes are bound by FP64 issue.
+// MODE (a template argument, so that every load of a cell is issued before
+// its stores):
+//   kDiffFirst  R = t_0                        (first of several directions)
+//   kDiffAcc    R += r_d t_d                   (a middle direction)
+//   kDiffRhs    R = (R + r_d t_d) / dx_0       (last direction of a plain RHS;
+//                                               R = t_0 / dx_0 in 1D)
+//   2, 3, 4     with s = R + r_d t_d (t_0 in 1D) and c = dt / dx_0:
+//               2: U1 = Un + c s;  3: U2 = 3/4 Un + 1/4 U1 + 1/4 c s;
+//               4: Un <- 1/3 Un + 2/3 U2 + 2/3 c s.
 // ---------------------------------------------------------------------------
+constexpr int kDiffFirst = 0, kDiffAcc = 1, kDiffRhs = 5;
+
 template <int NDIM, int DIR, int MODE>
 __global__ void __launch_bounds__(256) diff_kernel(
     const double* __restrict__ Fhat, double* __restrict__ R,
     const double* __restrict__ Un, const double* __restrict__ Uk,
     double* __restrict__ Uout, const double* __restrict__ dt_ptr, Grid G) {
-  constexpr int mode = MODE;
-  constexpr bool acc = DIR > 0;
+  constexpr bool stage = MODE >= 2 && MODE <= 4;
+  constexpr bool acc = DIR > 0;   // R holds the earlier directions' sum
   constexpr int NVAR = NDIM + 2;
   const int64_t ncell = G.ncell;
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
   const int64_t nifc = m0 * m1 * (G.n[2] + (DIR == 2));
-  const double idx = G.inv_dx[DIR];
-  double dt = 0.0;
-  if (mode >= 2) {
-    dt = *dt_ptr;
+  const double rd = G.dx[0] / G.dx[DIR];   // exactly 1 for equal spacings
+  double c = 0.0;
+  if (stage) {
+    const double dt = *dt_ptr;
     if (!(dt > 0.0)) {
       // t >= t_end: the state is left unchanged.  The stage buffers U1, U2
       // take U^n, so that the stages after this one read defined values.
-      if (mode <= 3)
+      if (MODE <= 3)
         for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < NVAR * ncell;
              e += (int64_t)gridDim.x * blockDim.x)
           Uout[e] = Un[e];
       return;
     }
+    c = dt * G.inv_dx[0];
   }
   // The interface left of cell c = (i2 n1 + i1) n0 + i0 is (i2 m1 + i1) m0 + i0:
   // x: c plus the row index c / n0 (one more interface per row); y: c plus
@@ -334,30 +345,33 @@ __global__ void __launch_bounds__(256) diff_kernel(
   const int64_t span = DIR == 0 ? G.n[0] : G.n[0] * G.n[1];
   const int64_t shift = DIR == 0 ? 1 : G.n[0];
   const bool narrow = ncell <= int64_t(UINT32_MAX);   // 32-bit division suffices
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int64_t left = c;
+  for (int64_t cc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cc < ncell;
+       cc += (int64_t)gridDim.x * blockDim.x) {
+    int64_t left = cc;
     if (DIR < 2) {
-      const int64_t q = narrow ? int64_t(uint32_t(c) / uint32_t(span)) : c / span;
+      const int64_t q = narrow ? int64_t(uint32_t(cc) / uint32_t(span)) : cc / span;
       left += q * shift;
     }
     const int64_t right = left + (DIR == 0 ? 1 : (DIR == 1 ? m0 : m0 * m1));
-    // all loads of the cell first (the branches on mode and acc are uniform)
-    double d[NVAR];
+    // all loads of the cell first
+    double s[NVAR];
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) d[v] = (Fhat[v * nifc + left] - Fhat[v * nifc + right]) * idx;
+    for (int v = 0; v < NVAR; ++v) s[v] = Fhat[v * nifc + left] - Fhat[v * nifc + right];
     if (acc)
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) d[v] += R[v * ncell + c];
-    if (mode <= 1) {
+      for (int v = 0; v < NVAR; ++v) s[v] = fma(rd, s[v], R[v * ncell + cc]);
+    if (MODE == kDiffFirst || MODE == kDiffAcc) {
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) R[v * ncell + c] = d[v];
+      for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = s[v];
+    } else if (MODE == kDiffRhs) {
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = s[v] * G.inv_dx[0];
     } else {
       double o[NVAR];
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) o[v] = stage_value(mode, dt, d[v], Un, Uk, v * ncell + c);
+      for (int v = 0; v < NVAR; ++v) o[v] = stage_value(MODE, c, s[v], Un, Uk, v * ncell + cc);
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) Uout[v * ncell + c] = o[v];
+      for (int v = 0; v < NVAR; ++v) Uout[v * ncell + cc] = o[v];
     }
   }
 }
@@ -529,11 +543,15 @@ cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, c
 template <int NDIM, int DIR>
 static void diff_launch(int blocks, int threads, cudaStream_t st, const double* Fhat,
                         double* R, const double* Un, const double* Uk, double* Uout,
-                        const double* dt, const Grid& G, int mode, int acc) {
-  (void)acc;   // acc == (DIR > 0), checked by launch_diff
+                        const double* dt, const Grid& G, int mode) {
+  // the first of several directions starts R; a middle one adds to it
+  if (DIR < NDIM - 1) {
+    if (DIR == 0) diff_kernel<NDIM, DIR, kDiffFirst><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G);
+    else diff_kernel<NDIM, DIR, kDiffAcc><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G);
+    return;
+  }
   switch (mode) {
-    case 0:
-    case 1: diff_kernel<NDIM, DIR, 1><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
+    case 0: diff_kernel<NDIM, DIR, kDiffRhs><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
     case 2: diff_kernel<NDIM, DIR, 2><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
     case 3: diff_kernel<NDIM, DIR, 3><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
     default: diff_kernel<NDIM, DIR, 4><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
@@ -542,19 +560,19 @@ static void diff_launch(int blocks, int threads, cudaStream_t st, const double* 
 
 cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
                         const double* Un, const double* Uk, double* Uout,
-                        const double* dt, const Grid& G, int mode, int acc,
+                        const double* dt, const Grid& G, int mode,
                         int nsm, cudaStream_t st) {
-  if ((acc != 0) != (dir > 0) || mode < 0 || mode > 4) return cudaErrorInvalidValue;
+  if (mode != 0 && (mode < 2 || mode > 4)) return cudaErrorInvalidValue;
   const int threads = 256;
   const int blocks = blocks_for(G.ncell, threads, nsm * 16);
-  if (ndim == 1) diff_launch<1, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
+  if (ndim == 1) diff_launch<1, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
   else if (ndim == 2) {
-    if (dir == 0) diff_launch<2, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
-    else diff_launch<2, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
+    if (dir == 0) diff_launch<2, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
+    else diff_launch<2, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
   } else {
-    if (dir == 0) diff_launch<3, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
-    else if (dir == 1) diff_launch<3, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
-    else diff_launch<3, 2>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, acc);
+    if (dir == 0) diff_launch<3, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
+    else if (dir == 1) diff_launch<3, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
+    else diff_launch<3, 2>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
   }
   return cudaGetLastError();
 }
@@ -602,9 +620,7 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
     if (launch_flux(g->ndim, d, U, aux, fh, alpha, Fhat, nullptr, list, count + d, status, G, S, nsm, st,
                     nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
-    const bool last = (d == g->ndim - 1);
-    const int m = last ? mode : (d == 0 ? 0 : 1);
-    if (launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt, G, m, d > 0 ? 1 : 0, nsm, st) != cudaSuccess)
+    if (launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt, G, mode, nsm, st) != cudaSuccess)
       return TENO_ERR_CUDA;
   }
   return TENO_OK;

@@ -38,9 +38,15 @@ cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, c
 constexpr size_t kPendingCountOffset = 9 * sizeof(unsigned long long);
 constexpr size_t kAlphaAndCountBytes = kPendingCountOffset + 3 * sizeof(unsigned);
 
+// The difference of direction `dir` (called for dir = 0..ndim-1 in order,
+// each after that direction's fluxes are in Fhat).  R carries the unscaled
+// partial sum between the calls (see diff_kernel).  mode 0: the last
+// direction writes L(U) into R; 2, 3, 4: the last direction writes the
+// SSP-RK3 stage (eq. 4.1-4.3) into Uout, with dt read from the device word
+// `dt` (dt <= 0: the state is left unchanged, stage buffers take Un).
 cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
                         const double* Un, const double* Uk, double* Uout,
-                        const double* dt, const Grid& G, int mode, int acc,
+                        const double* dt, const Grid& G, int mode,
                         int nsm, cudaStream_t st);
 
 cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,

@@ -140,8 +140,8 @@ extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, dou
     if (teno::launch_flux(g->ndim, d, U, aux, nullptr, alpha, Fhat, nullptr, nullptr, nullptr, status, G, S, nsm, st,
                           nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
-    if (teno::launch_diff(g->ndim, d, Fhat, dUdt, nullptr, nullptr, nullptr, nullptr, G,
-                          d == 0 ? 0 : 1, d > 0 ? 1 : 0, nsm, st) != cudaSuccess)
+    if (teno::launch_diff(g->ndim, d, Fhat, dUdt, nullptr, nullptr, nullptr, nullptr, G, 0, nsm,
+                          st) != cudaSuccess)
       return TENO_ERR_CUDA;
   }
   return TENO_OK;
