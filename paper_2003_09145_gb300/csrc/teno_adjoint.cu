@@ -588,6 +588,7 @@ Grid make_grid(const teno_grid* g) {
     G.bc[k] = k < g->ndim ? g->bc[k] : 0;
     G.dx[k] = k < g->ndim ? g->dx[k] : 1.0;
     G.inv_dx[k] = 1.0 / G.dx[k];
+    G.rdx[k] = G.dx[0] / G.dx[k];
   }
   G.ncell = g->n[0] * g->n[1] * g->n[2];
   return G;

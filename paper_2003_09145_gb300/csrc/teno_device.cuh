@@ -103,6 +103,7 @@ struct Grid {
   int bc[3];           // 0 periodic, 1 transmissive
   double dx[3];
   double inv_dx[3];
+  double rdx[3];       // dx[0] / dx[k] (exactly 1 for equal spacings)
 };
 
 // Index of a (possibly ghost) cell along an axis of n cells: periodic wrap,

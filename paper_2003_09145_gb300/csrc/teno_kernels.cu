@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) diff_kernel(
   const int64_t ncell = G.ncell;
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
   const int64_t nifc = m0 * m1 * (G.n[2] + (DIR == 2));
-  const double rd = G.dx[0] / G.dx[DIR];   // exactly 1 for equal spacings
+  const double rd = G.rdx[DIR];
   double c = 0.0;
   if (stage) {
     const double dt = *dt_ptr;
@@ -598,6 +598,7 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
     G.bc[k] = k < g->ndim ? g->bc[k] : 0;
     G.dx[k] = k < g->ndim ? g->dx[k] : 1.0;
     G.inv_dx[k] = 1.0 / G.dx[k];
+    G.rdx[k] = G.dx[0] / G.dx[k];
   }
   G.ncell = g->n[0] * g->n[1] * g->n[2];
   const Scheme S = make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);

@@ -121,6 +121,7 @@ extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, dou
     G.bc[k] = k < g->ndim ? g->bc[k] : 0;
     G.dx[k] = k < g->ndim ? g->dx[k] : 1.0;
     G.inv_dx[k] = 1.0 / G.dx[k];
+    G.rdx[k] = G.dx[0] / G.dx[k];
   }
   G.ncell = int64_t(ncell);
   const teno::Scheme S = teno::make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);
