@@ -387,11 +387,13 @@ TENO_HD inline void roe_point_vjp(double ir, const double (&u)[NDIM], double q, 
   constexpr int E = NDIM + 1;
   const double gm1 = gamma - 1.0;
   double uub = 0.0;
-  for (int k = 0; k < NDIM; ++k) uub += u[k] * uxb[k];
+  for (int k = 0; k < NDIM; ++k) uub = fma(u[k], uxb[k], uub);
   const double pb = Hxb * ir;
-  out[0] += 0.5 * sx * ir * sxb - Hx * pb + 0.5 * gm1 * q * pb - ir * uub;
-  for (int k = 0; k < NDIM; ++k) out[1 + k] += ir * uxb[k] - gm1 * u[k] * pb;
-  out[E] += pb + gm1 * pb;
+  // d/drho: sx/(2 rho) sxb + pb ((gamma-1) q/2 - Hx) - u.uxb / rho
+  out[0] += fma(0.5 * sx * ir, sxb, fma(pb, fma(0.5 * gm1, q, -Hx), -ir * uub));
+  const double gpb = gm1 * pb;
+  for (int k = 0; k < NDIM; ++k) out[1 + k] += fma(ir, uxb[k], -gpb * u[k]);
+  out[E] = fma(gamma, pb, out[E]);   // pb + (gamma-1) pb
 }
 
 // The interface part of the all-kept VJP: from the Roe state of cells i,
@@ -408,87 +410,83 @@ TENO_HD inline void interface_vjp_kept_ifc(const RoeState<NDIM>& R, const double
   constexpr int E = NDIM + 1;
   constexpr int N = DIR;
   const double gm1 = gamma - 1.0;
-  const double sa = R.sa, sb = R.sb, iS = R.iS, Ha = R.Ha, Hb = R.Hb, H = R.H;
-  const double q2 = R.q2, ic = R.ic, ic2 = R.ic2, c = R.c, b1 = R.b1, b2 = R.b2;
+  const double sa = R.sa, sb = R.sb, iS = R.iS, H = R.H;
+  const double q2 = R.q2, ic = R.ic, ic2 = R.ic2, c = R.c, b1 = R.b1;
+  const double hb1 = 0.5 * b1, hb2 = 0.5 * R.b2, hic = 0.5 * ic;
   const double* ut = R.ut;
   const double un = ut[N];
 
   // l_0 . X = A + B, l_E . X = A - B with A = (b2 X0 - b1 (u.Xm - XE))/2, B = (un X0 - X_{1+n})/(2c)
   double Sx = -Ut[E];
-  for (int k = 0; k < NDIM; ++k) Sx += ut[k] * Ut[1 + k];
-  const double Ax = 0.5 * (b2 * Ut[0] - b1 * Sx);
-  const double Bx = 0.5 * (un * Ut[0] - Ut[1 + N]) * ic;
+  for (int k = 0; k < NDIM; ++k) Sx = fma(ut[k], Ut[1 + k], Sx);
+  const double Ax = fma(hb2, Ut[0], -hb1 * Sx);
+  const double Bx = fma(un, Ut[0], -Ut[1 + N]) * hic;
   const double l0U = Ax + Bx, lEU = Ax - Bx;
   // r_0 . Fb and r_E . Fb
-  double rs = Fb[0];
-  for (int k = 0; k < NDIM; ++k) rs += ut[k] * Fb[1 + k];
-  rs += H * Fb[E];
-  const double rd = c * (Fb[1 + N] + un * Fb[E]);
+  double rs = fma(H, Fb[E], Fb[0]);
+  for (int k = 0; k < NDIM; ++k) rs = fma(ut[k], Fb[1 + k], rs);
+  const double rdn = fma(un, Fb[E], Fb[1 + N]);
+  const double rd = c * rdn;
   const double rho0 = rs - rd, rhoE = rs + rd;
   const double amid = alpha[1];
   const double d0 = alpha[0] - amid, dE = alpha[E] - amid;
   const double g0 = d0 * l0U, gE = dE * lEU;
 
   // ---- alpha ---------------------------------------------------------------
-  double FU = 0.0;
-  for (int v = 0; v < NV; ++v) FU += Fb[v] * Ut[v];
+  double FU = Fb[0] * Ut[0];
+  for (int v = 1; v < NV; ++v) FU = fma(Fb[v], Ut[v], FU);
   for (int s = 0; s < NV; ++s) ab[s] = 0.0;
   ab[0] = rho0 * l0U;
   ab[E] = rhoE * lEU;
-  ab[1] = FU - rho0 * l0U - rhoE * lEU;
+  ab[1] = FU - ab[0] - ab[E];
 
   // ---- U~ bar = a_mid Fb + d0 rho0 l_0 + dE rhoE l_E ---------------------------
   const double w0 = d0 * rho0, wE = dE * rhoE;
-  Utb[0] = amid * Fb[0] + 0.5 * (b2 * (w0 + wE) + un * ic * (w0 - wE));
-  for (int k = 0; k < NDIM; ++k)
-    Utb[1 + k] = amid * Fb[1 + k] - 0.5 * b1 * ut[k] * (w0 + wE) - (k == N ? 0.5 * ic * (w0 - wE) : 0.0);
-  Utb[E] = amid * Fb[E] + 0.5 * b1 * (w0 + wE);
+  const double sX = w0 + wE, dX = w0 - wE;
+  const double hb1sX = hb1 * sX, hicdX = hic * dX;
+  Utb[0] = fma(amid, Fb[0], fma(hb2, sX, un * hicdX));
+  for (int k = 0; k < NDIM; ++k) {
+    double t = fma(-hb1sX, ut[k], amid * Fb[1 + k]);
+    if (k == N) t -= hicdX;
+    Utb[1 + k] = t;
+  }
+  Utb[E] = fma(amid, Fb[E], hb1sX);
 
   // ---- gradients of the Roe parameters -------------------------------------
-  // L rows 0 and E are contracted with X0 = w0 U~ and XE = wE U~; R columns 0
-  // and E with fchar_0 = g0, fchar_E = gE (the other rows / columns do not
-  // enter the closed form).
+  // L rows 0 and E contracted with X0 = w0 U~ and XE = wE U~ (the terms of
+  // l_0 and l_E in b2, b1, u~ and c), R columns 0 and E with fchar_0 = g0,
+  // fchar_E = gE (the other rows / columns do not enter the closed form),
+  // with sX = w0 + wE, dX = w0 - wE:
+  //   b2bar = sX U~_0 / 2,   b1bar = -sX Sx / 2 + q2 b2bar / 2,
+  //   cbar  = dX (U~_{1+n} - un U~_0) / (2 c^2) + (gE - g0)(Fb_{1+n} + un Fb_E),
+  // and U~_{1+n} - un U~_0 = -2 c B, so the first term of cbar is -dX B / c.
   double utb[NDIM];
-  for (int k = 0; k < NDIM; ++k) utb[k] = 0.0;
-  double Hbar = 0.0, cb = 0.0, b1b = 0.0, b2b = 0.0, q2b = 0.0;
-  {
-    const double sX = w0 + wE, dX = w0 - wE;
-    b2b += 0.5 * sX * Ut[0];
-    utb[N] += 0.5 * ic * dX * Ut[0];
-    cb += -0.5 * un * ic2 * dX * Ut[0];
-    for (int k = 0; k < NDIM; ++k) {
-      b1b += -0.5 * ut[k] * sX * Ut[1 + k];
-      utb[k] += -0.5 * b1 * sX * Ut[1 + k];
-    }
-    cb += 0.5 * ic2 * dX * Ut[1 + N];
-    b1b += 0.5 * sX * Ut[E];
-  }
-  {
-    const double fs = g0 + gE, fd = gE - g0;
-    for (int k = 0; k < NDIM; ++k) utb[k] += Fb[1 + k] * fs;
-    cb += Fb[1 + N] * fd;
-    Hbar += Fb[E] * fs;
-    utb[N] += c * Fb[E] * fd;
-    cb += un * Fb[E] * fd;
-  }
-  b1b += 0.5 * q2 * b2b;
-  q2b += 0.5 * b1 * b2b;
-  const double c2b = -(b1 * ic2) * b1b + 0.5 * ic * cb;
-  Hbar += gm1 * c2b;
-  q2b += -0.5 * gm1 * c2b;
-  for (int k = 0; k < NDIM; ++k) utb[k] += 2.0 * ut[k] * q2b;
-  double uab[NDIM], ubb[NDIM], sab = 0.0, sbb = 0.0;
+  const double fs = g0 + gE, fd = gE - g0;
+  for (int k = 0; k < NDIM; ++k) utb[k] = fma(-hb1sX, Ut[1 + k], Fb[1 + k] * fs);
+  utb[N] += fma(hicdX, Ut[0], c * Fb[E] * fd);
+  const double b2b = 0.5 * sX * Ut[0];
+  const double b1b = fma(0.5 * q2, b2b, -0.5 * sX * Sx);
+  const double cb = fma(-(ic * dX), Bx, fd * rdn);
+  double q2b = hb1 * b2b;
+  const double c2b = fma(-(b1 * ic2), b1b, hic * cb);
+  const double Hbar = fma(gm1, c2b, Fb[E] * fs);
+  q2b = fma(-0.5 * gm1, c2b, q2b);
+  const double tq = 2.0 * q2b;
+  for (int k = 0; k < NDIM; ++k) utb[k] = fma(tq, ut[k], utb[k]);
+  // u~ = (sa ua + sb ub)/S and H~ = (sa Ha + sb Hb)/S, S = sa + sb, so
+  // d/dsa = sb (x_a - x_b)/S^2 and d/dsb = -sa (x_a - x_b)/S^2 for x = u, H
+  double Dsum = (R.Ha - R.Hb) * Hbar;
+  for (int k = 0; k < NDIM; ++k) Dsum = fma(R.ua[k] - R.ub[k], utb[k], Dsum);
+  const double tS = iS * iS * Dsum;
+  const double saS = sa * iS, sbS = sb * iS;
+  double uab[NDIM], ubb[NDIM];
   for (int k = 0; k < NDIM; ++k) {
-    uab[k] = sa * iS * utb[k];
-    ubb[k] = sb * iS * utb[k];
-    sab += (R.ua[k] - ut[k]) * iS * utb[k];
-    sbb += (R.ub[k] - ut[k]) * iS * utb[k];
+    uab[k] = saS * utb[k];
+    ubb[k] = sbS * utb[k];
   }
-  sab += (Ha - H) * iS * Hbar;
-  sbb += (Hb - H) * iS * Hbar;
   for (int v = 0; v < NV; ++v) roeA[v] = roeB[v] = 0.0;
-  roe_point_vjp<NDIM>(R.ira, R.ua, R.qa, sa, Ha, gamma, sab, sa * iS * Hbar, uab, roeA);
-  roe_point_vjp<NDIM>(R.irb, R.ub, R.qb, sb, Hb, gamma, sbb, sb * iS * Hbar, ubb, roeB);
+  roe_point_vjp<NDIM>(R.ira, R.ua, R.qa, sa, R.Ha, gamma, sb * tS, saS * Hbar, uab, roeA);
+  roe_point_vjp<NDIM>(R.irb, R.ub, R.qb, sb, R.Hb, gamma, -sa * tS, sbS * Hbar, ubb, roeB);
 }
 
 // The whole all-kept VJP of one interface, as interface_vjp (same inputs and
