@@ -316,8 +316,8 @@ constexpr int kDiffFirst = 0, kDiffAcc = 1, kDiffRhs = 5;
 template <int NDIM, int DIR, int MODE>
 __global__ void __launch_bounds__(256) diff_kernel(
     const double* __restrict__ Fhat, double* __restrict__ R,
-    const double* __restrict__ Un, const double* __restrict__ Uk,
-    double* __restrict__ Uout, const double* __restrict__ dt_ptr, Grid G) {
+    const double* Un, const double* Uk,   // not restrict: stage 3 writes Uout = Un in place
+    double* Uout, const double* __restrict__ dt_ptr, Grid G) {
   constexpr bool stage = MODE >= 2 && MODE <= 4;
   constexpr bool acc = DIR > 0;   // R holds the earlier directions' sum
   constexpr int NVAR = NDIM + 2;

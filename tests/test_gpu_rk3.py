@@ -50,12 +50,16 @@ def _oracle_run(oracle, P, steps, t_end=None, dt_fixed=0.0):
     ("shu_osher", 100),
     ("riemann2d", 20),
     ("turb3d", 6),
+    ("smooth3d_aniso", 8),  # three different spacings: the ratios dx_0/dx_d differ from 1
 ])
 def test_fixed_steps(api, oracle, case, steps):
     P = {"sod": lambda: inputs.shock_tube(200),
          "shu_osher": lambda: inputs.shu_osher(4096),
          "riemann2d": lambda: inputs.riemann_2d(n=128, t_end=10.0),
-         "turb3d": lambda: inputs.solenoidal_turbulence(n=24, t_end=10.0)}[case]()
+         "turb3d": lambda: inputs.solenoidal_turbulence(n=24, t_end=10.0),
+         "smooth3d_aniso": lambda: inputs.Problem(
+             "s3a", inputs.random_smooth_state(3, (14, 11, 9), seed=21, amp=0.03), (14, 11, 9),
+             (0.1, 0.07, 0.13), (0, 1, 0), 10.0)}[case]()
     Ug, tg, dg = _gpu_run(api, P, steps)
     Uo, to, do = _oracle_run(oracle, P, steps)
     err = rel_l1_err(Ug, Uo)
