@@ -36,20 +36,20 @@ FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
 # formulas the kernel evaluates in binary64 (add/mul = 1 flop, FMA = 2,
 # divide / rsqrt = 1).
 # * Every stencil kept at all ten reconstructions (certified in FP32): the
-#   closed form F~ + a_mid U~ + acoustic corrections -- Roe average 26 (from
-#   the cell pass's sqrt(rho) u/2: 1/(sr_a + sr_b), u~ 6, |u~|^2 5, H~ 2,
+#   closed form F~ + a_mid U~ + acoustic corrections -- Roe average 25 (from
+#   the cell pass's m/sqrt(rho): 1/(sr_a + sr_b), u~ 6, |u~|^2 5, H~ 2,
 #   c^2 3, rsqrt, c, the halved coefficients 5), per point 20 (the
 #   P-weighted sum of the cell pass's F/2 and the M-weighted sum of U),
 #   l_0.U~ and l_E.U~ as A +- B 12, the combined corrections 6 and the
-#   output 24: 188.  (Forming F_d/2 costs 5 flops per cell and direction in
+#   output 24: 187.  (Forming F_d/2 costs 5 flops per cell and direction in
 #   the cell pass, plus E + p once; its mass component m_d/2 is not formed:
 #   the P-weighted sum takes m_d itself.)
-# * Otherwise the characteristic path: Roe 28, projection 6 x 20, split 6 x 28,
-#   sum 5, back-projection 21 (= 342), plus per scalar reconstruction 9 when
+# * Otherwise the characteristic path: Roe 27, projection 6 x 20, split 6 x 28,
+#   sum 5, back-projection 21 (= 341), plus per scalar reconstruction 9 when
 #   its own FP32 pre-test keeps every stencil, else 38 for the binary64
 #   indicators, m and weights plus 21 for the cutoff test.
-ALG_CLOSED_3D = 188
-ALG_FIXED_3D = 342
+ALG_CLOSED_3D = 187
+ALG_FIXED_3D = 341
 ALG_PER_RECON_KEEP = 9
 ALG_PER_RECON = 38
 ALG_CUTOFF = 21

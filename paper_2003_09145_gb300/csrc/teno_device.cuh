@@ -66,7 +66,7 @@ static __constant__ double c_lin[8][5] = {
 
 constexpr int kMaxDim = 3;
 // Per-cell primitive fields the cell pass writes (aux, [aux_fields][ncell]):
-// u_k/2 (ndim), p/2, sqrt(rho), (E+p)/sqrt(rho), sqrt(rho) u_k/2 (ndim).
+// u_k/2 (ndim), p/2, sqrt(rho), (E+p)/sqrt(rho), m_k/sqrt(rho) = sqrt(rho) u_k (ndim).
 __host__ __device__ constexpr int aux_fields(int ndim) { return 2 * ndim + 3; }
 constexpr int kMaxVar = 5;
 constexpr int kMaxLadder = 16;

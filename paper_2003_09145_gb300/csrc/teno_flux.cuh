@@ -73,7 +73,7 @@ __device__ __forceinline__ bool certify_keep(float v0, float v1, float v2, float
 
 // ---------------------------------------------------------------------------
 // Roe state of the interface i+1/2 from the per-cell primitives of cells i
-// and i+1 (sqrt(rho), (E+p)/sqrt(rho) and su = sqrt(rho) u/2):
+// and i+1 (sqrt(rho), (E+p)/sqrt(rho) and su = sqrt(rho) u = m/sqrt(rho)):
 // u~ = (sr_a u_a + sr_b u_b)/(sr_a + sr_b), H~ = (sh_a + sh_b)/(sr_a + sr_b),
 // c~^2 = (gamma-1)(H~ - |u~|^2/2), b1 = (gamma-1)/c~^2, b2 = b1 |u~|^2/2.
 // ---------------------------------------------------------------------------
@@ -87,11 +87,10 @@ __device__ __forceinline__ void roe_interface(double sr2, double sr3, double sh2
                                               const double (&su2)[NDIM], const double (&su3)[NDIM],
                                               const Scheme& S, RoeIfc<NDIM>& R, int* __restrict__ status) {
   const double y = recip_pos(sr2 + sr3);
-  const double inv2 = 2.0 * y;
   R.q2 = 0.0;
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
-    R.u[k] = (su2[k] + su3[k]) * inv2;
+    R.u[k] = (su2[k] + su3[k]) * y;
     R.q2 = fma(R.u[k], R.u[k], R.q2);
   }
   R.H = (sh2 + sh3) * y;
@@ -522,7 +521,8 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
 // 1/sqrt(rho), sqrt(rho) = rho/sqrt(rho), 1/(2 rho) = (1/sqrt(rho))^2 / 2,
 // u/2 = m/(2 rho), p = (gamma-1)(E - 2 rho |u/2|^2) (eq. 4.7),
 // c = sqrt(gamma p / rho).  Writes the aux entries (u_k/2, p/2, sqrt(rho),
-// (E+p)/sqrt(rho), sqrt(rho) u_k/2 -- the Roe average's weighted velocities)
+// (E+p)/sqrt(rho), sqrt(rho) u_k = m_k/sqrt(rho) -- the Roe average's
+// weighted velocities)
 // and returns uh = u/2, c and E + p; false if the state is not physical
 // (rho <= 0, p <= 0 or non-finite).  Working with u/2 saves the halving
 // multiplies; every value equals the u-based evaluation's bit for bit,
@@ -555,7 +555,7 @@ __device__ __forceinline__ bool cell_primitives(const double* __restrict__ U, in
   aux[(NDIM + 1) * ncell + c] = sr;
   aux[(NDIM + 2) * ncell + c] = ep * isr;
 #pragma unroll
-  for (int k = 0; k < NDIM; ++k) aux[(NDIM + 3 + k) * ncell + c] = sr * uh[k];
+  for (int k = 0; k < NDIM; ++k) aux[(NDIM + 3 + k) * ncell + c] = U[(1 + k) * ncell + c] * isr;
   return pos_finite(rho) && pos_finite(p) && is_finite(E) && is_finite(q2h) && pos_finite(gpr);
 }
 

@@ -29,7 +29,7 @@ namespace teno {
 // (cell_primitives); the wave speeds |u_d - c|, |u_d|, |u_d + c| are reduced
 // to their maxima over all cells.
 // aux layout: [aux_fields(ndim) = 2 ndim + 3][ncell]: u_0/2..u_{ndim-1}/2,
-// p/2, sqrt(rho), (E+p)/sqrt(rho), sqrt(rho) u_0/2..sqrt(rho) u_{ndim-1}/2.
+// p/2, sqrt(rho), (E+p)/sqrt(rho), m_0/sqrt(rho)..m_{ndim-1}/sqrt(rho).
 // With `fh`, also the half physical fluxes F_d/2 (eq. 4.7)
 // of every direction, momentum and energy components only (the mass one is
 // m_d/2), [ndim][nvar - 1][ncell], for the closed-form flux pass.
