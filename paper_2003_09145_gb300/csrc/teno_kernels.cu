@@ -50,8 +50,11 @@ __device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], co
   }
 }
 
+#ifndef TENO_CELL_MINBLOCKS
+#define TENO_CELL_MINBLOCKS 2   // 128 registers, 16 warps per SM: measured 0.1 ms per step
+#endif                          // faster than 3 (80 registers) or 4 (64)
 template <int NDIM>
-__global__ void __launch_bounds__(256, 3) cell_kernel(const double* __restrict__ U,
+__global__ void __launch_bounds__(256, TENO_CELL_MINBLOCKS) cell_kernel(const double* __restrict__ U,
                                                    double* __restrict__ aux,
                                                    double* __restrict__ fh,
                                                    unsigned long long* __restrict__ alpha,
