@@ -40,7 +40,7 @@ struct BatchArgs {
   const double* Un;    // U^n
   const double* Uk;    // U1 (stage 2) or U2 (stage 3)
   double* Uout;        // U1, U2 or U^{n+1}
-  double* aux;         // [4][ncell]
+  double* aux;         // [aux_fields(1) = 5][ncell] (the grid path's per-cell primitives)
   double* fh;          // [2][ncell]: F/2 of every cell (eq. 4.7), momentum and energy
   const int64_t* offsets;
   const double* dx;
