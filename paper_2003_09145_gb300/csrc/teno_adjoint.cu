@@ -383,28 +383,56 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
     double acc[NVAR], Fsum[NVAR];
     for (int v = 0; v < NVAR; ++v) acc[v] = Fsum[v] = 0.0;
     const int idl = int(id), ndl = int(nd);
-    // interior cell whose six interfaces (qd = id+3-j) are all kept: the
-    // P-weighted Fbar sum as one stencil on Rbar
-    bool fast = idl >= 3 && idl <= ndl - 4;
-    if (fast)
-      for (int j = 0; j < 6; ++j) fast = fast && pending[q0 + (int64_t)(idl + 3 - j) * sd] == 0;
+    // a cell whose six interfaces are all kept: the P-weighted Fbar sum as
+    // one stencil on Rbar.  Interior cells (slot j's interface qd = id+3-j)
+    // always qualify.  With periodic ends and at least six cells every cell
+    // does: qd and the Rbar stencil wrap modulo nd, and faces 0 and nd --
+    // one physical face computed twice, each copy with its own Fbar -- both
+    // add their terms to the slot whose wrapped interface is 0 (their Fbar
+    // sum is the wrapped difference the stencil already holds).
+    const bool wrap = bc == 0 && ndl >= 6;
+    bool fast = wrap || (idl >= 3 && idl <= ndl - 4);
+    // slot j's interface: id + 3 - j, in [1, nd-1] for an interior cell,
+    // wrapped into [0, nd) otherwise (reached only when `wrap`)
+    auto slot_face = [idl, ndl](int j) {
+      int x = idl + 3 - j;
+      if (x < 0) x += ndl;
+      else if (x >= ndl) x -= ndl;
+      return x;
+    };
+    if (fast) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int x = slot_face(j);
+        fast = fast && pending[q0 + (int64_t)x * sd] == 0 && (x != 0 || pending[q0 + (int64_t)ndl * sd] == 0);
+      }
+    }
     if (fast) {
       const int toff[6] = {-3, -2, -1, 1, 2, 3};
       for (int v = 0; v < NVAR; ++v) {
-        const double* r = Rbar + v * ncell + c;
+        const double* r = Rbar + v * ncell + line;
         double f = 0.0;
 #pragma unroll
-        for (int t = 0; t < 6; ++t) f = fma(c_adjW[t], r[toff[t] * cstride], f);
+        for (int t = 0; t < 6; ++t) {
+          int y = idl + toff[t];
+          if (y < 0) y += ndl;
+          else if (y >= ndl) y -= ndl;
+          f = fma(c_adjW[t], r[(int64_t)y * cstride], f);
+        }
         Fsum[v] = f;
       }
       for (int j = 0; j < 6; ++j) {
-        const int64_t q = q0 + (int64_t)(idl + 3 - j) * sd;
         const double Mj = c_adjM[j];
-        for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
-        if (j == 2)
-          for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(NVAR + v) * nifc + q];
-        if (j == 3)
-          for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+        const int x = slot_face(j);
+        for (int copy = 0; copy < 2; ++copy) {
+          if (copy == 1 && x != 0) break;
+          const int64_t q = q0 + (int64_t)(copy == 0 ? x : ndl) * sd;
+          for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
+          if (j == 2)
+            for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(NVAR + v) * nifc + q];
+          if (j == 3)
+            for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+        }
       }
     }
     for (int j = 0; j < 6 && !fast; ++j) {
