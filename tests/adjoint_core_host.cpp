@@ -25,6 +25,16 @@ void run(int kept, const double* up, const double* al, double gamma, const doubl
 
 }  // namespace
 
+extern "C" void adj_flux_vjp3(int dir, const double* u, double gamma, const double* g, double* out) {
+  double U[5], G[5], O[5];
+  std::memcpy(U, u, sizeof(U));
+  std::memcpy(G, g, sizeof(G));
+  if (dir == 0) teno_adj::flux_vjp<3, 0>(U, gamma, G, O);
+  else if (dir == 1) teno_adj::flux_vjp<3, 1>(U, gamma, G, O);
+  else teno_adj::flux_vjp<3, 2>(U, gamma, G, O);
+  std::memcpy(out, O, sizeof(O));
+}
+
 extern "C" void adj_interface_vjp3(int dir, int kept, const double* up, const double* al, double gamma,
                                    const double* fb, double* ub, double* ab) {
   if (dir == 0) run<0>(kept, up, al, gamma, fb, ub, ab);

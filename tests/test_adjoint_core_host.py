@@ -2,9 +2,10 @@
 closed form (interface_vjp_kept, the one the adjoint kernels use where every
 stencil is kept) against the general frozen-selection VJP (interface_vjp)
 with every stencil selected -- two independent derivations of the same
-derivative -- and both against central differences of the closed-form flux
-restated here from the paper's linear weights (eq. 2.3) and Roe
-eigensystem."""
+derivative -- and the closed form against central differences of the
+flux restated here from the paper's linear weights (eq. 2.3) and Roe
+eigensystem; and the per-cell flux Jacobian transpose against central
+differences of eq. 4.7."""
 import ctypes
 import os
 import subprocess
@@ -27,6 +28,8 @@ def lib():
     P = ctypes.POINTER(ctypes.c_double)
     L.adj_interface_vjp3.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_double, P, P, P]
     L.adj_interface_vjp3.restype = None
+    L.adj_flux_vjp3.argtypes = [ctypes.c_int, P, ctypes.c_double, P, P]
+    L.adj_flux_vjp3.restype = None
     return L
 
 
@@ -130,3 +133,32 @@ def test_kept_vjp_matches_central_differences(lib, d):
             Pm[j, v] -= h
             fd = Fb @ (_closed_flux(Pp, alpha, d) - _closed_flux(Pm, alpha, d)) / (2 * h)
             assert abs(ub[j, v] - fd) <= 1e-7 * max(1.0, abs(fd)), (j, v)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_flux_jacobian_transpose_matches_central_differences(lib, d):
+    """flux_vjp = A(U)^T G with A = dF_d/dU (eq. 4.7), the per-cell product
+    the adjoint gather applies once per cell."""
+    rng = np.random.default_rng(300 + d)
+
+    def flux(U):
+        rho, m, E = U[0], U[1:4], U[4]
+        u = m / rho
+        p = (GAMMA - 1) * (E - 0.5 * rho * u @ u)
+        F = u[d] * U
+        F[1 + d] += p
+        F[4] += p * u[d]
+        return F
+
+    for _ in range(5):
+        U = _state(rng)[0]
+        G = rng.standard_normal(5)
+        out = np.zeros(5)
+        lib.adj_flux_vjp3(d, _p(np.ascontiguousarray(U)), GAMMA, _p(np.ascontiguousarray(G)), _p(out))
+        h = 1e-6
+        for v in range(5):
+            Up, Um = U.copy(), U.copy()
+            Up[v] += h
+            Um[v] -= h
+            fd = G @ (flux(Up) - flux(Um)) / (2 * h)
+            assert abs(out[v] - fd) <= 1e-7 * max(1.0, abs(fd)), v
