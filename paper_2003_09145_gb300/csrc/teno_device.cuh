@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "teno_cert.cuh"
+
 namespace teno {
 
 // Ladder of eq. 3.3: c_lad[m] = 10^-m written as decimal literals, so
@@ -85,9 +87,8 @@ struct Scheme {
   int top;        // largest power of two <= nthr (binary-search start)
   unsigned keep_all;  // bit m set: every chi_k >= C_T is guaranteed at this m
   int keep_idx;   // keep_all = {m >= B_l + keep_idx + 1}: tau <= thr[keep_idx] dmin (-1: none)
-  float thr_keep_f;   // thr[keep_idx] rounded down to binary32
+  float thr_keep_f;   // thr[keep_idx] rounded down to binary32 (0: no FP32 pre-test)
   float eps4_f;       // 4 eps rounded down to binary32
-  float kerr_f;       // 10000 * 2^-24: error bound factor of the FP32 pre-test
   // m = B_l + #{ j in 1..B_u-B_l : tau <= thr[j-1] * min_k(beta_k + eps) }.
   // With theta = 1/(1 + max_k chi~_k / H) and max_k chi~_k = tau / min_k(beta_k
   // + eps) (eq. 3.2), floor(theta (B_u - B_l)) >= j  <=>  max chi~ <=
@@ -166,16 +167,9 @@ __device__ __forceinline__ bool pos_finite(double x) {
 }
 __device__ __forceinline__ bool is_finite(double x) { return (dbits(x) & kExpMask) != kExpMask; }
 
-// binary32 approximation of a double built on the integer pipe from its high
-// word: exponent rebiased, mantissa truncated to 20 bits (|f - x| < 2^-20 |x|),
-// magnitudes clamped to [2^-126, 2^128).
-__device__ __forceinline__ float hi_float(double x) {
-  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
-  unsigned mag = hi & 0x7fffffffu;
-  mag = max(mag, 897u << 20);
-  mag = min(mag, (1150u << 20) | 0xFFFFFu);
-  return __uint_as_float(((mag - (896u << 20)) << 3) | (hi & 0x80000000u));
-}
+// binary32 approximation of a double on the integer pipe (teno_cert.cuh):
+// mantissa truncated to 20 bits, |f - x| < 2^-20 |x| in the normal range.
+__device__ __forceinline__ float hi_float(double x) { return teno_cert::hi_float(x); }
 
 // ---------------------------------------------------------------------------
 // Reciprocal of a positive double with few FP64 instructions (GB300's FP64
@@ -237,34 +231,13 @@ template <bool WITH_M>
 __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
                                             double v3, double v4, double acc,
                                             const Scheme& S, unsigned& flag) {
-  if (!WITH_M && S.keep_idx >= 0) {
-    // Certified single-precision pre-test of "every stencil kept": the scaled
-    // indicators are evaluated in FP32 from 20-bit truncations of the values
-    // (hi_float, integer pipe).  With V = max |v_j| and E = max |e_k| each
-    // differs from its exact value by at most 133 u_c E V + 200 u E^2
-    // <= 2528 u E V (u_c = 2^-20, u = 2^-24; kerr_f carries a further factor
-    // 4), so when tau + 2 err <= thr (dmin - err) holds here, tau <= thr * dmin
-    // holds for the exact values with margin: the binary64 test below and the
-    // bound of Scheme::keep_all would both keep every stencil.  Otherwise fall
-    // through to the binary64 evaluation.
-    const float g0 = hi_float(v0), g1 = hi_float(v1), g2 = hi_float(v2);
-    const float g3 = hi_float(v3), g4 = hi_float(v4);
-    const float Vf = fmaxf(fmaxf(fmaxf(fabsf(g0), fabsf(g1)), fmaxf(fabsf(g2), fabsf(g3))), fabsf(g4));
-    const float f0 = g1 - g0, f1 = g2 - g1, f2 = g3 - g2, f3 = g4 - g3;
-    const float Ef = fmaxf(fmaxf(fabsf(f0), fabsf(f1)), fmaxf(fabsf(f2), fabsf(f3)));
-    const float k13_3f = 13.0f / 3.0f;
-    const float a0f = f1 - f0, a1f = f2 - f1, a2f = f3 - f2;
-    const float c0f = fmaf(3.0f, f1, -f0), c1f = f1 + f2, c2f = fmaf(-3.0f, f2, f3);
-    const float b0f = fmaf(k13_3f * a0f, a0f, c0f * c0f);
-    const float b1f = fmaf(k13_3f * a1f, a1f, c1f * c1f);
-    const float b2f = fmaf(k13_3f * a2f, a2f, c2f * c2f);
-    const float tauf = fabsf(b2f - b0f);
-    const float dminf = fminf(b0f, fminf(b1f, b2f)) + S.eps4_f;
-    const float err = S.kerr_f * Ef * Vf;
-    if (err <= 1.0e38f && tauf + 2.0f * err <= S.thr_keep_f * (dminf - err) * (1.0f - 1e-5f)) {
-      flag = 7u;
-      return fma(c_lin[7][0], v0, fma(c_lin[7][1], v1, fma(c_lin[7][2], v2, fma(c_lin[7][3], v3, fma(c_lin[7][4], v4, acc)))));
-    }
+  if (!WITH_M && S.keep_idx >= 0 &&
+      teno_cert::certify_keep_values(v0, v1, v2, v3, v4, S.thr_keep_f, S.eps4_f)) {
+    // Certified single-precision pre-test (teno_cert.cuh): the exact values
+    // satisfy tau <= thr[keep_idx] * dmin with margin, so the binary64 test
+    // below and the bound of Scheme::keep_all would both keep every stencil.
+    flag = 7u;
+    return fma(c_lin[7][0], v0, fma(c_lin[7][1], v1, fma(c_lin[7][2], v2, fma(c_lin[7][3], v3, fma(c_lin[7][4], v4, acc)))));
   }
   const double e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
   // eq. 2.9-2.11 scaled by 4: 4 beta_k = (13/3) a_k^2 + c_k^2.  Every use of

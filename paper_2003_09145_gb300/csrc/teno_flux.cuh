@@ -39,39 +39,6 @@ __device__ __forceinline__ void project(const double (&X)[NDIM + 2],
 }
 
 // ---------------------------------------------------------------------------
-// Certified single-precision test that one reconstruction keeps every stencil.
-// v0..v4 are FP32 approximations of the split characteristic values, each
-// within `dlt` of its exact value (exact arithmetic on the binary64 state).
-// The scaled indicators of eq. 2.9-2.11 and their error bounds are carried in
-// FP32; the test passes only if tau <= thr * min_k(beta_k + eps) holds for the
-// exact values with margin, in which case the binary64 evaluation and the
-// bound behind Scheme::keep_all both keep every stencil (eq. 2.14 with
-// m >= B_l + keep_idx + 1).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool certify_keep(float v0, float v1, float v2, float v3, float v4,
-                                             float dlt, const Scheme& S) {
-  const float u = 0x1p-24f;
-  const float e0 = v1 - v0, e1 = v2 - v1, e2 = v3 - v2, e3 = v4 - v3;
-  const float a0 = e1 - e0, a1 = e2 - e1, a2 = e3 - e2;
-  const float c0 = fmaf(3.0f, e1, -e0), c1 = e1 + e2, c2 = fmaf(-3.0f, e2, e3);
-  const float k = 13.0f / 3.0f;
-  const float b0 = fmaf(k * a0, a0, c0 * c0);
-  const float b1 = fmaf(k * a1, a1, c1 * c1);
-  const float b2 = fmaf(k * a2, a2, c2 * c2);
-  // error bounds: |e| <= 2 dlt, |a| <= 4 dlt, |c| <= 8 dlt (plus the FP32
-  // rounding of beta itself)
-  const float da = 4.0f * dlt, dc = 8.0f * dlt;
-  const float db0 = fmaf(k * fmaf(2.0f, fabsf(a0), da), da, fmaf(2.0f, fabsf(c0), dc) * dc) + 4.0f * u * b0;
-  const float db1 = fmaf(k * fmaf(2.0f, fabsf(a1), da), da, fmaf(2.0f, fabsf(c1), dc) * dc) + 4.0f * u * b1;
-  const float db2 = fmaf(k * fmaf(2.0f, fabsf(a2), da), da, fmaf(2.0f, fabsf(c2), dc) * dc) + 4.0f * u * b2;
-  const float tau = fabsf(b2 - b0);
-  const float dtau = db0 + db2 + u * tau;
-  const float dmin = fminf(b0, fminf(b1, b2)) + S.eps4_f;
-  const float ddmin = fmaxf(db0, fmaxf(db1, db2)) + u * dmin;
-  return (dtau <= 1.0e38f) && (tau + dtau <= S.thr_keep_f * (dmin - ddmin) * (1.0f - 1e-5f));
-}
-
-// ---------------------------------------------------------------------------
 // Roe state of the interface i+1/2 from the per-cell primitives of cells i
 // and i+1 (sqrt(rho), (E+p)/sqrt(rho) and su = sqrt(rho) u = m/sqrt(rho)):
 // u~ = (sr_a u_a + sr_b u_b)/(sr_a + sr_b), H~ = (sh_a + sh_b)/(sr_a + sr_b),
@@ -107,111 +74,21 @@ __device__ __forceinline__ void roe_interface(double sr2, double sr3, double sh2
   R.hud = 0.5 * R.u[DIR];
 }
 
-// ---------------------------------------------------------------------------
 // Certified FP32 test that all ten reconstructions of the interface keep
-// every stencil.  cert_point takes one stencil point (its state and half
-// u_d, p) to FP32 split characteristic values v+-[j] with the bounds of their
-// absolute evaluation; cert_keep runs certify_keep on every field and side
-// with the accumulated error bound.
-// ---------------------------------------------------------------------------
-template <int NDIM>
-struct CertIfc {
-  float uf[NDIM], hb1f, hb2f, hicf, b1f, hudf, haf[NDIM + 2];
-  float vp32[6][NDIM + 2], vm32[6][NDIM + 2], mp[NDIM + 2], mm[NDIM + 2], vmax;
-};
+// every stencil: teno_cert.cuh (cert_begin, cert_point, cert_keep).
+using teno_cert::CertIfc;
 
 template <int NDIM, int DIR>
 __device__ __forceinline__ void cert_begin(const RoeIfc<NDIM>& R, const double (&alpha)[NDIM + 2],
                                            CertIfc<NDIM>& C) {
-  constexpr int NVAR = NDIM + 2;
-#pragma unroll
-  for (int k = 0; k < NDIM; ++k) C.uf[k] = hi_float(R.u[k]);
-  C.hb1f = hi_float(R.hb1);
-  C.hb2f = hi_float(R.hb2);
-  C.hicf = hi_float(R.hic);
-  // b1 = 2 hb1 and hud = u_d/2 from the truncated values (exact scalings:
-  // the same 2^-20 relative bound, no FP64 work)
-  C.b1f = 2.0f * C.hb1f;
-  C.hudf = 0.5f * C.uf[DIR];
-#pragma unroll
-  for (int f = 0; f < NVAR; ++f) {
-    C.haf[f] = hi_float(alpha[f]);
-    C.mp[f] = C.mm[f] = 0.0f;
-  }
-  C.vmax = 0.0f;
+  teno_cert::cert_begin<NDIM, DIR>(R.u, R.hb1, R.hb2, R.hic, alpha, C);
 }
 
-template <int NDIM, int DIR>
-__device__ __forceinline__ void cert_point(int j, const double (&Uj)[NDIM + 2], double unj, double pnj,
-                                           CertIfc<NDIM>& C) {
-  constexpr int NVAR = NDIM + 2;
-  float X[NVAR], Xa[NVAR];
-#pragma unroll
-  for (int v = 0; v < NVAR; ++v) {
-    X[v] = hi_float(Uj[v]);
-    Xa[v] = fabsf(X[v]);
-  }
-  // projection (same form as project()) and its absolute-value evaluation
-  float Sv = -X[NVAR - 1], Sa = Xa[NVAR - 1];
-#pragma unroll
-  for (int k = 0; k < NDIM; ++k) {
-    Sv = fmaf(C.uf[k], X[1 + k], Sv);
-    Sa = fmaf(fabsf(C.uf[k]), Xa[1 + k], Sa);
-  }
-  const float A = fmaf(C.hb2f, X[0], -C.hb1f * Sv);
-  const float Aa = fmaf(fabsf(C.hb2f), Xa[0], fabsf(C.hb1f) * Sa);
-  const float B = fmaf(C.uf[DIR], X[0], -X[1 + DIR]) * C.hicf;
-  const float Ba = fmaf(fabsf(C.uf[DIR]), Xa[0], Xa[1 + DIR]) * fabsf(C.hicf);
-  float w[NVAR], wa[NVAR];
-  w[0] = A + B;
-  wa[0] = Aa + Ba;
-  w[1] = fmaf(-2.0f, A, X[0]);
-  wa[1] = fmaf(2.0f, Aa, Xa[0]);
-  {
-    int f = 2;
-#pragma unroll
-    for (int t = 0; t < NDIM; ++t) {
-      if (t == DIR) continue;
-      w[f] = fmaf(-C.uf[t], X[0], X[1 + t]);
-      wa[f] = fmaf(fabsf(C.uf[t]), Xa[0], Xa[1 + t]);
-      ++f;
-    }
-  }
-  w[NVAR - 1] = A - B;
-  wa[NVAR - 1] = Aa + Ba;
-  const float huf = hi_float(unj), hpf = hi_float(pnj);
-  const float az = hpf * (C.b1f * (huf - C.hudf));
-  const float aza = fabsf(hpf) * (fabsf(C.b1f) * (fabsf(huf) + fabsf(C.hudf)));
-  const float bz = hpf * C.hicf, bza = fabsf(hpf) * fabsf(C.hicf);
-#pragma unroll
-  for (int f = 0; f < NVAR; ++f) {
-    const float t = (f == 0) ? az - bz : (f == NVAR - 1) ? az + bz : (f == 1) ? -2.0f * az : 0.0f;
-    const float ta = (f == 0 || f == NVAR - 1) ? aza + bza : (f == 1) ? 2.0f * aza : 0.0f;
-    C.vp32[j][f] = fmaf(huf + C.haf[f], w[f], t);
-    C.vm32[j][f] = fmaf(-2.0f * C.haf[f], w[f], C.vp32[j][f]);
-    const float pa = fmaf(fabsf(huf) + C.haf[f], wa[f], ta);
-    const float ma = fmaf(2.0f * C.haf[f], wa[f], pa);
-    if (j <= 4) C.mp[f] = fmaxf(C.mp[f], pa);
-    if (j >= 1) C.mm[f] = fmaxf(C.mm[f], ma);
-    C.vmax = fmaxf(C.vmax, fmaxf(fabsf(C.vp32[j][f]), fabsf(C.vm32[j][f])));
-  }
-}
+using teno_cert::cert_point;
 
 template <int NDIM>
 __device__ __forceinline__ bool cert_keep(const CertIfc<NDIM>& C, const Scheme& S) {
-  constexpr int NVAR = NDIM + 2;
-  // |v32 - v| <= 8 * 2^-20 * (absolute evaluation) + 8 u max|v|: the
-  // inputs are 20-bit truncations, each FP32 operation adds 2^-24
-  const float kd = 8.0f * 0x1p-20f, ku = 8.0f * 0x1p-24f * C.vmax;
-  bool keep = true;
-#pragma unroll
-  for (int f = 0; f < NVAR; ++f) {
-    keep = keep && certify_keep(C.vp32[0][f], C.vp32[1][f], C.vp32[2][f], C.vp32[3][f], C.vp32[4][f],
-                                fmaf(kd, C.mp[f], ku), S);
-    keep = keep && certify_keep(C.vm32[5][f], C.vm32[4][f], C.vm32[3][f], C.vm32[2][f], C.vm32[1][f],
-                                fmaf(kd, C.mm[f], ku), S);
-  }
-  return keep;
+  return teno_cert::cert_keep<NDIM>(C, S.thr_keep_f, S.eps4_f);
 }
 
 // ---------------------------------------------------------------------------
