@@ -292,7 +292,9 @@ teno_status teno_scalar_rk3_step(const teno_grid* g, double a, int mode, double*
  * up to 131,065 cells; in 2D 308^2; in 3D 42^3.
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before capturing
- * a stream into a CUDA graph.
+ * a stream into a CUDA graph.  The cached address dies with the device's
+ * context: after cudaDeviceReset on a device, do not call this entry point on
+ * that device again in the same process.
  * All calls share the one array and each call starts by clearing the parts
  * that must start at zero, so calls whose work overlaps on the GPU (other
  * streams, other host threads) race and give wrong results: serialise them.

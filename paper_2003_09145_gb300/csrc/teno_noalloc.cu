@@ -8,6 +8,7 @@
 // the workspace that teno_rhs takes.  This entry point runs the same kernels
 // as teno_rhs with the workspace carved from one file-scope device array of
 // fixed size, so it never allocates.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -37,7 +38,9 @@ size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Device address of the scratch array on the current device.  In host code
 // the symbol g_noalloc_scratch is only a host-side stand-in, so the address is
-// looked up once per device (with that device current) and cached.
+// looked up once per device (with that device current) and cached.  The cache
+// does not survive cudaDeviceReset (the context that held the array is gone):
+// a process that resets a device must not call teno_rhs_noalloc on it again.
 teno_status scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TENO_ERR_CUDA;
@@ -65,6 +68,7 @@ bool grid_valid(const teno_grid* g) {
       return false;
   }
   if (!(g->gamma > 1.0) || !(g->H > 0.0) || !(g->eps > 0.0)) return false;
+  if (!std::isfinite(g->gamma) || !std::isfinite(g->H) || !std::isfinite(g->eps)) return false;
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
   return true;
 }
