@@ -44,20 +44,29 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("H", ctypes.c_double), ("eps", ctypes.c_double),
-                ("b_l", ctypes.c_int), ("b_u", ctypes.c_int)]
+                ("b_l", ctypes.c_int), ("b_u", ctypes.c_int), ("scheme", ctypes.c_int), ("ct_m", ctypes.c_int)]
+
+
+# The reconstruction's cutoff or weights (see or_teno5_lad): the paper's
+# adaptive LAD cutoff (eq. 3.1-3.4), a fixed C_T = 10^-ct_m (TENO5, Sec. 2;
+# Sec. 4 uses 1e-7), TENO5-A (eq. 2.16-2.18) and WENO-Z (tau_5 of eq. 2.12).
+SCHEMES = {"lad": 0, "teno5": 1, "teno5a": 2, "wenoz": 3}
 
 
 @dataclass
 class Params:
-    """Scheme parameters: gamma (eq. 4.7), H, B_l, B_u (eq. 3.1-3.2), eps (eq. 2.8)."""
+    """Scheme parameters: gamma (eq. 4.7), H, B_l, B_u (eq. 3.1-3.2), eps
+    (eq. 2.8), the reconstruction ``scheme`` and TENO5's fixed magnitude."""
     gamma: float = 1.4
     H: float = 10.0
     eps: float = 1e-6
     b_l: int = 4
     b_u: int = 10
+    scheme: str = "lad"
+    ct_m: int = 7
 
     def c(self) -> _Params:
-        return _Params(self.gamma, self.H, self.eps, self.b_l, self.b_u)
+        return _Params(self.gamma, self.H, self.eps, self.b_l, self.b_u, SCHEMES[self.scheme], self.ct_m)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -152,7 +161,7 @@ def _bc3(bc):
 
 DIAG_NAMES = ["beta0", "beta1", "beta2", "tau", "chit0", "chit1", "chit2", "theta", "m", "CT",
               "gamma0", "gamma1", "gamma2", "chi0", "chi1", "chi2", "f0", "f1", "f2",
-              "omega0", "omega1", "omega2", "fhat"]
+              "omega0", "omega1", "omega2", "fhat", "eta", "mA", "gA", "betaA"]
 
 
 def num_threads() -> int:

@@ -16,6 +16,9 @@
  *   - LAD cutoff: chi~_k and theta (eq. 3.2), m (eq. 3.1), Ladder (eq. 3.3-3.4);
  *   - scale separation gamma_k (eq. 2.8), normalisation (eq. 2.13),
  *     cutoff delta_k (eq. 2.14), weights omega_k (eq. 2.15), flux (eq. 2.7);
+ *   - the paper's comparison schemes on the same reconstruction: a fixed
+ *     C_T (TENO5, Sec. 2 and Sec. 4), TENO5-A's adaptive C_T (eq. 2.16-2.18)
+ *     and WENO-Z weights on tau_5 (eq. 2.12);
  *   - the linear upwind flux, eq. 2.3;
  *   - the Euler flux, eq. 4.7 (extended to 2D/3D by the usual momentum rows);
  *   - global Lax-Friedrichs splitting with characteristic projection (Sec. 4,
@@ -53,7 +56,19 @@ typedef struct {
   double eps;   /* small value in eq. 2.8 and eq. 3.2 */
   int b_l;      /* lower magnitude bound B_l (eq. 3.1) */
   int b_u;      /* upper magnitude bound B_u (eq. 3.1) */
+  int scheme;   /* OR_SCHEME_*: which cutoff / weights (see or_teno5_lad) */
+  int ct_m;     /* OR_SCHEME_TENO5: the fixed C_T = 10^-ct_m (Sec. 4: 7) */
 } or_params;
+
+/* The reconstruction's cutoff or weights:
+ *   LAD    the paper's adaptive C_T = Lad(m) (eq. 3.1-3.4);
+ *   TENO5  a fixed C_T = 10^-ct_m (eq. 2.8-2.15; the paper's comparison
+ *          scheme uses 1e-7, Sec. 4);
+ *   TENO5A the adaptive C_T of eq. 2.16-2.18 (TENO5-A) with the parameters
+ *          alpha_1 = 10.5, alpha_2 = 3.5, C_r = 0.25, xi = 1e-3 (Sec. 2);
+ *   WENOZ  the WENO-Z weights built on tau_5 of eq. 2.12:
+ *          omega_k = alpha_k / sum alpha, alpha_k = c_k (1 + tau_5/(beta_k + eps)). */
+enum { OR_SCHEME_LAD = 0, OR_SCHEME_TENO5 = 1, OR_SCHEME_TENO5A = 2, OR_SCHEME_WENOZ = 3 };
 
 /* Diagnostic record of one scalar reconstruction, in the paper's symbols. */
 enum {
@@ -61,6 +76,7 @@ enum {
   OR_D_CHIT0, OR_D_CHIT1, OR_D_CHIT2, OR_D_THETA, OR_D_M, OR_D_CT,
   OR_D_GAMMA0, OR_D_GAMMA1, OR_D_GAMMA2, OR_D_CHI0, OR_D_CHI1, OR_D_CHI2,
   OR_D_F0, OR_D_F1, OR_D_F2, OR_D_OMEGA0, OR_D_OMEGA1, OR_D_OMEGA2, OR_D_FHAT,
+  OR_D_ETA, OR_D_MA, OR_D_GA, OR_D_BETAA, /* TENO5-A: eta_{i+1/2}, m, g(m), beta (eq. 2.16-2.17) */
   OR_D_COUNT
 };
 
@@ -84,6 +100,15 @@ double or_ladder(int m) {
 double or_upwind5(const double v[5]) {
   return 2.0 / 60.0 * v[0] - 13.0 / 60.0 * v[1] + 47.0 / 60.0 * v[2] +
          27.0 / 60.0 * v[3] - 3.0 / 60.0 * v[4];
+}
+
+/*
+ * TENO5-A's sensor eta_i of eq. 2.18 at a point whose neighbouring first
+ * differences are dp = f_{i+1} - f_i and dm = f_i - f_{i-1}; the denominator
+ * is read as (dp)^2 + (dm)^2 + eps (the printed one repeats dp).
+ */
+static double teno5a_eta(double dp, double dm, double eps_a) {
+  return (2.0 * fabs(dp * dm) + eps_a) / (dp * dp + dm * dm + eps_a);
 }
 
 /*
@@ -126,8 +151,31 @@ double or_teno5_lad(const double v[5], const or_params* P, int forced,
     if (chit[k] > chit_max) chit_max = chit[k];
   double theta = 1.0 / (1.0 + chit_max / P->H);
 
-  /* eq. 3.1: magnitude m, and eq. 3.3-3.4: C_T = Lad(m) */
-  int m = P->b_l + (int)floor(theta * (double)(P->b_u - P->b_l));
+  int m;
+  double eta = NAN, mA = NAN, gA = NAN, betaA = NAN;
+  if (P->scheme == OR_SCHEME_TENO5) {
+    /* a fixed cutoff C_T = 10^-ct_m */
+    m = P->ct_m;
+  } else if (P->scheme == OR_SCHEME_TENO5A) {
+    /* eq. 2.16-2.18: eta at the points i-1, i, i+1 of the stencil, their
+     * minimum, m = 1 - min(1, eta / C_r), g(m) = (1 - m)^4 (1 + 4 m),
+     * beta = alpha_1 - alpha_2 (1 - g(m)), C_T = 10^-floor(beta) */
+    const double a1 = 10.5, a2 = 3.5, Cr = 0.25, xi = 1e-3;
+    double eps_a = 0.9 * Cr / (1.0 - 0.9 * Cr) * xi * xi;
+    double eta_m1 = teno5a_eta(v[2] - v[1], v[1] - v[0], eps_a);
+    double eta_0 = teno5a_eta(v[3] - v[2], v[2] - v[1], eps_a);
+    double eta_p1 = teno5a_eta(v[4] - v[3], v[3] - v[2], eps_a);
+    eta = fmin(eta_m1, fmin(eta_0, eta_p1));
+    mA = 1.0 - fmin(1.0, eta / Cr);
+    double t = 1.0 - mA;
+    double t2 = t * t;
+    gA = t2 * t2 * (1.0 + 4.0 * mA);
+    betaA = a1 - a2 * (1.0 - gA);
+    m = (int)floor(betaA);
+  } else {
+    /* eq. 3.1: magnitude m (the Ladder of eq. 3.3-3.4 gives C_T below) */
+    m = P->b_l + (int)floor(theta * (double)(P->b_u - P->b_l));
+  }
   double CT = or_ladder(m);
 
   /* eq. 2.8: gamma_k = (C + tau/(beta_k + eps))^q with C = 1, q = 6 */
@@ -151,6 +199,20 @@ double or_teno5_lad(const double v[5], const or_params* P, int forced,
   for (int k = 0; k < 3; ++k) dsum += delta[k] * c[k];
   double omega[3];
   for (int k = 0; k < 3; ++k) omega[k] = delta[k] * c[k] / dsum;
+
+  if (P->scheme == OR_SCHEME_WENOZ) {
+    /* WENO-Z: no cutoff; alpha_k = c_k (1 + tau_5 / (beta_k + eps)),
+     * omega_k = alpha_k / sum_j alpha_j.  Flag: every delta set, m = 0. */
+    double alpha[3], asum = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      alpha[k] = c[k] * (1.0 + tau / (beta[k] + P->eps));
+      asum += alpha[k];
+    }
+    for (int k = 0; k < 3; ++k) omega[k] = alpha[k] / asum;
+    for (int k = 0; k < 3; ++k) delta[k] = 1;
+    m = 0;
+    CT = 0.0;
+  }
 
   /* eq. 2.7 */
   double fhat = omega[0] * f0 + omega[1] * f1 + omega[2] * f2;
@@ -182,6 +244,10 @@ double or_teno5_lad(const double v[5], const or_params* P, int forced,
     diag[OR_D_OMEGA1] = omega[1];
     diag[OR_D_OMEGA2] = omega[2];
     diag[OR_D_FHAT] = fhat;
+    diag[OR_D_ETA] = eta;
+    diag[OR_D_MA] = mA;
+    diag[OR_D_GA] = gA;
+    diag[OR_D_BETAA] = betaA;
   }
   return fhat;
 }
