@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define TENO_ABI_VERSION 1
+#define TENO_ABI_VERSION 2
 
 typedef enum {
   TENO_OK = 0,
@@ -64,6 +64,22 @@ typedef enum {
                              /* entry points return TENO_ERR_UNSUPPORTED)      */
 } teno_bc;
 
+/* The reconstruction's cutoff (teno_grid.scheme).  The paper's method is
+ * TENO_SCHEME_LAD; the others are the schemes it is compared with (Sec. 4,
+ * Tab. 2), on the same characteristic-wise flux and the same kernels. */
+typedef enum {
+  TENO_SCHEME_LAD = 0,     /* C_T = Lad(m), m = B_l + floor(theta (B_u - B_l))  */
+                           /* (eq. 3.1-3.4)                                    */
+  TENO_SCHEME_TENO5 = 1,   /* fixed C_T = 10^-ct_m (eq. 2.14; Sec. 4: 1e-7)     */
+  TENO_SCHEME_TENO5A = 2,  /* TENO5-A: C_T = 10^-floor(beta) from the sensor    */
+                           /* eta of eq. 2.16-2.18 (alpha_1 10.5, alpha_2 3.5,  */
+                           /* C_r 0.25, xi 1e-3; eq. 2.18's denominator read    */
+                           /* as (df_{i+1/2})^2 + (df_{i-1/2})^2 + eps)         */
+  TENO_SCHEME_WENOZ = 3    /* WENO-Z: omega_k = alpha_k / sum alpha,            */
+                           /* alpha_k = c_k (1 + tau_5 / (beta_k + eps))        */
+                           /* (tau_5 of eq. 2.12); no cutoff                    */
+} teno_scheme;
+
 /* Grid and scheme parameters (problem statement: eq. 2.1-2.2, eq. 4.7,
  * eq. 3.1-3.2).  Unused dimensions must have n = 1, dx = 1. */
 typedef struct {
@@ -75,6 +91,8 @@ typedef struct {
   double H;          /* discontinuity threshold H of eq. 3.2 (paper: 10)     */
   int b_l, b_u;      /* magnitude bounds B_l, B_u of eq. 3.1 (paper: 4, 10)  */
   double eps;        /* epsilon of eq. 2.8 / eq. 3.2 (paper: 1e-6)           */
+  int scheme;        /* teno_scheme (TENO_SCHEME_LAD = 0)                     */
+  int ct_m;          /* TENO_SCHEME_TENO5 only: C_T = 10^-ct_m, 1..15         */
 } teno_grid;
 
 /* Workspace sizes for each operation (teno_workspace_bytes `op`). */
@@ -86,7 +104,7 @@ enum {
 };
 
 /* Fills `g` with the paper's parameters (gamma 1.4, H 10, B_l 4, B_u 10,
- * eps 1e-6; Sec. 2 and Sec. 4) for an ndim grid of n cells of spacing dx with
+ * eps 1e-6, TENO_SCHEME_LAD, ct_m 7; Sec. 2 and Sec. 4) for an ndim grid of n cells of spacing dx with
  * boundary type bc on every axis. */
 void teno_grid_default(teno_grid* g, int ndim, const int64_t* n,
                        const double* dx, int bc);
@@ -205,7 +223,8 @@ size_t teno_adjoint_workspace_bytes(const teno_grid* g, int op);
  * constant, so J is the derivative of L almost everywhere.  The global
  * Lax-Friedrichs speed max_cells |lambda_s| is differentiated through its
  * arg-max cell (the lowest linear index on ties).  Deterministic: no atomics
- * on floating-point data.
+ * on floating-point data.  The TENO schemes (LAD, TENO5, TENO5-A) only:
+ * WENO-Z's weights are not piecewise constant (TENO_ERR_UNSUPPORTED).
  *   U, dUdt_bar : [in] device, nvar * ncell doubles.
  *   U_bar       : [in/out] device, accumulated; must not alias the inputs.
  *   ws          : >= teno_adjoint_workspace_bytes(g, TENO_OP_RHS_ADJOINT).

@@ -35,7 +35,13 @@ class TenoGrid(ctypes.Structure):
         ("b_l", ctypes.c_int),
         ("b_u", ctypes.c_int),
         ("eps", ctypes.c_double),
+        ("scheme", ctypes.c_int),
+        ("ct_m", ctypes.c_int),
     ]
+
+
+# teno_scheme: the paper's LAD cutoff and the schemes it is compared with
+SCHEMES = {"lad": 0, "teno5": 1, "teno5a": 2, "wenoz": 3}
 
 
 class TenoBatch(ctypes.Structure):
@@ -131,7 +137,7 @@ def check(status: int, where: str) -> None:
         raise TenoError(status, where)
 
 
-def make_grid(n, dx, bc, gamma=1.4, H=10.0, b_l=4, b_u=10, eps=1e-6) -> TenoGrid:
+def make_grid(n, dx, bc, gamma=1.4, H=10.0, b_l=4, b_u=10, eps=1e-6, scheme="lad", ct_m=7) -> TenoGrid:
     """teno_grid for an ndim = len(n) grid; bc may be one value or one per axis."""
     ndim = len(n)
     g = TenoGrid()
@@ -142,4 +148,6 @@ def make_grid(n, dx, bc, gamma=1.4, H=10.0, b_l=4, b_u=10, eps=1e-6) -> TenoGrid
         g.dx[k] = float(dx[k]) if k < ndim else 1.0
         g.bc[k] = int(bcs[k]) if k < ndim else 0
     g.gamma, g.H, g.b_l, g.b_u, g.eps = float(gamma), float(H), int(b_l), int(b_u), float(eps)
+    g.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    g.ct_m = int(ct_m)
     return g

@@ -43,12 +43,17 @@ def alloc_workspace(nbytes: int, device) -> torch.Tensor:
 
 @dataclass
 class Scheme:
-    """Scheme parameters of eq. 2.8, 3.1-3.2 and the gas (eq. 4.7)."""
+    """Scheme parameters of eq. 2.8, 3.1-3.2 and the gas (eq. 4.7).
+    ``scheme`` selects the cutoff: "lad" (the paper's, eq. 3.1-3.4), or the
+    comparison schemes "teno5" (fixed C_T = 10^-ct_m), "teno5a" (eq.
+    2.16-2.18) and "wenoz" (WENO-Z weights on tau_5, eq. 2.12)."""
     gamma: float = 1.4
     H: float = 10.0
     b_l: int = 4
     b_u: int = 10
     eps: float = 1e-6
+    scheme: str = "lad"
+    ct_m: int = 7
 
 
 class EulerGrid:
@@ -61,7 +66,7 @@ class EulerGrid:
         self.bc = tuple(bc) if isinstance(bc, (list, tuple)) else (int(bc),) * len(self.n)
         self.scheme = scheme or Scheme()
         s = self.scheme
-        self.c = _lib.make_grid(self.n, self.dx, self.bc, s.gamma, s.H, s.b_l, s.b_u, s.eps)
+        self.c = _lib.make_grid(self.n, self.dx, self.bc, s.gamma, s.H, s.b_l, s.b_u, s.eps, s.scheme, s.ct_m)
         self.lib = _lib.load()
 
     @property

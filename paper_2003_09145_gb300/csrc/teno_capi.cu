@@ -35,6 +35,7 @@ bool grid_ok(const teno_grid* g) {
   if (!(g->H > 0.0) || !std::isfinite(g->H)) return false;
   if (!(g->eps > 0.0) || !std::isfinite(g->eps)) return false;
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
+  if (!teno::scheme_fields_ok(g)) return false;
   // total cell count must stay addressable with 64-bit indices
   const double cells = double(g->n[0]) * double(g->n[1]) * double(g->n[2]);
   if (cells * teno::aux_fields(g->ndim) > 9.0e18 / 8.0) return false;
@@ -96,9 +97,7 @@ Grid make_grid(const teno_grid* g) {
   return G;
 }
 
-Scheme make_scheme(const teno_grid* g) {
-  return teno::make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);
-}
+Scheme make_scheme(const teno_grid* g) { return teno::scheme_of(g); }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -230,6 +229,8 @@ void teno_grid_default(teno_grid* g, int ndim, const int64_t* n, const double* d
   g->b_l = 4;
   g->b_u = 10;
   g->eps = 1e-6;
+  g->scheme = TENO_SCHEME_LAD;
+  g->ct_m = 7;
 }
 
 size_t teno_workspace_bytes(const teno_grid* g, int op) {

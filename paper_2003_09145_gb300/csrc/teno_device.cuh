@@ -76,8 +76,21 @@ constexpr int kMaxLadder = 16;
 // Device status bits recorded in the workspace header.
 enum : int { kStatusNonphysical = 1, kStatusTimeout = 2 };
 
+// Cutoff variants (teno_scheme of the C-ABI): the paper's LAD cutoff
+// (eq. 3.1-3.4) and its comparison schemes -- a fixed C_T (TENO5), TENO5-A's
+// sensor (eq. 2.16-2.18) and WENO-Z weights (tau_5 of eq. 2.12, no cutoff).
+enum : int { kSchemeLad = 0, kSchemeTeno5 = 1, kSchemeTeno5A = 2, kSchemeWenoZ = 3 };
+
+// TENO5-A's parameters (Sec. 2): alpha_1, alpha_2, C_r = 1/4 (so eta / C_r
+// = 4 eta exactly) and eps = 0.9 C_r / (1 - 0.9 C_r) xi^2 with xi = 1e-3,
+// evaluated in that order as in the formula (Scheme::eps_a).
+constexpr double kTeno5AAlpha1 = 10.5, kTeno5AAlpha2 = 3.5, kTeno5ACr = 0.25, kTeno5AXi = 1e-3;
+
 // Scheme constants, passed to kernels by value.
 struct Scheme {
+  int variant;    // kScheme*
+  int m_fixed;    // kSchemeTeno5: C_T = 10^-m_fixed
+  double eps_a;   // kSchemeTeno5A: eps of eq. 2.18
   double gamma;   // ratio of specific heats (eq. 4.7)
   double gm1;     // gamma - 1
   double eps;     // epsilon of eq. 2.8 / 3.2
@@ -209,6 +222,32 @@ __device__ __forceinline__ double recip_pos(double x) {
 }
 
 // ---------------------------------------------------------------------------
+// TENO5-A's magnitude m = floor(beta) (eq. 2.16-2.18) from the first
+// differences e_k = v_{k+1} - v_k of the five stencil values: the sensor
+//   eta_j = (2 |d+ d-| + eps) / ((d+)^2 + (d-)^2 + eps)
+// at the stencil points 1, 2, 3 (i-1, i, i+1; d+- the differences on either
+// side; the printed denominator repeats d+, read as d+ and d-), their
+// minimum eta, m_A = 1 - min(1, eta / C_r), g = (1 - m_A)^4 (1 + 4 m_A),
+// beta = alpha_1 - alpha_2 (1 - g).  Every operation is rounded as written
+// (no contraction), so the magnitude equals a plain evaluation's bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double teno5a_eta(double dp, double dm, double eps_a) {
+  const double num = __dadd_rn(2.0 * fabs(__dmul_rn(dp, dm)), eps_a);
+  const double den = __dadd_rn(__dadd_rn(__dmul_rn(dp, dp), __dmul_rn(dm, dm)), eps_a);
+  return __ddiv_rn(num, den);
+}
+
+__device__ __forceinline__ int teno5a_magnitude(double e0, double e1, double e2, double e3, double eps_a) {
+  const double eta = fmin(teno5a_eta(e1, e0, eps_a), fmin(teno5a_eta(e2, e1, eps_a), teno5a_eta(e3, e2, eps_a)));
+  const double mA = __dsub_rn(1.0, fmin(1.0, __ddiv_rn(eta, kTeno5ACr)));
+  const double t = __dsub_rn(1.0, mA);
+  const double t2 = __dmul_rn(t, t);
+  const double g = __dmul_rn(__dmul_rn(t2, t2), __dadd_rn(1.0, 4.0 * mA));
+  const double beta = __dsub_rn(kTeno5AAlpha1, __dmul_rn(kTeno5AAlpha2, __dsub_rn(1.0, g)));
+  return static_cast<int>(floor(beta));
+}
+
+// ---------------------------------------------------------------------------
 // TENO5-LAD scalar reconstruction of the interface value from five values
 // v0..v4 = (f_{i-2}, ..., f_{i+2}).  Returns acc + f^ (eq. 2.7); `flag`
 // receives delta bits 0..2 and m in bits 3..6.
@@ -260,20 +299,50 @@ __device__ __forceinline__ double teno5_lad(double v0, double v1, double v2,
   const unsigned long long btau = dbits(tau);
   unsigned sel = 7u;
   int m = S.b_u;
+  if (S.variant == kSchemeWenoZ) {
+    // WENO-Z: omega_k = a_k / sum_j a_j with a_k = c_k (1 + tau / D_k),
+    // D_k = beta_k + eps (the common factor 4 cancels); with N_k = D_k + tau
+    // and A_k = c_k N_k prod_{j != k} D_j = a_k D_0 D_1 D_2, omega_k =
+    // A_k / sum A (one division; three where the products leave the range)
+    const double d0 = beta0 + S.eps4, d1 = beta1 + S.eps4, d2 = beta2 + S.eps4;
+    double A0 = 0.1 * (d0 + tau) * (d1 * d2), A1 = 0.6 * (d1 + tau) * (d0 * d2), A2 = 0.3 * (d2 + tau) * (d0 * d1);
+    double As = A0 + A1 + A2;
+    if (!(As > 0.0 && As <= 1.7976931348623157e308)) {
+      A0 = 0.1 * (1.0 + tau / d0);
+      A1 = 0.6 * (1.0 + tau / d1);
+      A2 = 0.3 * (1.0 + tau / d2);
+      As = A0 + A1 + A2;
+    }
+    const double r = 1.0 / As;
+    const double o0 = A0 * r, o1 = A1 * r, o2 = A2 * r;
+    flag = 7u;
+    // f^ = v2 + sum_k w_k e_k (see c_coef)
+    const double w0 = o0 * (-1.0 / 3.0), w1 = fma(o0, 5.0 / 6.0, o1 * (1.0 / 6.0));
+    const double w2 = fma(o1, 1.0 / 3.0, o2 * (2.0 / 3.0)), w3 = o2 * (-1.0 / 6.0);
+    return fma(w0, e0, fma(w1, e1, fma(w2, e2, fma(w3, e3, v2 + acc))));
+  }
   if (!WITH_M && S.keep_idx >= 0 && btau <= dbits(S.thr[S.keep_idx] * dmin)) {
-    // m lies in the keep-all range (a suffix of B_l..B_u): every stencil is kept
+    // tau below the keep-all threshold: every stencil is kept (for LAD, m
+    // lies in the keep-all range, a suffix of B_l..B_u; for TENO5 and
+    // TENO5-A, chi_k >= 1/(3 (1 + max chi~)^6) exceeds the largest C_T)
     flag = 7u;
   } else {
-    int cnt = 0;
+    if (S.variant == kSchemeLad) {
+      int cnt = 0;
 #pragma unroll
-    for (int step = 8; step >= 1; step >>= 1) {
-      if (step <= S.top) {
-        const int idx = cnt + step - 1;
-        if (btau <= dbits(S.thr[idx] * dmin)) cnt += step;
+      for (int step = 8; step >= 1; step >>= 1) {
+        if (step <= S.top) {
+          const int idx = cnt + step - 1;
+          if (btau <= dbits(S.thr[idx] * dmin)) cnt += step;
+        }
       }
+      cnt = min(cnt, S.nthr);
+      m = S.b_l + cnt;
+    } else if (S.variant == kSchemeTeno5) {
+      m = S.m_fixed;
+    } else {
+      m = teno5a_magnitude(e0, e1, e2, e3, S.eps_a);
     }
-    cnt = min(cnt, S.nthr);
-    m = S.b_l + cnt;
     if (!((S.keep_all >> m) & 1u)) {
       // eq. 3.4, eq. 2.8, eq. 2.13-2.14 (division-free form, see above)
       const double ct = c_lad[m];

@@ -421,45 +421,66 @@ __global__ void dt_kernel(const unsigned long long* __restrict__ alpha_bits,
 // ---------------------------------------------------------------------------
 // Scheme constants (host side)
 // ---------------------------------------------------------------------------
-Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u) {
+Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u, int variant, int ct_m) {
   static const double kPow10Neg[16] = {1e-0, 1e-1, 1e-2,  1e-3,  1e-4,  1e-5,  1e-6,  1e-7,
                                        1e-8, 1e-9, 1e-10, 1e-11, 1e-12, 1e-13, 1e-14, 1e-15};
   Scheme S;
   std::memset(&S, 0, sizeof(S));
+  S.variant = variant;
+  S.m_fixed = ct_m;
+  S.eps_a = kTeno5ACr * 0.9 / (1.0 - 0.9 * kTeno5ACr) * kTeno5AXi * kTeno5AXi;
   S.gamma = gamma;
   S.gm1 = gamma - 1.0;
   S.eps = eps;
   S.eps4 = 4.0 * eps;
   S.b_l = b_l;
   S.b_u = b_u;
-  const int K = b_u - b_l;
-  S.nthr = K;
-  S.top = 1;
-  while (S.top * 2 <= K) S.top *= 2;
-  // floor(theta K) >= j  <=>  max chi~ <= H (K/j - 1)   (eq. 3.1-3.2)
-  for (int j = 1; j < K; ++j) S.thr[j - 1] = H * (double(K) / double(j) - 1.0);
-  // theta == 1 in binary64  <=>  max chi~ / H <= 2^-53
-  S.thr[K - 1] = H * 0x1p-53;
-  // All stencils are kept whenever 3 (1 + max chi~)^6 C_T < 1 (then
-  // chi_k >= gamma_min / (3 gamma_max) >= 1 / (3 (1 + max chi~)^6) > C_T); at
-  // a given m, max chi~ <= thr[m - B_l - 1].  A relative margin of 1e-9 covers
-  // the rounding of the threshold products.
   S.keep_all = 0;
-  for (int c = 1; c <= K; ++c) {
-    const int m = b_l + c;
-    const double x = 1.0 + S.thr[c - 1];
-    const double x6 = x * x * x * x * x * x;
-    if (3.0 * x6 * kPow10Neg[m] <= 1.0 - 1e-9) S.keep_all |= 1u << m;
-  }
-  // the keep-all set is a suffix of B_l..B_u (the bound loosens as m grows)
   S.keep_idx = -1;
-  for (int c = 1; c <= K; ++c) {
-    const unsigned suffix = ((1u << (b_u + 1)) - 1u) & ~((1u << (b_l + c)) - 1u);
-    if (S.keep_all == suffix) {
-      S.keep_idx = c - 1;
-      break;
+  if (variant == kSchemeLad) {
+    const int K = b_u - b_l;
+    S.nthr = K;
+    S.top = 1;
+    while (S.top * 2 <= K) S.top *= 2;
+    // floor(theta K) >= j  <=>  max chi~ <= H (K/j - 1)   (eq. 3.1-3.2)
+    for (int j = 1; j < K; ++j) S.thr[j - 1] = H * (double(K) / double(j) - 1.0);
+    // theta == 1 in binary64  <=>  max chi~ / H <= 2^-53
+    S.thr[K - 1] = H * 0x1p-53;
+    // All stencils are kept whenever 3 (1 + max chi~)^6 C_T < 1 (then
+    // chi_k >= gamma_min / (3 gamma_max) >= 1 / (3 (1 + max chi~)^6) > C_T); at
+    // a given m, max chi~ <= thr[m - B_l - 1].  A relative margin of 1e-9 covers
+    // the rounding of the threshold products.
+    for (int c = 1; c <= K; ++c) {
+      const int m = b_l + c;
+      const double x = 1.0 + S.thr[c - 1];
+      const double x6 = x * x * x * x * x * x;
+      if (3.0 * x6 * kPow10Neg[m] <= 1.0 - 1e-9) S.keep_all |= 1u << m;
+    }
+    // the keep-all set is a suffix of B_l..B_u (the bound loosens as m grows)
+    for (int c = 1; c <= K; ++c) {
+      const unsigned suffix = ((1u << (b_u + 1)) - 1u) & ~((1u << (b_l + c)) - 1u);
+      if (S.keep_all == suffix) {
+        S.keep_idx = c - 1;
+        break;
+      }
+    }
+  } else if (variant == kSchemeTeno5 || variant == kSchemeTeno5A) {
+    // The same bound with the largest C_T the scheme can take (TENO5: the
+    // fixed one; TENO5-A: 1e-7): every stencil is kept when max chi~ <= thr
+    // with 3 (1 + thr)^6 C_T <= 1 - 1e-9.
+    const double ct = kPow10Neg[variant == kSchemeTeno5 ? ct_m : 7];
+    double thr = std::pow(1.0 / (3.0 * ct), 1.0 / 6.0) - 1.0;
+    for (int it = 0; it < 200 && thr > 0.0; ++it) {
+      const double x = 1.0 + thr;
+      if (3.0 * (x * x * x * x * x * x) * ct <= 1.0 - 1e-9) break;
+      thr *= 1.0 - 1e-7;
+    }
+    if (thr > 0.0) {
+      S.thr[0] = thr;
+      S.keep_idx = 0;
     }
   }
+  // (WENO-Z has no cutoff and no keep-all shortcut: keep_idx stays -1)
   // binary32 constants of the pre-test, rounded towards zero (conservative)
   auto down = [](double x) {
     float f = static_cast<float>(x);
@@ -605,7 +626,7 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
     G.rdx[k] = G.dx[0] / G.dx[k];
   }
   G.ncell = g->n[0] * g->n[1] * g->n[2];
-  const Scheme S = make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);
+  const Scheme S = scheme_of(g);
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)

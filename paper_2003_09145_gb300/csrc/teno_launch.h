@@ -10,8 +10,22 @@
 
 namespace teno {
 
-// Scheme constants for the given gas and LAD parameters (eq. 3.1-3.2, 2.8).
-Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u);
+// Scheme constants for the given gas, LAD parameters (eq. 3.1-3.2, 2.8) and
+// cutoff variant (teno_scheme; ct_m: TENO5's fixed magnitude).
+Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u, int variant = TENO_SCHEME_LAD,
+                   int ct_m = 7);
+
+// The grid's scheme fields are valid: a known teno_scheme, and for
+// TENO_SCHEME_TENO5 a magnitude 1..15.
+inline bool scheme_fields_ok(const teno_grid* g) {
+  if (g->scheme < TENO_SCHEME_LAD || g->scheme > TENO_SCHEME_WENOZ) return false;
+  if (g->scheme == TENO_SCHEME_TENO5 && (g->ct_m < 1 || g->ct_m > 15)) return false;
+  return true;
+}
+
+inline Scheme scheme_of(const teno_grid* g) {
+  return make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u, g->scheme, g->ct_m);
+}
 
 // Primitives (aux) and LF speeds of every cell; with `fh` (nullable) also
 // the half physical fluxes F_d/2 without their mass component,

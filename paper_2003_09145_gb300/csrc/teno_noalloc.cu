@@ -70,6 +70,7 @@ bool grid_valid(const teno_grid* g) {
   if (!(g->gamma > 1.0) || !(g->H > 0.0) || !(g->eps > 0.0)) return false;
   if (!std::isfinite(g->gamma) || !std::isfinite(g->H) || !std::isfinite(g->eps)) return false;
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
+  if (!teno::scheme_fields_ok(g)) return false;
   return true;
 }
 
@@ -128,7 +129,7 @@ extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, dou
     G.rdx[k] = G.dx[0] / G.dx[k];
   }
   G.ncell = int64_t(ncell);
-  const teno::Scheme S = teno::make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);
+  const teno::Scheme S = teno::scheme_of(g);
 
   int nsm = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

@@ -85,6 +85,7 @@ bool scalar_grid_ok(const teno_grid* g) {
   if (!(g->dx[0] > 0.0) || !std::isfinite(g->dx[0])) return false;
   if (!(g->H > 0.0) || !std::isfinite(g->H) || !(g->eps > 0.0) || !std::isfinite(g->eps)) return false;
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
+  if (!teno::scheme_fields_ok(g)) return false;
   return true;
 }
 
@@ -128,7 +129,7 @@ teno_status scalar_stage(const teno_grid* g, double a, int mode_recon, const dou
                          double dt, const double* un, const double* uk, double* out, cudaStream_t st) {
   const int64_t n = g->n[0];
   const int nsm = sm_count();
-  const Scheme S = teno::make_scheme(1.4, g->H, g->eps, g->b_l, g->b_u);
+  const Scheme S = teno::make_scheme(1.4, g->H, g->eps, g->b_l, g->b_u, g->scheme, g->ct_m);
   scalar_flux_kernel<<<blocks_for(n + 1, 128, nsm * 16), 128, 0, st>>>(u, n, a, mode_recon, S, F);
   scalar_diff_kernel<<<blocks_for(n, 256, nsm * 8), 256, 0, st>>>(F, n, 1.0 / g->dx[0], mode, dt, un, uk, out);
   return cudaGetLastError() == cudaSuccess ? TENO_OK : TENO_ERR_CUDA;

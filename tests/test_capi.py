@@ -51,6 +51,9 @@ def test_grid_validation(lib):
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.n[2] = 3; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.gamma = 1.0; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.eps = -1.0; bad.append(g)
+    g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.scheme = 4; bad.append(g)
+    g = _lib.make_grid((32, 16), (0.1, 0.1), 1, scheme="teno5", ct_m=0); bad.append(g)
+    g = _lib.make_grid((32, 16), (0.1, 0.1), 1, scheme="teno5", ct_m=16); bad.append(g)
     for g in bad:
         assert lib.teno_workspace_bytes(ctypes.byref(g), _lib.OP_RHS) == 0
         st = lib.teno_rhs(ctypes.byref(g), None, None, None, None, 0, None)
@@ -76,7 +79,7 @@ def test_status_strings(lib):
     assert lib.teno_status_string(0) == b"TENO_OK"
     assert lib.teno_status_string(4) == b"TENO_ERR_NONPHYSICAL"
     assert lib.teno_status_string(99) == b"TENO_UNKNOWN_STATUS"
-    assert lib.teno_abi_version() == 1
+    assert lib.teno_abi_version() == 2
 
 
 def test_scalar_mode_validation(lib):
