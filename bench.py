@@ -48,8 +48,22 @@ FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
 #   sum 5, back-projection 21 (= 341), plus per scalar reconstruction 9 when
 #   its own FP32 pre-test keeps every stencil, else 38 for the binary64
 #   indicators, m and weights plus 21 for the cutoff test.
-ALG_CLOSED_3D = 187
-ALG_FIXED_3D = 341
+def alg_counts(ndim: int):
+    """(closed form, characteristic path) algorithmic FP64 flops per interface
+    for an ndim grid, term by term as listed above (D = ndim, nvar = D + 2):
+    closed = Roe (2 + 2D + (2D - 1) + 2 + 3 + 1 + 1 + 5) + 6 points x 4 nvar
+             + A +- B (2D + 6) + corrections 6 + output (4D + 12);
+    characteristic = Roe (the same + b1 and u_d/2: 2) + 6 x projection (4D + 8)
+             + 6 x split (22 + 3 (D - 1)) + sum nvar + back-projection
+             (13 + 4 (D - 1)).  3D: 187 and 341; 2D: 153 and 290."""
+    D, nv = ndim, ndim + 2
+    roe = 2 + 2 * D + (2 * D - 1) + 2 + 3 + 1 + 1 + 5
+    closed = roe + 6 * 4 * nv + (2 * D + 6) + 6 + (4 * D + 12)
+    char = roe + 2 + 6 * (4 * D + 8) + 6 * (22 + 3 * (D - 1)) + nv + (13 + 4 * (D - 1))
+    return closed, char
+
+
+ALG_CLOSED_3D, ALG_FIXED_3D = alg_counts(3)
 ALG_PER_RECON_KEEP = 9
 ALG_PER_RECON = 38
 ALG_CUTOFF = 21
@@ -238,6 +252,116 @@ def _keep_all_mask(scheme) -> int:
     return mask
 
 
+def flux_classes(api, grid, U):
+    """Per interface of U (from the flag path's selections): the number of its
+    2 nvar reconstructions whose m lies outside the keep-all magnitudes (those
+    evaluate the cutoff; an interface with none takes the closed form).
+    Returns (algorithmic flops per interface, fraction of reconstructions that
+    evaluate the cutoff, fraction of interfaces off the closed form)."""
+    import torch
+    _, fl = api.rhs(grid, U, want_flags=True)
+    keep_all = _keep_all_mask(grid.scheme)
+    nvar, ndim = grid.nvar, grid.ndim
+    closed, char = alg_counts(ndim)
+    alg_sum, nk_sum, off_sum, tot, off = 0.0, 0.0, 0.0, 0, 0
+    for d in range(ndim):
+        nifc_d = 1
+        for k in range(ndim):
+            nifc_d *= grid.n[k] + (1 if k == d else 0)
+        blk = fl[off:off + nvar * 2 * nifc_d].view(nvar * 2, nifc_d)
+        off += nvar * 2 * nifc_d
+        nk = (((keep_all >> (blk >> 3).to(torch.int64)) & 1) == 0).sum(dim=0).double()
+        per = torch.where(nk == 0, torch.full_like(nk, float(closed)),
+                          char + 2 * nvar * ALG_PER_RECON_KEEP
+                          + nk * (ALG_PER_RECON - ALG_PER_RECON_KEEP + ALG_CUTOFF))
+        alg_sum += float(per.sum())
+        nk_sum += float(nk.sum())
+        off_sum += float((nk > 0).sum())
+        tot += nifc_d
+    del fl
+    return alg_sum / tot, nk_sum / (2 * nvar * tot), off_sum / tot
+
+
+def timed_steps(api, lib, solver, U, steps):
+    """Event-timed `steps` RK3 steps of U; returns (ms per step, per-kind
+    kernel ms and launch counts from the library's launch timer)."""
+    import torch
+    from paper_2003_09145_gb300 import _lib
+    _lib.check(lib.teno_timer_begin(), "teno_timer_begin")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        solver.step(U)
+    e1.record()
+    torch.cuda.synchronize()
+    kms = (ctypes.c_double * 4)()
+    kcount = (ctypes.c_int64 * 4)()
+    _lib.check(lib.teno_timer_end(kms, kcount), "teno_timer_end")
+    return e0.elapsed_time(e1) / steps, dict(zip(_lib.KERNEL_KINDS, zip(list(kms), list(kcount))))
+
+
+def bench_riemann2d(api, lib, device, steps: int, warm_steps: int, peak: float) -> dict:
+    """The adaptive path at scale: the four-quadrant Riemann problem at 2048^2
+    (split at (0.8, 0.8)), advanced `warm_steps` untimed steps so that its
+    shocks, contacts and their interactions spread over the grid, then
+    `steps` timed steps.  The roofline weights the closed-form and the
+    characteristic-path counts by the classes of the timed start state."""
+    import torch
+    from paper_2003_09145_gb300 import inputs
+    P = inputs.riemann_2d(n=2048)
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    solver = api.Solver(grid, device=device, cfl=0.5)
+    U = torch.from_numpy(P.U0).to(device)
+    solver.run(U, float("inf"), max_steps=warm_steps)
+    torch.cuda.synchronize()
+    assert solver.status() == 0
+    t_start = float(solver.t.item())
+    alg, cut, off = flux_classes(api, grid, U)
+    ms, kinds = timed_steps(api, lib, solver, U, steps)
+    flux_ms = kinds["flux"][0]
+    nifc = (P.n[0] + 1) * P.n[1] + P.n[0] * (P.n[1] + 1)
+    # one flux evaluation = both passes of one direction in one RK stage
+    flux_s_per_step = flux_ms / steps * 1e-3
+    achieved = alg * nifc * 3 / flux_s_per_step / 1e12
+    return {"value": grid.ncell / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "workload": "2D four-quadrant Riemann problem (split (0.8, 0.8)), 2048^2, TENO5-LAD, SSP-RK3 "
+                        f"CFL 0.5, timed from t = {t_start:.4f} (after {warm_steps} steps)",
+            "interfaces_off_closed_form": off, "cutoff_evaluated_fraction": cut,
+            "alg_flops_per_interface": alg,
+            "kernel_ms_per_step": {k: v[0] / steps for k, v in kinds.items()},
+            "flux_roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                              "frac": achieved / peak}}
+
+
+def bench_schemes(api, lib, device, steps: int, workloads) -> dict:
+    """The paper's cost comparison (Tab. 2) on this GPU: ms per RK3 step of
+    the same state under TENO5-LAD and its comparison schemes (TENO5 with
+    C_T = 1e-7, TENO5-A, WENO-Z), and the ratio to TENO5-LAD."""
+    import torch
+    out = {}
+    for name, P, U0 in workloads:
+        row = {}
+        for sch in ("lad", "teno5", "teno5a", "wenoz"):
+            grid = api.EulerGrid(P.n, P.dx, P.bc, api.Scheme(scheme=sch))
+            solver = api.Solver(grid, device=device, cfl=0.5)
+            U = U0.clone()
+            for _ in range(2):
+                solver.step(U)
+            torch.cuda.synchronize()
+            ms, _ = timed_steps(api, lib, solver, U, steps)
+            assert solver.status() == 0
+            row[sch] = {"ms_per_step": ms}
+            del solver, U
+            torch.cuda.empty_cache()
+        for sch in row:
+            row[sch]["vs_lad"] = row[sch]["ms_per_step"] / row["lad"]["ms_per_step"]
+        out[name] = row
+    out["paper_context"] = ("Tab. 2 (2D Euler, the paper's CPU workstation, seconds per step): TENO5-LAD about "
+                            "1.05x TENO5, TENO5-A about 1.3x TENO5, WENO-Z about 0.9x TENO5")
+    return out
+
+
 def fp64_probe(api, device) -> float:
     """Measured FP64 FMA throughput (flop/s) of this GPU."""
     import torch
@@ -329,7 +453,10 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_CELLS_1D, help="cells per axis (default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint / 2D / scheme forms")
+    ap.add_argument("--form", choices=["riemann2d", "adjoint"], default=None,
+                    help="run only this form and print its record (profiling aid)")
+    ap.add_argument("--warm-steps", type=int, default=400, help="untimed steps before the riemann2d form")
     args = ap.parse_args()
 
     dist, rank, world = _dist()
@@ -348,6 +475,19 @@ def main() -> None:
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     lib = _lib.load()
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+
+    if args.form == "riemann2d":
+        print(json.dumps(bench_riemann2d(api, lib, device, args.steps, args.warm_steps, peak)), flush=True)
+        return
+    if args.form == "adjoint":
+        P = inputs.solenoidal_turbulence(n=args.n)
+        grid = api.EulerGrid(P.n, P.dx, P.bc)
+        print(json.dumps(bench_adjoint(api, device, grid, torch.from_numpy(P.U0).to(device), args.steps)),
+              flush=True)
+        return
 
     n = args.n
     P = inputs.solenoidal_turbulence(n=n)
@@ -365,23 +505,7 @@ def main() -> None:
     # algorithmic FP64 flops per interface on the timed start state: the flags
     # tell, per interface, how many of its ten reconstructions fall outside the
     # magnitudes m at which every stencil is provably kept
-    _, fl = api.rhs(grid, U, want_flags=True)
-    keep_all = _keep_all_mask(grid.scheme)
-    nifc_d = (n + 1) * n * n
-    nvar = grid.nvar
-    alg_sum, nk_sum, tot = 0.0, 0.0, 0
-    for d in range(3):
-        blk = fl[d * nvar * 2 * nifc_d:(d + 1) * nvar * 2 * nifc_d].view(nvar * 2, nifc_d)
-        nk = (((keep_all >> (blk >> 3).to(torch.int64)) & 1) == 0).sum(dim=0).double()
-        per = torch.where(nk == 0, torch.full_like(nk, float(ALG_CLOSED_3D)),
-                          ALG_FIXED_3D + 10 * ALG_PER_RECON_KEEP
-                          + nk * (ALG_PER_RECON - ALG_PER_RECON_KEEP + ALG_CUTOFF))
-        alg_sum += float(per.sum())
-        nk_sum += float(nk.sum())
-        tot += nifc_d
-    alg_per_ifc = alg_sum / tot
-    cut_frac = nk_sum / (10 * tot)
-    del fl
+    alg_per_ifc, cut_frac, _ = flux_classes(api, grid, U)
 
     # ---- device-resident timed region --------------------------------------
     clocks = ClockSampler(local)
@@ -418,9 +542,6 @@ def main() -> None:
     nifc = (n + 1) * n * n
     flux_avg_s = flux_ms / flux_evals * 1e-3
     achieved = alg_per_ifc * nifc / flux_avg_s / 1e12
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
     probe = fp64_probe(api, device) / 1e12
     traffic = _traffic_per_launch()
     total_kernel_ms = sum(kms)
@@ -463,6 +584,15 @@ def main() -> None:
     if not args.no_forms:
         forms["batched"] = bench_batched(api, device, max(args.steps, 4))
         forms["adjoint"] = bench_adjoint(api, device, grid, U0, 2)
+        forms["riemann2d"] = bench_riemann2d(api, lib, device, max(args.steps, 5), args.warm_steps, peak)
+        quad = inputs.riemann_2d(n=2048)
+        qgrid = api.EulerGrid(quad.n, quad.dx, quad.bc)
+        qsolver = api.Solver(qgrid, device=device, cfl=0.5)
+        Uq = torch.from_numpy(quad.U0).to(device)
+        qsolver.run(Uq, float("inf"), max_steps=args.warm_steps)
+        del qsolver
+        forms["schemes"] = bench_schemes(api, lib, device, 3,
+                                         [("riemann2d_2048", quad, Uq), ("turbulence_256", P, U0)])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
