@@ -227,82 +227,156 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
   block_alpha_sum(asum, apart);
 }
 
-// The pending interfaces: each warp scans its chunks of 32 in order, queues
-// the pending ones in shared memory and processes them 32 at a time (the
-// selections by the forward pass's own binary64 decisions, then the general
-// VJP, or the closed form where every stencil is kept after all); the six
-// cells' contributions go to contrib[6 nvar][nifc].  The order of the
-// d/dalpha sums is fixed by the grid, so results are deterministic.
+// The pending interfaces (those the kept kernel's certified test leaves
+// undecided) are gathered into one list ordered by interface index, so that
+// the general VJP runs on full warps: on the turbulence box they are a few
+// per ten thousand, and a warp with one active lane pays the FP64 pipe's full
+// cost per instruction.  Three small passes build the list:
+//   adj_count_kernel   : block b counts the pending interfaces of its fixed,
+//                        contiguous range of 32-interface chunks;
+//   adj_scan_kernel    : one block turns the nblk counts into offsets and the
+//                        total;
+//   adj_scatter_kernel : block b writes its pending interfaces, in index
+//                        order, from its offset on.
+// The list order depends only on the data, so the general kernel's d/dalpha
+// sums (per thread in list order, then per block) are deterministic.
+constexpr int kListThreads = 256;
+
+__device__ __forceinline__ void chunk_range(int64_t nchunk, int64_t& c0, int64_t& c1) {
+  const int64_t per = (nchunk + gridDim.x - 1) / gridDim.x;
+  c0 = (int64_t)blockIdx.x * per;
+  c1 = c0 + per < nchunk ? c0 + per : nchunk;
+}
+
+__global__ void __launch_bounds__(kListThreads) adj_count_kernel(const unsigned char* __restrict__ pending,
+                                                                  int64_t nifc, int* __restrict__ bcount) {
+  __shared__ int wsum[kListThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t c0, c1;
+  chunk_range((nifc + 31) / 32, c0, c1);
+  int cnt = 0;
+  for (int64_t c = c0 + wid; c < c1; c += kListThreads / 32) {
+    const int64_t q = c * 32 + lane;
+    cnt += __popc(__ballot_sync(0xffffffffu, q < nifc && pending[q] != 0));
+  }
+  if (lane == 0) wsum[wid] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kListThreads / 32; ++w) t += wsum[w];
+    bcount[blockIdx.x] = t;
+  }
+}
+
+// exclusive offsets boff[b] = sum_{b' < b} bcount[b'] and the total, one
+// block of kListThreads (nblk <= 8 kListThreads: eight entries per thread)
+__global__ void __launch_bounds__(kListThreads) adj_scan_kernel(const int* __restrict__ bcount, int nblk,
+                                                                 int* __restrict__ boff, int* __restrict__ total) {
+  __shared__ int wsum[kListThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int v[8], s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int b = threadIdx.x * 8 + k;
+    v[k] = b < nblk ? bcount[b] : 0;
+    s += v[k];
+  }
+  int inc = s;   // inclusive scan of the per-thread sums within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  int base = 0;
+  for (int w = 0; w < wid; ++w) base += wsum[w];
+  int run = base + inc - s;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int b = threadIdx.x * 8 + k;
+    if (b < nblk) boff[b] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kListThreads - 1) *total = run;
+}
+
+__global__ void __launch_bounds__(kListThreads) adj_scatter_kernel(const unsigned char* __restrict__ pending,
+                                                                    int64_t nifc, const int* __restrict__ boff,
+                                                                    uint32_t* __restrict__ list) {
+  __shared__ int wcnt[kListThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t c0, c1;
+  chunk_range((nifc + 31) / 32, c0, c1);
+  int run = boff[blockIdx.x];
+  for (int64_t cb = c0; cb < c1; cb += kListThreads / 32) {
+    const int64_t c = cb + wid;
+    const int64_t q = c * 32 + lane;
+    const bool p = c < c1 && q < nifc && pending[q] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, p);
+    if (lane == 0) wcnt[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int w = 0; w < kListThreads / 32; ++w) {
+      before += w < wid ? wcnt[w] : 0;
+      all += wcnt[w];
+    }
+    if (p) list[run + before + __popc(m & ((1u << lane) - 1u))] = static_cast<uint32_t>(q);
+    run += all;
+    __syncthreads();
+  }
+}
+
+// The listed interfaces, one thread each: the selections by the forward
+// pass's own binary64 decisions, then the general VJP (or the closed form
+// where every stencil is kept after all); the six cells' contributions go to
+// contrib[6 nvar][nifc].
 template <int NDIM, int DIR>
 __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
     const double* __restrict__ U, const double* __restrict__ aux,
     const unsigned long long* __restrict__ alpha_bits, const double* __restrict__ Rbar, double scale,
-    double* __restrict__ contrib, const unsigned char* __restrict__ pending, double* __restrict__ apart,
-    int* __restrict__ status, Grid G, Scheme S) {
+    double* __restrict__ contrib, const uint32_t* __restrict__ list, const int* __restrict__ count,
+    double* __restrict__ apart, int* __restrict__ status, Grid G, Scheme S) {
   constexpr int NVAR = NDIM + 2;
-  constexpr int kWarps = kAdjThreads / 32;
-  __shared__ int64_t queue[kWarps][64];
   const IfcGeom<NDIM, DIR> I(G);
   double fa[NVAR], ha[NVAR], nfa[NVAR];
   field_speeds<NDIM, DIR>(alpha_bits, fa, ha, nfa);
   const double fscale = scale * G.inv_dx[DIR];
   double asum[3] = {0.0, 0.0, 0.0};
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  int64_t chunk = (int64_t)blockIdx.x * kWarps + wid;   // chunks of 32 interfaces
-  const int64_t nchunk = (I.nifc + 31) / 32;
-  int qn = 0;                                           // queued entries (warp-uniform)
-  for (;;) {
-    while (qn < 32 && chunk < nchunk) {
-      const int64_t q = chunk * 32 + lane;
-      const bool p = q < I.nifc && pending[q] != 0;
-      const unsigned m = __ballot_sync(0xffffffffu, p);
-      if (p) queue[wid][qn + __popc(m & ((1u << lane) - 1u))] = q;
-      qn += __popc(m);
-      chunk += nwarps;
+  const int64_t n = *count;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = list[i];
+    int64_t id, base, cells[6];
+    I.locate(q, G, id, base, cells);
+    double fout[NVAR];
+    unsigned fl[NVAR][2];
+    teno::interface_flux<NDIM, DIR, false, teno::kFluxSelect>(U, aux, I.ncell, cells, 0u, ha, nfa, S, fout, fl,
+                                                              status);
+    unsigned sel[NVAR][2];
+    bool all_kept = true;
+#pragma unroll
+    for (int f = 0; f < NVAR; ++f) {
+      sel[f][0] = fl[f][0] & 7u;
+      sel[f][1] = fl[f][1] & 7u;
+      all_kept = all_kept && sel[f][0] == 7u && sel[f][1] == 7u;
     }
-    __syncwarp();
-    if (qn == 0) break;
-    if (lane < qn) {
-      const int64_t q = queue[wid][lane];
-      int64_t id, base, cells[6];
-      I.locate(q, G, id, base, cells);
-      double fout[NVAR];
-      unsigned fl[NVAR][2];
-      teno::interface_flux<NDIM, DIR, false, teno::kFluxSelect>(U, aux, I.ncell, cells, 0u, ha, nfa, S, fout, fl,
-                                                                status);
-      unsigned sel[NVAR][2];
-      bool all_kept = true;
+    double Up[6][NVAR];
 #pragma unroll
-      for (int f = 0; f < NVAR; ++f) {
-        sel[f][0] = fl[f][0] & 7u;
-        sel[f][1] = fl[f][1] & 7u;
-        all_kept = all_kept && sel[f][0] == 7u && sel[f][1] == 7u;
-      }
-      double Up[6][NVAR];
+    for (int j = 0; j < 6; ++j)
 #pragma unroll
-      for (int j = 0; j < 6; ++j)
+      for (int v = 0; v < NVAR; ++v) Up[j][v] = U[v * I.ncell + cells[j]];
+    double Fb[NVAR];
+    interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
+    double Ub[6][NVAR], ab[NVAR];
+    if (all_kept)
+      teno_adj::interface_vjp_kept<NDIM, DIR>(Up, fa, S.gamma, Fb, Ub, ab);
+    else
+      teno_adj::interface_vjp<NDIM, DIR>(Up, fa, sel, S.gamma, Fb, Ub, ab);
 #pragma unroll
-        for (int v = 0; v < NVAR; ++v) Up[j][v] = U[v * I.ncell + cells[j]];
-      double Fb[NVAR];
-      interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
-      double Ub[6][NVAR], ab[NVAR];
-      if (all_kept)
-        teno_adj::interface_vjp_kept<NDIM, DIR>(Up, fa, S.gamma, Fb, Ub, ab);
-      else
-        teno_adj::interface_vjp<NDIM, DIR>(Up, fa, sel, S.gamma, Fb, Ub, ab);
+    for (int j = 0; j < 6; ++j)
 #pragma unroll
-      for (int j = 0; j < 6; ++j)
-#pragma unroll
-        for (int v = 0; v < NVAR; ++v) contrib[(int64_t)(j * NVAR + v) * I.nifc + q] = Ub[j][v];
-      add_alpha<NVAR>(ab, asum);
-    }
-    __syncwarp();
-    const int rest = qn > 32 ? qn - 32 : 0;
-    const int64_t moved = (lane < rest) ? queue[wid][32 + lane] : 0;
-    __syncwarp();
-    if (lane < rest) queue[wid][lane] = moved;
-    qn = rest;
+      for (int v = 0; v < NVAR; ++v) contrib[(int64_t)(j * NVAR + v) * I.nifc + q] = Ub[j][v];
+    add_alpha<NVAR>(ab, asum);
   }
   block_alpha_sum(asum, apart);
 }
@@ -535,6 +609,13 @@ bool grid_valid(const teno_grid* g) {
   }
   if (!(g->gamma > 1.0) || !(g->H > 0.0) || !(g->eps > 0.0)) return false;
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
+  if (!teno::scheme_fields_ok(g)) return false;
+  // the pending list holds 32-bit interface indices and int counts
+  for (int d = 0; d < g->ndim; ++d) {
+    double m = 1.0;
+    for (int k = 0; k < 3; ++k) m *= double(g->n[k] + (k == d ? 1 : 0));
+    if (m >= 2147483647.0) return false;
+  }
   return true;
 }
 
@@ -554,12 +635,15 @@ int64_t nifc_of(const teno_grid* g, int d) {
 }
 
 int adj_blocks(int nsm) { return nsm * 8; }
+// blocks of the list-building passes (at most 8 kListThreads, the scan's reach)
+int adj_list_blocks(int nsm) { return nsm * 4 < 8 * kListThreads ? nsm * 4 : 8 * kListThreads; }
 
 struct AdjLayout {
   // header: [0] status, [8] dt, [64] alpha bits (9 x 8), [136] pending-list counters of the
   // recomputed forward stages (3 x 4), [160] arg-max (9 x 8)
   size_t status = 0, dt = 8, alpha = 64, argidx = 160;
-  size_t aux = 0, fh = 0, kb = 0, contrib = 0, pending = 0, list = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0, total = 0;
+  size_t aux = 0, fh = 0, kb = 0, contrib = 0, pending = 0, list = 0, lcount = 0, apart = 0, R = 0, U1 = 0, U2 = 0,
+         B1 = 0, B2 = 0, total = 0;
 };
 
 AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
@@ -577,8 +661,10 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   off += round_up(sizeof(double) * 6 * nvar * size_t(maxifc));
   L.pending = off;
   off += round_up(size_t(maxifc));
-  L.list = off;   // pending list of the recomputed forward stages
+  L.list = off;   // pending list (recomputed forward stages; the adjoint's general pass)
   off += round_up(sizeof(uint32_t) * size_t(maxifc));
+  L.lcount = off;   // the general pass's per-block counts, offsets and total
+  off += round_up(sizeof(int) * (2 * size_t(adj_list_blocks(nsm)) + 1));
   L.apart = off;
   off += round_up(sizeof(double) * 3 * 2 * size_t(adj_blocks(nsm)));
   if (op == TENO_OP_RK3_ADJOINT) {
@@ -636,12 +722,21 @@ bool al(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 
 template <int NDIM, int DIR>
 void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const double* aux,
                     const unsigned long long* alpha, const double* Rbar, double scale, double* kb,
-                    double* contrib, unsigned char* pending, double* apart, int* status, double* Ubar,
-                    const unsigned long long* argidx,
+                    double* contrib, unsigned char* pending, uint32_t* list, int* lcount, double* apart,
+                    int* status, double* Ubar, const unsigned long long* argidx,
                     const Grid& G, const Scheme& S) {
   adj_kept_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
                                                           status, G, S);
-  adj_general_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, contrib, pending,
+  int64_t nifc = 1;
+  for (int k = 0; k < 3; ++k) nifc *= G.n[k] + (k == DIR ? 1 : 0);
+  const int lblk = adj_list_blocks(nsm);
+  int* bcount = lcount;
+  int* boff = lcount + lblk;
+  int* total = lcount + 2 * lblk;
+  adj_count_kernel<<<lblk, kListThreads, 0, st>>>(pending, nifc, bcount);
+  adj_scan_kernel<<<1, kListThreads, 0, st>>>(bcount, lblk, boff, total);
+  adj_scatter_kernel<<<lblk, kListThreads, 0, st>>>(pending, nifc, boff, list);
+  adj_general_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, contrib, list, total,
                                                              apart + 3 * nblk, status, G, S);
   int64_t gb = (G.ncell + 255) / 256;
   if (gb > int64_t(nsm) * 16) gb = int64_t(nsm) * 16;
@@ -654,7 +749,7 @@ void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const d
 teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, const double* U,
                              const double* Rbar, double* Ubar, double scale, cudaStream_t st) {
   const Grid G = make_grid(g);
-  const Scheme S = teno::make_scheme(g->gamma, g->H, g->eps, g->b_l, g->b_u);
+  const Scheme S = teno::scheme_of(g);
   const int nsm = sm_count();
   const int nblk = adj_blocks(nsm);
   int* status = reinterpret_cast<int*>(ws + L.status);
@@ -665,6 +760,8 @@ teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, c
   double* contrib = reinterpret_cast<double*>(ws + L.contrib);
   double* apart = reinterpret_cast<double*>(ws + L.apart);
   auto* pending = reinterpret_cast<unsigned char*>(ws + L.pending);
+  auto* list = reinterpret_cast<uint32_t*>(ws + L.list);
+  auto* lcount = reinterpret_cast<int*>(ws + L.lcount);
   if (cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
   if (cudaMemsetAsync(argidx, 0xff, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
   if (teno::launch_cell(g->ndim, U, aux, nullptr, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
@@ -678,12 +775,12 @@ teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, c
     default: argmax_kernel<3><<<unsigned(cb), 256, 0, st>>>(U, alpha, argidx, G.ncell, g->gamma, aux); break;
   }
   for (int d = 0; d < g->ndim; ++d) {
-    if (g->ndim == 1) launch_adj_dir<1, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
-    else if (g->ndim == 2 && d == 0) launch_adj_dir<2, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
-    else if (g->ndim == 2) launch_adj_dir<2, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
-    else if (d == 0) launch_adj_dir<3, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
-    else if (d == 1) launch_adj_dir<3, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
-    else launch_adj_dir<3, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, apart, status, Ubar, argidx, G, S);
+    if (g->ndim == 1) launch_adj_dir<1, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
+    else if (g->ndim == 2 && d == 0) launch_adj_dir<2, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
+    else if (g->ndim == 2) launch_adj_dir<2, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
+    else if (d == 0) launch_adj_dir<3, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
+    else if (d == 1) launch_adj_dir<3, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
+    else launch_adj_dir<3, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
     if (cudaGetLastError() != cudaSuccess) return TENO_ERR_CUDA;
   }
   return TENO_OK;
@@ -708,7 +805,9 @@ size_t teno_adjoint_workspace_bytes(const teno_grid* g, int op) {
 
 teno_status teno_rhs_adjoint(const teno_grid* g, const double* U, const double* dUdt_bar, double* U_bar,
                              void* ws, size_t ws_bytes, void* stream) {
-  if (has_reflective(g)) return TENO_ERR_UNSUPPORTED;
+  // reflecting walls are not differentiated; WENO-Z's weights are not
+  // piecewise constant (the TENO cutoffs are)
+  if (has_reflective(g) || g->scheme == TENO_SCHEME_WENOZ) return TENO_ERR_UNSUPPORTED;
   if (!grid_valid(g) || !U || !dUdt_bar || !U_bar) return TENO_ERR_INVALID_ARG;
   if (!al(U, 16) || !al(dUdt_bar, 16) || !al(U_bar, 16)) return TENO_ERR_INVALID_ARG;
   if (U_bar == U || U_bar == dUdt_bar) return TENO_ERR_INVALID_ARG;
@@ -721,7 +820,9 @@ teno_status teno_rhs_adjoint(const teno_grid* g, const double* U, const double* 
 
 teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double dt, const double* Ubar_next,
                                   double* Ubar_n, void* ws, size_t ws_bytes, void* stream) {
-  if (has_reflective(g)) return TENO_ERR_UNSUPPORTED;
+  // reflecting walls are not differentiated; WENO-Z's weights are not
+  // piecewise constant (the TENO cutoffs are)
+  if (has_reflective(g) || g->scheme == TENO_SCHEME_WENOZ) return TENO_ERR_UNSUPPORTED;
   if (!grid_valid(g) || !U_n || !Ubar_next || !Ubar_n || !(dt >= 0.0) || !std::isfinite(dt))
     return TENO_ERR_INVALID_ARG;
   if (!al(U_n, 16) || !al(Ubar_next, 16) || !al(Ubar_n, 16) || Ubar_n == U_n) return TENO_ERR_INVALID_ARG;

@@ -142,3 +142,32 @@ def test_host_pipeline_equals_one_item_at_a_time(api):
         U = hi.cuda()
         api.Solver(grid).step(U)
         assert torch.equal(U.cpu(), ho)
+
+
+def _full_grid_steps(api, oracle, P, steps):
+    """`steps` CFL steps of the whole grid on the GPU (the benchmark's
+    flag-free path: certified closed form plus pending pass) and in the oracle
+    (one call, all host cores)."""
+    Ug, tg, dg = _gpu_run(api, P, steps)
+    Uo, to, k = oracle.euler_run(P.U0, P.n, P.dx, P.bc, P.t_end, sigma=P.cfl, max_steps=steps,
+                                 params=oracle.Params(gamma=P.gamma))
+    assert k == steps
+    assert tg == pytest.approx(to, rel=1e-13)
+    err = rel_l1_err(Ug, Uo)
+    assert err <= STEP_RTOL, err
+    return err
+
+
+@pytest.mark.slow
+def test_four_quadrant_2048_twenty_steps_full_grid(api, oracle):
+    """The 2D four-quadrant configuration at its benchmark size, 20 RK3
+    steps, every cell against the oracle (eq. 4.1-4.3, eq. dt2)."""
+    _full_grid_steps(api, oracle, inputs.riemann_2d(n=2048, t_end=10.0), 20)
+
+
+@pytest.mark.slow
+def test_turbulence_256_two_steps_full_grid(api, oracle):
+    """The 3D turbulence box at the benchmark's size and launch configuration
+    (api.Solver, the flag-free two-pass flux evaluation), 2 RK3 steps, every
+    cell against the oracle."""
+    _full_grid_steps(api, oracle, inputs.solenoidal_turbulence(n=256, t_end=10.0), 2)
