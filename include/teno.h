@@ -57,11 +57,15 @@ typedef enum {
 typedef enum {
   TENO_BC_PERIODIC = 0,      /* wrap-around                                   */
   TENO_BC_TRANSMISSIVE = 1,  /* zero gradient: the boundary cell is copied    */
-  TENO_BC_REFLECTIVE = 2     /* solid wall: cells mirrored about the wall with */
+  TENO_BC_REFLECTIVE = 2,    /* solid wall: cells mirrored about the wall with */
                              /* the normal velocity reversed (Sec. 4.2's blast */
                              /* waves); teno_rhs, teno_rk3_step and            */
                              /* teno_rhs_noalloc only (the adjoint and batched */
                              /* entry points return TENO_ERR_UNSUPPORTED)      */
+  TENO_BC_DIRICHLET = 3      /* fixed state: every ghost cell of a face holds  */
+                             /* the face's teno_grid.bc_state (Sec. 4.3.2's    */
+                             /* Rayleigh-Taylor top and bottom); teno_rhs,     */
+                             /* teno_rk3_step and the staged step only         */
 } teno_bc;
 
 /* The reconstruction's cutoff (teno_grid.scheme).  The paper's method is
@@ -93,6 +97,13 @@ typedef struct {
   double eps;        /* epsilon of eq. 2.8 / eq. 3.2 (paper: 1e-6)           */
   int scheme;        /* teno_scheme (TENO_SCHEME_LAD = 0)                     */
   int ct_m;          /* TENO_SCHEME_TENO5 only: C_T = 10^-ct_m, 1..15         */
+  double grav[3];    /* body acceleration g: the source (0, rho g, rho u.g)   */
+                     /* is added to L(U) (Sec. 4.3.2: rho in the y momentum,  */
+                     /* rho v in the energy, g = (0, 1)); zero: no source.    */
+                     /* teno_rhs, teno_rk3_step, the staged step only         */
+  double bc_state[3][2][5]; /* TENO_BC_DIRICHLET axes: the conservative      */
+                     /* ghost state (rho, rho u.., E; first nvar entries) of  */
+                     /* the low [0] and high [1] face; rho, p > 0, finite     */
 } teno_grid;
 
 /* Workspace sizes for each operation (teno_workspace_bytes `op`). */
@@ -149,6 +160,72 @@ teno_status teno_rk3_step(const teno_grid* g, double* U, double cfl,
                           double dt_fixed, double* t_dev, double t_end,
                           double* dt_dev, void* ws, size_t ws_bytes,
                           void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Decomposed stepping: one SSP-RK3 step in stages, so that a caller that    */
+/* splits the domain over GPUs (or over slabs) can exchange halos and reduce */
+/* the LF speeds between the stages.                                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A step of teno_rk3_step is, for stage k = 1, 2, 3 with input
+ * Uin = U^n, U1, U2 and output Uout = U1, U2, U^n:
+ *   teno_rk3_stage_begin(g, Uin, ...)   cell pass: primitives of Uin and this
+ *                                       grid's Lax-Friedrichs speeds, written
+ *                                       to the workspace as nine 64-bit words
+ *                                       at byte teno_alpha_offset() (per
+ *                                       direction: max|u-c|, max|u|, max|u+c|
+ *                                       as the bit patterns of non-negative
+ *                                       doubles, so an integer maximum over
+ *                                       ranks is the maximum of the speeds);
+ *   [the caller replaces the nine words by their maximum over all ranks]
+ *   teno_rk3_stage_end(g, k, Uin, U^n, Uout, ...)
+ *                                       stage 1 also takes dt (eq. dt1 / dt2 /
+ *                                       the 3D form, from the speeds in the
+ *                                       workspace, or dt_fixed) and advances
+ *                                       *t_dev; then the interface fluxes,
+ *                                       the difference and the stage of
+ *                                       eq. 4.1 / 4.2 / 4.3.
+ * Called in this order on one grid and workspace with nothing in between,
+ * the stages give teno_rk3_step's result bit for bit (global LF speeds and
+ * dt are functions of the speeds alone, Sec. 4 and reading C7).
+ *
+ * Domain decomposition along the slowest axis (z in 3D, y in 2D, x in 1D):
+ * a rank stores its slab with three ghost planes on each side (n along that
+ * axis = interior planes + 6; transmissive bc on that axis) and fills the
+ * ghost planes of every stage input before stage_begin -- from the
+ * neighbouring slabs' interior planes (periodic ends wrap), or, at a
+ * transmissive end, with copies of the boundary plane.  The interior cells'
+ * fluxes then read only real data, and the interior result equals the
+ * undivided grid's bit for bit.  The ghost planes' own results are not
+ * meaningful.
+ *   Uin, Un, Uout : device states of grid g; stage 1: Uin == Un, Uout != Un;
+ *                   stage 2: Uout distinct from both; stage 3: Uout may be Un.
+ *   t_dev, dt_dev, cfl, dt_fixed, t_end : as teno_rk3_step (stage 1 only).
+ *   ws : >= teno_workspace_bytes(g, TENO_OP_RK3), the same for all stages.
+ */
+teno_status teno_rk3_stage_begin(const teno_grid* g, const double* Uin, void* ws,
+                                 size_t ws_bytes, void* stream);
+teno_status teno_rk3_stage_end(const teno_grid* g, int stage, const double* Uin,
+                               double* Un, double* Uout, double cfl,
+                               double dt_fixed, double* t_dev, double t_end,
+                               double* dt_dev, void* ws, size_t ws_bytes,
+                               void* stream);
+
+/* Byte offset, in any workspace, of the nine LF-speed words (above). */
+size_t teno_alpha_offset(void);
+
+/*
+ * teno_planes_copy -- copies nplanes consecutive planes along the slowest
+ * axis (all nvar fields) from src to dst, both device arrays: a state of
+ * grid g (planes from src_plane / dst_plane) or, with *_packed = 1, a packed
+ * buffer [nvar][nplanes][plane] (plane = cells of one plane).  One
+ * cudaMemcpy2DAsync on `stream`; used for halo exchange (between slabs on
+ * one GPU, or packing for a transfer between GPUs).
+ */
+teno_status teno_planes_copy(const teno_grid* g, const double* src, int64_t src_plane,
+                             int src_packed, double* dst, int64_t dst_plane,
+                             int dst_packed, int64_t nplanes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched mode: many independent 1D problems advanced together.             */

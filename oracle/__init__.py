@@ -28,6 +28,8 @@ _lib = None
 
 BC_PERIODIC = 0
 BC_TRANSMISSIVE = 1
+BC_REFLECTIVE = 2
+BC_DIRICHLET = 3
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +46,8 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("H", ctypes.c_double), ("eps", ctypes.c_double),
-                ("b_l", ctypes.c_int), ("b_u", ctypes.c_int), ("scheme", ctypes.c_int), ("ct_m", ctypes.c_int)]
+                ("b_l", ctypes.c_int), ("b_u", ctypes.c_int), ("scheme", ctypes.c_int), ("ct_m", ctypes.c_int),
+                ("grav", ctypes.c_double * 3), ("bc_state", ctypes.c_double * 30)]
 
 
 # The reconstruction's cutoff or weights (see or_teno5_lad): the paper's
@@ -64,9 +67,14 @@ class Params:
     b_u: int = 10
     scheme: str = "lad"
     ct_m: int = 7
+    grav: tuple = (0.0, 0.0, 0.0)      # body acceleration of Sec. 4.3.2's source
+    bc_state: object = None            # bc 3: conservative ghost states [3][2][5]
 
     def c(self) -> _Params:
-        return _Params(self.gamma, self.H, self.eps, self.b_l, self.b_u, SCHEMES[self.scheme], self.ct_m)
+        g = (ctypes.c_double * 3)(*[float(x) for x in (list(self.grav) + [0.0] * 3)[:3]])
+        st = np.zeros(30) if self.bc_state is None else np.asarray(self.bc_state, dtype=np.float64).reshape(30)
+        return _Params(self.gamma, self.H, self.eps, self.b_l, self.b_u, SCHEMES[self.scheme], self.ct_m, g,
+                       (ctypes.c_double * 30)(*st.tolist()))
 
 
 _D = ctypes.POINTER(ctypes.c_double)

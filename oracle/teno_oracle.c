@@ -36,7 +36,10 @@
  * stencil when chi_k >= C_T; transmissive boundaries copy the boundary cell
  * into three ghost cells, periodic ones wrap, reflecting ones (the blast-wave
  * test of Sec. 4.2) mirror the cells about the wall with the normal velocity
- * reversed; the LF speeds and the time step use the interior cells only.
+ * reversed, fixed-state ones (Sec. 4.3.2's top and bottom) hold the given
+ * state; the LF speeds and the time step use the interior cells only.  The
+ * Rayleigh-Taylor body force of Sec. 4.3.2 (rho added to the y momentum, rho v
+ * to the energy) is the source (0, rho g, rho u.g) added to L(U).
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no FMA contraction,
  * so every product and sum is rounded separately as written).
@@ -58,6 +61,9 @@ typedef struct {
   int b_u;      /* upper magnitude bound B_u (eq. 3.1) */
   int scheme;   /* OR_SCHEME_*: which cutoff / weights (see or_teno5_lad) */
   int ct_m;     /* OR_SCHEME_TENO5: the fixed C_T = 10^-ct_m (Sec. 4: 7) */
+  double grav[3];            /* body acceleration: source (0, rho g, rho u.g) (Sec. 4.3.2) */
+  double bc_state[3][2][5];  /* bc 3 (fixed state): conservative ghost state of the
+                                low [0] and high [1] face of each direction */
 } or_params;
 
 /* The reconstruction's cutoff or weights:
@@ -478,7 +484,14 @@ static int interface_flux(const or_shape* s, int d, const int64_t ifc[3],
   int64_t base = ifc[d] - 1; /* i */
   for (int j = 0; j < 6; ++j) {
     int64_t idx[3] = {ifc[0], ifc[1], ifc[2]};
-    idx[d] = ghost_index(base - 2 + j, s->n[d], bc[d]);
+    int64_t k = base - 2 + j;
+    if (bc[d] == 3 && (k < 0 || k >= s->n[d])) {
+      /* fixed-state face: the ghost cell holds the face's state */
+      for (int r = 0; r < nvar; ++r) Upt[j][r] = P->bc_state[d][k < 0 ? 0 : 1][r];
+      physical_flux(ndim, d, Upt[j], P->gamma, Fpt[j]);
+      continue;
+    }
+    idx[d] = ghost_index(k, s->n[d], bc[d]);
     load_cell(s, U, cell_linear(s, idx), Upt[j]);
     /* reflecting wall: the ghost state has the normal momentum reversed */
     if (ghost_reflects(base - 2 + j, s->n[d], bc[d])) Upt[j][1 + d] = -Upt[j][1 + d];
@@ -541,6 +554,20 @@ static int interface_flux(const or_shape* s, int d, const int64_t ifc[3],
  *   alpha_out (nullable): [ndim][nvar] LF speeds used.
  * Returns 0, -1 for a non-physical state.
  */
+/* The body-force source of Sec. 4.3.2, S = (0, rho g, rho u.g), of cell lin
+ * added to out[r * ostride], r = 0..nvar-1. */
+static void add_source(const or_shape* s, const or_params* P, const double* U, int64_t lin, double* out,
+                       int64_t ostride) {
+  int ndim = s->ndim, nvar = s->nvar;
+  double rho = U[lin];
+  double w = 0.0;
+  for (int k = 0; k < ndim; ++k) {
+    out[(1 + k) * ostride] += rho * P->grav[k];
+    w += U[(1 + k) * s->ncell + lin] * P->grav[k];
+  }
+  out[(nvar - 1) * ostride] += w;
+}
+
 int or_euler_rhs(int ndim, const int64_t* n, const double* dx, const int* bc,
                  const or_params* P, const double* U, double* Rhs,
                  unsigned char* flags_out, const unsigned char* flags_in,
@@ -610,6 +637,7 @@ int or_euler_rhs(int ndim, const int64_t* n, const double* dx, const int* bc,
     }
     if (line_status) status = -1;
   }
+  for (int64_t lin = 0; lin < s.ncell; ++lin) add_source(&s, P, U, lin, Rhs + lin, s.ncell);
   return status;
 }
 
@@ -669,6 +697,7 @@ int or_euler_rhs_sample(int ndim, const int64_t* n, const double* dx,
       for (int r = 0; r < nvar; ++r)
         out[k * nvar + r] += -(Fh[1][r] - Fh[0][r]) / dx[d];
     }
+    add_source(&s, P, U, lin, out + k * nvar, 1);
   }
   return (status || bad) ? -1 : 0;
 }

@@ -19,7 +19,7 @@ STATUS_NAMES = {
     7: "TENO_ERR_UNIMPLEMENTED",
 }
 OP_RHS, OP_RK3, OP_RHS_ADJOINT, OP_RK3_ADJOINT = 0, 1, 2, 3
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_DIRICHLET = 0, 1, 2, 3
 KERNEL_KINDS = ("cell", "flux", "diff", "dt")
 
 
@@ -37,6 +37,8 @@ class TenoGrid(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("scheme", ctypes.c_int),
         ("ct_m", ctypes.c_int),
+        ("grav", ctypes.c_double * 3),
+        ("bc_state", ctypes.c_double * 30),
     ]
 
 
@@ -80,6 +82,12 @@ SIGNATURES = [
     ("teno_rhs", ctypes.c_int, [_GP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     ("teno_rk3_step", ctypes.c_int, [_GP, _VP, ctypes.c_double, ctypes.c_double, _VP,
                                      ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("teno_rk3_stage_begin", ctypes.c_int, [_GP, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("teno_rk3_stage_end", ctypes.c_int, [_GP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP,
+                                          ctypes.c_double, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("teno_alpha_offset", ctypes.c_size_t, []),
+    ("teno_planes_copy", ctypes.c_int, [_GP, _VP, ctypes.c_int64, ctypes.c_int, _VP, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_int64, _VP]),
     ("teno_get_device_status", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int)]),
     ("teno_adjoint_workspace_bytes", ctypes.c_size_t, [_GP, ctypes.c_int]),
     ("teno_rhs_adjoint", ctypes.c_int, [_GP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
@@ -137,7 +145,8 @@ def check(status: int, where: str) -> None:
         raise TenoError(status, where)
 
 
-def make_grid(n, dx, bc, gamma=1.4, H=10.0, b_l=4, b_u=10, eps=1e-6, scheme="lad", ct_m=7) -> TenoGrid:
+def make_grid(n, dx, bc, gamma=1.4, H=10.0, b_l=4, b_u=10, eps=1e-6, scheme="lad", ct_m=7, grav=None,
+              bc_state=None) -> TenoGrid:
     """teno_grid for an ndim = len(n) grid; bc may be one value or one per axis."""
     ndim = len(n)
     g = TenoGrid()
@@ -150,4 +159,11 @@ def make_grid(n, dx, bc, gamma=1.4, H=10.0, b_l=4, b_u=10, eps=1e-6, scheme="lad
     g.gamma, g.H, g.b_l, g.b_u, g.eps = float(gamma), float(H), int(b_l), int(b_u), float(eps)
     g.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     g.ct_m = int(ct_m)
+    for k, v in enumerate(list(grav or [])[:3]):
+        g.grav[k] = float(v)
+    if bc_state is not None:
+        # [3][2][5] conservative ghost states of fixed-state faces
+        flat = [float(x) for row in bc_state for side in row for x in side]
+        for i, v in enumerate(flat[:30]):
+            g.bc_state[i] = v
     return g

@@ -58,15 +58,28 @@ class Scheme:
 
 class EulerGrid:
     """A uniform ndim grid of ``n`` cells (x first) with spacing ``dx`` and
-    boundary types ``bc`` (0 periodic, 1 transmissive, 2 reflecting)."""
+    boundary types ``bc`` (0 periodic, 1 transmissive, 2 reflecting, 3 fixed
+    state).  ``grav``: body acceleration of the source (0, rho g, rho u.g)
+    (Sec. 4.3.2); ``bc_state``: for fixed-state axes, the conservative ghost
+    state of each face, indexed [axis][side] (side 0 low, 1 high)."""
 
-    def __init__(self, n, dx, bc, scheme: Scheme | None = None):
+    def __init__(self, n, dx, bc, scheme: Scheme | None = None, grav=None, bc_state=None):
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
         self.bc = tuple(bc) if isinstance(bc, (list, tuple)) else (int(bc),) * len(self.n)
         self.scheme = scheme or Scheme()
+        self.grav = tuple(float(v) for v in grav) if grav is not None else None
+        self.bc_state = bc_state
         s = self.scheme
-        self.c = _lib.make_grid(self.n, self.dx, self.bc, s.gamma, s.H, s.b_l, s.b_u, s.eps, s.scheme, s.ct_m)
+        st = None
+        if bc_state is not None:
+            st = [[[0.0] * 5, [0.0] * 5] for _ in range(3)]
+            for k in range(len(self.n)):
+                for side in range(2):
+                    vals = list(bc_state[k][side]) if bc_state[k] is not None else []
+                    st[k][side][:len(vals)] = [float(x) for x in vals]
+        self.c = _lib.make_grid(self.n, self.dx, self.bc, s.gamma, s.H, s.b_l, s.b_u, s.eps, s.scheme, s.ct_m,
+                                self.grav, st)
         self.lib = _lib.load()
 
     @property
@@ -437,3 +450,87 @@ class TenoRK3Rollout(torch.autograd.Function):
 def rollout(U0: torch.Tensor, grid: EulerGrid, steps: int, dt: float, checkpoint_every: int = 0) -> torch.Tensor:
     """Differentiable fixed-dt rollout (see TenoRK3Rollout)."""
     return TenoRK3Rollout.apply(U0, grid, steps, dt, checkpoint_every)
+
+
+# ----------------------------------------------------------------------------
+# Domain decomposition along the slowest axis (decomp.py): the GPU engine
+# ----------------------------------------------------------------------------
+
+def slab_grid(grid: EulerGrid, plan) -> EulerGrid:
+    """The stored grid of one slab of ``grid``: plan.stored planes along the
+    slowest axis (interior + 3 ghost planes per side), transmissive there
+    (the ghost planes carry the neighbours' or the boundary's data)."""
+    from . import decomp
+    ax = grid.ndim - 1
+    if plan.n != grid.n[ax]:
+        raise ValueError("plan does not match the grid")
+    n = list(grid.n)
+    n[ax] = plan.stored
+    bc = list(grid.bc)
+    if bc[ax] not in (_lib.BC_PERIODIC, _lib.BC_TRANSMISSIVE):
+        raise ValueError("the split axis must be periodic or transmissive")
+    bc[ax] = _lib.BC_TRANSMISSIVE
+    assert decomp.GHOST == 3
+    return EulerGrid(tuple(n), grid.dx, tuple(bc), grid.scheme, grid.grav, grid.bc_state)
+
+
+def slab_from_global(U: torch.Tensor, grid: EulerGrid, plan) -> torch.Tensor:
+    """A stored slab state (ghost planes zero) holding plan's planes of U."""
+    from .decomp import GHOST
+    shape = (grid.nvar,) + tuple(reversed(grid.n))
+    Ug = U.reshape(shape)
+    out = torch.zeros((grid.nvar, plan.stored) + shape[2:], dtype=U.dtype, device=U.device)
+    out[:, GHOST:GHOST + plan.count] = Ug[:, plan.start:plan.start + plan.count]
+    return out.reshape(-1)
+
+
+def slab_interior(Us: torch.Tensor, grid: EulerGrid, plan) -> torch.Tensor:
+    """The interior planes of a stored slab state, shaped like U's slice."""
+    from .decomp import GHOST
+    shape = (grid.nvar, plan.stored) + tuple(reversed(grid.n))[1:]
+    return Us.reshape(shape)[:, GHOST:GHOST + plan.count]
+
+
+class SlabEngine:
+    """decomp.py's engine for one slab on a GPU: the staged SSP-RK3 entry
+    points (teno_rk3_stage_begin / _end), the LF-speed words of its
+    workspace, and plane copies (teno_planes_copy)."""
+
+    def __init__(self, grid: EulerGrid, device="cuda", cfl: float = 0.5):
+        self.grid = grid
+        self.device = torch.device(device)
+        self.cfl = float(cfl)
+        self.ws = alloc_workspace(grid.workspace_bytes(_lib.OP_RK3), self.device)
+        off = int(grid.lib.teno_alpha_offset())
+        self._alpha = self.ws[off:off + 9 * 8].view(torch.int64)
+        self.t = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.dt = torch.zeros(1, dtype=torch.float64, device=self.device)
+        ax = grid.ndim - 1
+        self.plane = grid.ncell // grid.n[ax]
+
+    def begin(self, Uin: torch.Tensor) -> None:
+        g = self.grid
+        _check_state(Uin, g.nvar, g.ncell, "Uin")
+        _lib.check(g.lib.teno_rk3_stage_begin(ctypes.byref(g.c), _ptr(Uin), _ptr(self.ws), self.ws.numel(),
+                                              _stream_ptr()), "teno_rk3_stage_begin")
+
+    def alpha_words(self) -> torch.Tensor:
+        return self._alpha
+
+    def end(self, stage: int, Uin, Un, Uout, t_end: float = float("inf"), dt_fixed: float = 0.0) -> None:
+        g = self.grid
+        _lib.check(g.lib.teno_rk3_stage_end(ctypes.byref(g.c), int(stage), _ptr(Uin), _ptr(Un), _ptr(Uout),
+                                            self.cfl, float(dt_fixed), _ptr(self.t), float(t_end), _ptr(self.dt),
+                                            _ptr(self.ws), self.ws.numel(), _stream_ptr()), "teno_rk3_stage_end")
+
+    def copy_planes(self, src, src_plane, src_packed, dst, dst_plane, dst_packed, nplanes) -> None:
+        g = self.grid
+        _lib.check(g.lib.teno_planes_copy(ctypes.byref(g.c), _ptr(src), int(src_plane), int(src_packed), _ptr(dst),
+                                          int(dst_plane), int(dst_packed), int(nplanes), _stream_ptr()),
+                   "teno_planes_copy")
+
+    def packed(self, nplanes: int) -> torch.Tensor:
+        return torch.empty(self.grid.nvar * nplanes * self.plane, dtype=torch.float64, device=self.device)
+
+    def status(self) -> int:
+        return device_status(self.ws)

@@ -619,14 +619,17 @@ bool grid_valid(const teno_grid* g) {
   return true;
 }
 
-// Reflecting walls are not differentiated here (the adjoint supports
-// periodic and transmissive boundaries).
-bool has_reflective(const teno_grid* g) {
+// What the adjoint does not differentiate: reflecting walls and fixed-state
+// faces (it supports periodic and transmissive boundaries), a body-force
+// source, and WENO-Z (its weights are not piecewise constant; the TENO
+// cutoffs are).
+bool adjoint_unsupported(const teno_grid* g) {
   if (!g || g->ndim < 1 || g->ndim > 3) return false;
   for (int k = 0; k < g->ndim; ++k)
-    if (g->bc[k] == TENO_BC_REFLECTIVE) return true;
-  return false;
+    if (g->bc[k] == TENO_BC_REFLECTIVE || g->bc[k] == TENO_BC_DIRICHLET || g->grav[k] != 0.0) return true;
+  return g->scheme == TENO_SCHEME_WENOZ;
 }
+
 
 int64_t nifc_of(const teno_grid* g, int d) {
   int64_t m = 1;
@@ -805,9 +808,7 @@ size_t teno_adjoint_workspace_bytes(const teno_grid* g, int op) {
 
 teno_status teno_rhs_adjoint(const teno_grid* g, const double* U, const double* dUdt_bar, double* U_bar,
                              void* ws, size_t ws_bytes, void* stream) {
-  // reflecting walls are not differentiated; WENO-Z's weights are not
-  // piecewise constant (the TENO cutoffs are)
-  if (has_reflective(g) || g->scheme == TENO_SCHEME_WENOZ) return TENO_ERR_UNSUPPORTED;
+  if (adjoint_unsupported(g)) return TENO_ERR_UNSUPPORTED;
   if (!grid_valid(g) || !U || !dUdt_bar || !U_bar) return TENO_ERR_INVALID_ARG;
   if (!al(U, 16) || !al(dUdt_bar, 16) || !al(U_bar, 16)) return TENO_ERR_INVALID_ARG;
   if (U_bar == U || U_bar == dUdt_bar) return TENO_ERR_INVALID_ARG;
@@ -820,9 +821,7 @@ teno_status teno_rhs_adjoint(const teno_grid* g, const double* U, const double* 
 
 teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double dt, const double* Ubar_next,
                                   double* Ubar_n, void* ws, size_t ws_bytes, void* stream) {
-  // reflecting walls are not differentiated; WENO-Z's weights are not
-  // piecewise constant (the TENO cutoffs are)
-  if (has_reflective(g) || g->scheme == TENO_SCHEME_WENOZ) return TENO_ERR_UNSUPPORTED;
+  if (adjoint_unsupported(g)) return TENO_ERR_UNSUPPORTED;
   if (!grid_valid(g) || !U_n || !Ubar_next || !Ubar_n || !(dt >= 0.0) || !std::isfinite(dt))
     return TENO_ERR_INVALID_ARG;
   if (!al(U_n, 16) || !al(Ubar_next, 16) || !al(Ubar_n, 16) || Ubar_n == U_n) return TENO_ERR_INVALID_ARG;

@@ -19,6 +19,22 @@ constexpr size_t kHeader = 256;  // status word, dt, alpha bit patterns
 
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// the fixed ghost states of axis k are physical: rho > 0, p > 0, finite
+bool fixed_states_ok(const teno_grid* g, int k) {
+  const int nvar = g->ndim + 2;
+  for (int side = 0; side < 2; ++side) {
+    const double* U = g->bc_state[k][side];
+    double q = 0.0;
+    for (int v = 0; v < nvar; ++v)
+      if (!std::isfinite(U[v])) return false;
+    if (!(U[0] > 0.0)) return false;
+    for (int j = 0; j < g->ndim; ++j) q += U[1 + j] * U[1 + j];
+    const double p = (g->gamma - 1.0) * (U[nvar - 1] - 0.5 * q / U[0]);
+    if (!(p > 0.0) || !std::isfinite(p)) return false;
+  }
+  return true;
+}
+
 bool grid_ok(const teno_grid* g) {
   if (!g) return false;
   if (g->ndim < 1 || g->ndim > 3) return false;
@@ -27,8 +43,11 @@ bool grid_ok(const teno_grid* g) {
     if (k >= g->ndim && g->n[k] != 1) return false;
     if (k < g->ndim) {
       if (!(g->dx[k] > 0.0) || !std::isfinite(g->dx[k])) return false;
-      if (g->bc[k] != TENO_BC_PERIODIC && g->bc[k] != TENO_BC_TRANSMISSIVE && g->bc[k] != TENO_BC_REFLECTIVE)
+      if (g->bc[k] != TENO_BC_PERIODIC && g->bc[k] != TENO_BC_TRANSMISSIVE && g->bc[k] != TENO_BC_REFLECTIVE &&
+          g->bc[k] != TENO_BC_DIRICHLET)
         return false;
+      if (!std::isfinite(g->grav[k])) return false;
+      if (g->bc[k] == TENO_BC_DIRICHLET && !fixed_states_ok(g, k)) return false;
     }
   }
   if (!(g->gamma > 1.0) || !std::isfinite(g->gamma)) return false;
@@ -54,7 +73,7 @@ struct Layout {
   // header: [0] status, [8] dt, [64] LF speeds (9 x 8) then the pending-list
   // counters (3 x 4)
   size_t status = 0, dt = 8, alpha = 64;
-  size_t aux = 0, fh = 0, fhat = 0, list = 0, R = 0, U1 = 0, U2 = 0, total = 0;
+  size_t aux = 0, fh = 0, fhat = 0, list = 0, ghost = 0, R = 0, U1 = 0, U2 = 0, total = 0;
 };
 
 Layout layout_of(const teno_grid* g, int op) {
@@ -72,6 +91,8 @@ Layout layout_of(const teno_grid* g, int op) {
   off += round_up(sizeof(double) * nvar * size_t(maxifc));
   L.list = off;
   off += round_up(sizeof(uint32_t) * size_t(maxifc));
+  L.ghost = off;   // fixed-state ghost cells (state, primitives, half fluxes of 6 face slots)
+  off += round_up(sizeof(double) * size_t(teno::ghost_block_doubles(g->ndim)));
   if (op == TENO_OP_RK3) {
     L.R = off;
     off += round_up(sizeof(double) * nvar * ncell);
@@ -94,10 +115,31 @@ Grid make_grid(const teno_grid* g) {
     G.rdx[k] = G.dx[0] / G.dx[k];
   }
   G.ncell = ncell_of(g);
+  for (int k = 0; k < 3; ++k) {
+    G.grav[k] = k < g->ndim ? g->grav[k] : 0.0;
+    if (G.grav[k] != 0.0) G.has_grav = 1;
+  }
   return G;
 }
 
 Scheme make_scheme(const teno_grid* g) { return teno::scheme_of(g); }
+
+// make_grid with the fixed-state ghost block of workspace ws attached
+Grid grid_in(const teno_grid* g, const Layout& L, char* ws) {
+  Grid G = make_grid(g);
+  double* gb = reinterpret_cast<double*>(ws + L.ghost);
+  const int nvar = g->ndim + 2;
+  G.gU = gb;
+  G.gaux = gb + nvar * teno::kGhostSlots;
+  G.gfh = gb + (nvar + teno::aux_fields(g->ndim)) * teno::kGhostSlots;
+  return G;
+}
+
+bool has_dirichlet(const teno_grid* g) {
+  for (int k = 0; k < g->ndim; ++k)
+    if (g->bc[k] == TENO_BC_DIRICHLET) return true;
+  return false;
+}
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -163,16 +205,45 @@ struct TimerScope {
     if ((call) != cudaSuccess) return TENO_ERR_CUDA;     \
   } while (0)
 
-// One right-hand-side evaluation of state `U`.  mode_last selects what the
-// last direction's difference kernel does (0: write/accumulate dUdt into R;
-// 2/3/4: SSP-RK3 stage into Uout).
-teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
-                         const double* U, double* R, uint8_t* flags,
-                         int mode_last, const double* Un, const double* Uk,
-                         double* Uout, cudaStream_t st, bool with_dt,
-                         double cfl, double dt_fixed, double* t_dev,
-                         double t_end, double* dt_out) {
-  const Grid G = make_grid(g);
+// The first half of a right-hand-side evaluation of state `U`: clear the LF
+// speeds and pending counters, then the cell pass (primitives, half fluxes
+// for the two-pass flux evaluation, this grid's LF speeds).
+teno_status stage_begin(const teno_grid* g, const Layout& L, char* ws, const double* U, bool one_pass,
+                        cudaStream_t st) {
+  const Grid G = grid_in(g, L, ws);
+  const int nsm = sm_count();
+  int* status = reinterpret_cast<int*>(ws + L.status);
+  auto* alpha = reinterpret_cast<unsigned long long*>(ws + L.alpha);
+  double* aux = reinterpret_cast<double*>(ws + L.aux);
+  double* fh = one_pass ? nullptr : reinterpret_cast<double*>(ws + L.fh);
+  TENO_CUDA(cudaMemsetAsync(alpha, 0, teno::kAlphaAndCountBytes, st));
+  TimerScope ts(st, TENO_KERNEL_CELL);
+  if (has_dirichlet(g)) {
+    teno::GhostStates gs;
+    std::memset(&gs, 0, sizeof(gs));
+    unsigned mask = 0;
+    for (int d = 0; d < g->ndim; ++d) {
+      if (g->bc[d] != TENO_BC_DIRICHLET) continue;
+      for (int side = 0; side < 2; ++side) {
+        for (int v = 0; v < g->ndim + 2; ++v) gs.U[2 * d + side][v] = g->bc_state[d][side][v];
+        mask |= 1u << (2 * d + side);
+      }
+    }
+    TENO_CUDA(teno::launch_ghost_cells(g->ndim, gs, mask, G, g->gamma, st));
+  }
+  TENO_CUDA(teno::launch_cell(g->ndim, U, aux, fh, alpha, status, G.ncell, g->gamma, nsm, st));
+  return TENO_OK;
+}
+
+// The second half, with the LF speeds in the workspace: the CFL step (with_dt),
+// then per direction the interface fluxes and the difference; mode_last
+// selects what the last direction's difference does (0: dUdt into R; 2/3/4:
+// the SSP-RK3 stage into Uout).
+teno_status stage_finish(const teno_grid* g, const Layout& L, char* ws, const double* U, double* R,
+                         uint8_t* flags, int mode_last, const double* Un, const double* Uk, double* Uout,
+                         cudaStream_t st, bool with_dt, double cfl, double dt_fixed, double* t_dev, double t_end,
+                         double* dt_out) {
+  const Grid G = grid_in(g, L, ws);
   const Scheme S = make_scheme(g);
   const int nsm = sm_count();
   int* status = reinterpret_cast<int*>(ws + L.status);
@@ -183,11 +254,6 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
   uint32_t* list = reinterpret_cast<uint32_t*>(ws + L.list);
   double* fh = flags ? nullptr : reinterpret_cast<double*>(ws + L.fh);   // the flag path is one-pass
   unsigned* count = reinterpret_cast<unsigned*>(ws + L.alpha + teno::kPendingCountOffset);
-  TENO_CUDA(cudaMemsetAsync(alpha, 0, teno::kAlphaAndCountBytes, st));
-  {
-    TimerScope ts(st, TENO_KERNEL_CELL);
-    TENO_CUDA(teno::launch_cell(g->ndim, U, aux, fh, alpha, status, G.ncell, g->gamma, nsm, st));
-  }
   if (with_dt) {
     TimerScope ts(st, TENO_KERNEL_DT);
     TENO_CUDA(teno::launch_dt(g->ndim, alpha, G, cfl, dt_fixed, t_dev, t_end, dt_ws, dt_out, st));
@@ -205,10 +271,23 @@ teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
     foff += int64_t(g->ndim + 2) * 2 * nifc_of(g, d);
     {
       TimerScope ts(st, TENO_KERNEL_DIFF);
-      TENO_CUDA(teno::launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt_ws, G, mode_last, nsm, st));
+      TENO_CUDA(teno::launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt_ws, G, mode_last, nsm, st, U));
     }
   }
   return TENO_OK;
+}
+
+// One right-hand-side evaluation of state `U` (both halves).
+teno_status rhs_sequence(const teno_grid* g, const Layout& L, char* ws,
+                         const double* U, double* R, uint8_t* flags,
+                         int mode_last, const double* Un, const double* Uk,
+                         double* Uout, cudaStream_t st, bool with_dt,
+                         double cfl, double dt_fixed, double* t_dev,
+                         double t_end, double* dt_out) {
+  const teno_status s = stage_begin(g, L, ws, U, flags != nullptr, st);
+  if (s != TENO_OK) return s;
+  return stage_finish(g, L, ws, U, R, flags, mode_last, Un, Uk, Uout, st, with_dt, cfl, dt_fixed, t_dev, t_end,
+                      dt_out);
 }
 
 }  // namespace
@@ -285,6 +364,62 @@ teno_status teno_rk3_step(const teno_grid* g, double* U, double cfl, double dt_f
   if (s != TENO_OK) return s;
   // eq. 4.3: U <- 1/3 U + 2/3 U2 + 2/3 dt L(U2)
   return rhs_sequence(g, L, w, U2, R, nullptr, 4, U, U2, U, st, false, 0, 0, nullptr, 0, nullptr);
+}
+
+teno_status teno_rk3_stage_begin(const teno_grid* g, const double* Uin, void* ws, size_t ws_bytes, void* stream) {
+  if (!grid_ok(g) || !Uin || !aligned(Uin, 16) || !is_device_ptr(Uin)) return TENO_ERR_INVALID_ARG;
+  const Layout L = layout_of(g, TENO_OP_RK3);
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < L.total || !is_device_ptr(ws)) return TENO_ERR_WORKSPACE;
+  return stage_begin(g, L, static_cast<char*>(ws), Uin, false, static_cast<cudaStream_t>(stream));
+}
+
+teno_status teno_rk3_stage_end(const teno_grid* g, int stage, const double* Uin, double* Un, double* Uout,
+                               double cfl, double dt_fixed, double* t_dev, double t_end, double* dt_dev, void* ws,
+                               size_t ws_bytes, void* stream) {
+  if (!grid_ok(g) || stage < 1 || stage > 3 || !Uin || !Un || !Uout) return TENO_ERR_INVALID_ARG;
+  if (!aligned(Uin, 16) || !aligned(Un, 16) || !aligned(Uout, 16)) return TENO_ERR_INVALID_ARG;
+  if (!is_device_ptr(Uin) || !is_device_ptr(Un) || !is_device_ptr(Uout)) return TENO_ERR_INVALID_ARG;
+  // stage 1 reads U^n itself and writes U1 elsewhere; stage 2 writes U2
+  // apart from its inputs; stage 3 may write over U^n
+  if ((stage == 1 && (Uin != Un || Uout == Un)) || (stage == 2 && (Uout == Un || Uout == Uin)) ||
+      (stage == 3 && Uout == Uin))
+    return TENO_ERR_INVALID_ARG;
+  if (stage == 1) {
+    if (!t_dev || !aligned(t_dev, 8) || !is_device_ptr(t_dev) || (dt_dev && !is_device_ptr(dt_dev)))
+      return TENO_ERR_INVALID_ARG;
+    if (!(dt_fixed > 0.0) && !(cfl > 0.0 && std::isfinite(cfl))) return TENO_ERR_INVALID_ARG;
+    if (!std::isfinite(dt_fixed) || std::isnan(t_end)) return TENO_ERR_INVALID_ARG;
+  }
+  const Layout L = layout_of(g, TENO_OP_RK3);
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < L.total || !is_device_ptr(ws)) return TENO_ERR_WORKSPACE;
+  char* w = static_cast<char*>(ws);
+  double* R = reinterpret_cast<double*>(w + L.R);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // eq. 4.1 / 4.2 / 4.3 (diff modes 2 / 3 / 4); dt from the LF speeds now in ws
+  return stage_finish(g, L, w, Uin, R, nullptr, stage + 1, Un, stage == 1 ? nullptr : Uin, Uout, st, stage == 1,
+                      cfl, dt_fixed, t_dev, t_end, dt_dev);
+}
+
+size_t teno_alpha_offset(void) { return Layout().alpha; }
+
+teno_status teno_planes_copy(const teno_grid* g, const double* src, int64_t src_plane, int src_packed,
+                             double* dst, int64_t dst_plane, int dst_packed, int64_t nplanes, void* stream) {
+  if (!grid_ok(g) || !src || !dst || nplanes < 1) return TENO_ERR_INVALID_ARG;
+  const int ax = g->ndim - 1;
+  const int64_t nax = g->n[ax];
+  const int64_t plane = ncell_of(g) / nax;
+  const int64_t ncell = ncell_of(g);
+  if (!src_packed && (src_plane < 0 || src_plane + nplanes > nax)) return TENO_ERR_INVALID_ARG;
+  if (!dst_packed && (dst_plane < 0 || dst_plane + nplanes > nax)) return TENO_ERR_INVALID_ARG;
+  if (!aligned(src, 8) || !aligned(dst, 8) || !is_device_ptr(src) || !is_device_ptr(dst)) return TENO_ERR_INVALID_ARG;
+  const size_t width = sizeof(double) * size_t(nplanes * plane);
+  const size_t spitch = src_packed ? width : sizeof(double) * size_t(ncell);
+  const size_t dpitch = dst_packed ? width : sizeof(double) * size_t(ncell);
+  const double* s0 = src + (src_packed ? 0 : src_plane * plane);
+  double* d0 = dst + (dst_packed ? 0 : dst_plane * plane);
+  TENO_CUDA(cudaMemcpy2DAsync(d0, dpitch, s0, spitch, width, size_t(g->ndim + 2), cudaMemcpyDeviceToDevice,
+                              static_cast<cudaStream_t>(stream)));
+  return TENO_OK;
 }
 
 teno_status teno_get_device_status(void* ws, void* stream, int* status) {

@@ -111,13 +111,23 @@ struct Scheme {
   double thr[kMaxLadder];
 };
 
+// entries per field of the fixed-state ghost block: one per face (2 d + side)
+constexpr int kGhostSlots = 6;
+
 struct Grid {
   int64_t n[3];
   int64_t ncell;
-  int bc[3];           // 0 periodic, 1 transmissive
+  int bc[3];           // 0 periodic, 1 transmissive, 2 reflecting, 3 fixed state
   double dx[3];
   double inv_dx[3];
   double rdx[3];       // dx[0] / dx[k] (exactly 1 for equal spacings)
+  double grav[3] = {0.0, 0.0, 0.0};   // body acceleration of the source (0, rho g, rho u.g)
+  int has_grav = 0;                    // grav is not zero
+  // fixed-state (bc 3) ghost cells: state, primitives and half fluxes of the
+  // virtual cells ncell + 2 d + side (see GhostCells)
+  const double* gU = nullptr;
+  const double* gaux = nullptr;
+  const double* gfh = nullptr;
 };
 
 // Index of a (possibly ghost) cell along an axis of n cells: periodic wrap,

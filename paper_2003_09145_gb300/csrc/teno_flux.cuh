@@ -9,6 +9,26 @@
 
 namespace teno {
 
+// Fixed-state (Dirichlet) ghost cells: a stencil point outside a Dirichlet
+// face is the virtual cell ncell + 2 d + side; its state, primitives and half
+// fluxes sit in small blocks laid out like the cell arrays with
+// kGhostSlots entries per field (U [nvar][6], aux [aux_fields][6],
+// fh [ndim][nvar - 1][6]), filled by the cell pass of the fixed states.
+struct GhostCells {
+  const double* U = nullptr;
+  const double* aux = nullptr;
+  const double* fh = nullptr;
+};
+
+// field `f` of cell c of an array with ncell entries per field, or of the
+// ghost block when GH and c is a virtual cell
+template <bool GH>
+__device__ __forceinline__ double ldc(const double* __restrict__ a, const double* __restrict__ ga, int64_t ncell,
+                                      int64_t f, int64_t c) {
+  if (GH && c >= ncell) return ga[f * kGhostSlots + (c - ncell)];
+  return a[f * ncell + c];
+}
+
 // Characteristic projection of one vector X (conservative ordering) onto the
 // left eigenvectors of the Roe state (reading of the convective-term
 // paragraph of Sec. 4; rows as in the library's design notes):
@@ -182,29 +202,34 @@ __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const d
 // Returns false, with `out` unwritten, when the test does not keep every
 // stencil; otherwise `out` equals interface_flux's.
 // ---------------------------------------------------------------------------
-template <int NDIM, int DIR>
+// (GH: the sweep direction has fixed-state ghost cells, read from gc; the
+// half fluxes of the ghost block are taken at direction DIR's block.)
+template <int NDIM, int DIR, bool GH = false>
 __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__ U,
                                                       const double* __restrict__ aux,
                                                       const double* __restrict__ fh, int64_t ncell,
                                                       const int64_t (&cells)[6], unsigned flips,
                                                       const double (&alpha)[NDIM + 2],
                                                       const double (&nal)[NDIM + 2], const Scheme& S,
-                                                      double (&out)[NDIM + 2], int* __restrict__ status) {
+                                                      double (&out)[NDIM + 2], int* __restrict__ status,
+                                                      const GhostCells& gc = GhostCells()) {
   constexpr int NVAR = NDIM + 2;
   if (S.keep_idx < 0) return false;
+  const double* gfh = GH ? gc.fh + DIR * (NVAR - 1) * kGhostSlots : nullptr;
   RoeIfc<NDIM> R;
   {
     double su2[NDIM], su3[NDIM];
 #pragma unroll
     for (int k = 0; k < NDIM; ++k) {
-      su2[k] = aux[(NDIM + 3 + k) * ncell + cells[2]];
-      su3[k] = aux[(NDIM + 3 + k) * ncell + cells[3]];
+      su2[k] = ldc<GH>(aux, gc.aux, ncell, NDIM + 3 + k, cells[2]);
+      su3[k] = ldc<GH>(aux, gc.aux, ncell, NDIM + 3 + k, cells[3]);
     }
     su2[DIR] = flip_sign(su2[DIR], (flips >> 2) & 1u);
     su3[DIR] = flip_sign(su3[DIR], (flips >> 3) & 1u);
-    roe_interface<NDIM, DIR>(aux[(NDIM + 1) * ncell + cells[2]], aux[(NDIM + 1) * ncell + cells[3]],
-                             aux[(NDIM + 2) * ncell + cells[2]], aux[(NDIM + 2) * ncell + cells[3]], su2, su3,
-                             S, R, status);
+    roe_interface<NDIM, DIR>(ldc<GH>(aux, gc.aux, ncell, NDIM + 1, cells[2]),
+                             ldc<GH>(aux, gc.aux, ncell, NDIM + 1, cells[3]),
+                             ldc<GH>(aux, gc.aux, ncell, NDIM + 2, cells[2]),
+                             ldc<GH>(aux, gc.aux, ncell, NDIM + 2, cells[3]), su2, su3, S, R, status);
   }
   CertIfc<NDIM> C;
   cert_begin<NDIM, DIR>(R, alpha, C);
@@ -219,12 +244,12 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
     const bool fj = (flips >> j) & 1u;
     double Uj[NVAR], Fhj[NVAR];
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) Uj[v] = U[v * ncell + c];
+    for (int v = 0; v < NVAR; ++v) Uj[v] = ldc<GH>(U, gc.U, ncell, v, c);
     Fhj[0] = 0.0;   // unused: the mass term comes from m_d
 #pragma unroll
-    for (int v = 1; v < NVAR; ++v) Fhj[v] = flip_sign(fh[(v - 1) * ncell + c], fj && v != 1 + DIR);
+    for (int v = 1; v < NVAR; ++v) Fhj[v] = flip_sign(ldc<GH>(fh, gfh, ncell, v - 1, c), fj && v != 1 + DIR);
     Uj[1 + DIR] = flip_sign(Uj[1 + DIR], fj);
-    const double unj = flip_sign(aux[DIR * ncell + c], fj), pnj = aux[NDIM * ncell + c];
+    const double unj = flip_sign(ldc<GH>(aux, gc.aux, ncell, DIR, c), fj), pnj = ldc<GH>(aux, gc.aux, ncell, NDIM, c);
     closed_point<NDIM, DIR>(j, Uj, Fhj, Ft, Ut);
     cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
   }
@@ -256,7 +281,7 @@ constexpr unsigned kUndecided = 0xffu;
 
 // the certify-only instantiation ends early: its remaining code is unreachable
 #pragma nv_diag_suppress 128
-template <int NDIM, int DIR, bool WITH_FLAGS, int MODE = kFluxFull>
+template <int NDIM, int DIR, bool WITH_FLAGS, int MODE = kFluxFull, bool GH = false>
 __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
                                                const double* __restrict__ aux,
                                                int64_t ncell, const int64_t (&cells)[6], unsigned flips,
@@ -264,7 +289,8 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
                                                const double (&nal)[NDIM + 2],
                                                const Scheme& S, double (&out)[NDIM + 2],
                                                unsigned (&fl)[NDIM + 2][2],
-                                               int* __restrict__ status) {
+                                               int* __restrict__ status,
+                                               const GhostCells& gc = GhostCells()) {
   constexpr int NVAR = NDIM + 2;
   {
     // six-point stencil i-2..i+3 with i = id - 1
@@ -275,21 +301,21 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
       const int64_t c = cells[j];
       const bool fj = (flips >> j) & 1u;   // mirrored wall point
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) Ux[j][v] = U[v * ncell + c];
+      for (int v = 0; v < NVAR; ++v) Ux[j][v] = ldc<GH>(U, gc.U, ncell, v, c);
       Ux[j][1 + DIR] = flip_sign(Ux[j][1 + DIR], fj);
-      un[j] = flip_sign(aux[DIR * ncell + c], fj);
-      pn[j] = aux[NDIM * ncell + c];
+      un[j] = flip_sign(ldc<GH>(aux, gc.aux, ncell, DIR, c), fj);
+      pn[j] = ldc<GH>(aux, gc.aux, ncell, NDIM, c);
       if (j == 2 || j == 3) {
         double* su = (j == 2) ? su2 : su3;
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) su[k] = aux[(NDIM + 3 + k) * ncell + c];
+        for (int k = 0; k < NDIM; ++k) su[k] = ldc<GH>(aux, gc.aux, ncell, NDIM + 3 + k, c);
         su[DIR] = flip_sign(su[DIR], fj);
         if (j == 2) {
-          sr2 = aux[(NDIM + 1) * ncell + c];
-          sh2 = aux[(NDIM + 2) * ncell + c];
+          sr2 = ldc<GH>(aux, gc.aux, ncell, NDIM + 1, c);
+          sh2 = ldc<GH>(aux, gc.aux, ncell, NDIM + 2, c);
         } else {
-          sr3 = aux[(NDIM + 1) * ncell + c];
-          sh3 = aux[(NDIM + 2) * ncell + c];
+          sr3 = ldc<GH>(aux, gc.aux, ncell, NDIM + 1, c);
+          sh3 = ldc<GH>(aux, gc.aux, ncell, NDIM + 2, c);
         }
       }
     }

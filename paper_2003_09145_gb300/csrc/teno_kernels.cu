@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256, TENO_CELL_MINBLOCKS) cell_kernel(const do
 #define TENO_FLUX_MINBLOCKS 4
 #endif
 
-template <int NDIM, int DIR, bool WITH_FLAGS>
+template <int NDIM, int DIR, bool WITH_FLAGS, bool GH>
 __global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
     const double* __restrict__ U, const double* __restrict__ aux,
     const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
@@ -165,12 +165,14 @@ __global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       bool f;
-      cells[j] = base + ghost(id - 3 + j, nd, bcd, f) * stride_d;
-      flips |= unsigned(f) << j;
+      const int64_t k = id - 3 + j;
+      cells[j] = (GH && (k < 0 || k >= nd)) ? ncell + 2 * DIR + (k >= nd) : base + ghost(k, nd, bcd, f) * stride_d;
+      flips |= GH ? 0u : unsigned(f) << j;
     }
     double out[NVAR];
     unsigned fl[NVAR][2];
-    interface_flux<NDIM, DIR, WITH_FLAGS>(U, aux, ncell, cells, flips, alpha, nal, S, out, fl, status);
+    interface_flux<NDIM, DIR, WITH_FLAGS, kFluxFull, GH>(U, aux, ncell, cells, flips, alpha, nal, S, out, fl, status,
+                                                        GhostCells{G.gU, G.gaux, G.gfh});
     if (WITH_FLAGS) {
       // direction block offset is applied by the caller through `flags`
 #pragma unroll
@@ -197,7 +199,9 @@ __global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
 #define TENO_CLOSED_MINBLOCKS 4
 #endif
 
-template <int NDIM, int DIR>
+// GH: fixed-state faces along DIR, whose ghost points are the virtual cells
+// ncell + 2 DIR + side
+template <int NDIM, int DIR, bool GH = false>
 __device__ __forceinline__ void interface_cells(int64_t q, const Grid& G, int64_t (&cells)[6], unsigned& flips) {
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
   const int64_t stride_d = (DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1]);
@@ -213,8 +217,13 @@ __device__ __forceinline__ void interface_cells(int64_t q, const Grid& G, int64_
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     bool f;
-    cells[j] = base + ghost(id - 3 + j, G.n[DIR], G.bc[DIR], f) * stride_d;
-    flips |= unsigned(f) << j;
+    const int64_t k = id - 3 + j;
+    if (GH && (k < 0 || k >= G.n[DIR])) {
+      cells[j] = G.ncell + 2 * DIR + (k >= G.n[DIR]);
+    } else {
+      cells[j] = base + ghost(k, G.n[DIR], G.bc[DIR], f) * stride_d;
+      flips |= unsigned(f) << j;
+    }
   }
 }
 
@@ -233,10 +242,11 @@ __device__ __forceinline__ void half_speeds(const unsigned long long* __restrict
   for (int f = 0; f < NVAR; ++f) nal[f] = -2.0 * alpha[f];
 }
 
-// REFLECT: the sweep direction has a reflecting wall, so stencil points may be
-// mirrored; without one the mirror flags are the constant 0 and their sign
+// WALL: 1 -- the sweep direction has a reflecting wall, so stencil points may
+// be mirrored; 2 -- fixed-state faces (ghost points read from the ghost
+// block); 0 -- neither: the mirror flags are the constant 0 and their sign
 // flips fold away.
-template <int NDIM, int DIR, bool REFLECT>
+template <int NDIM, int DIR, int WALL>
 __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel(
     const double* __restrict__ U, const double* __restrict__ aux, const double* __restrict__ fh,
     const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
@@ -251,10 +261,11 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
        q += (int64_t)gridDim.x * blockDim.x) {
     int64_t cells[6];
     unsigned flips;
-    interface_cells<NDIM, DIR>(q, G, cells, flips);
+    interface_cells<NDIM, DIR, WALL == 2>(q, G, cells, flips);
     double out[NVAR];
-    const bool done = interface_flux_closed<NDIM, DIR>(U, aux, fh + (int64_t)DIR * (NVAR - 1) * G.ncell, G.ncell, cells,
-                                                       REFLECT ? flips : 0u, alpha, nal, S, out, status);
+    const bool done = interface_flux_closed<NDIM, DIR, WALL == 2>(
+        U, aux, fh + (int64_t)DIR * (NVAR - 1) * G.ncell, G.ncell, cells, WALL == 1 ? flips : 0u, alpha, nal, S,
+        out, status, GhostCells{G.gU, G.gaux, G.gfh});
     if (done) {
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
@@ -272,7 +283,7 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
   }
 }
 
-template <int NDIM, int DIR>
+template <int NDIM, int DIR, bool GH>
 __global__ void __launch_bounds__(128) flux_pending_kernel(
     const double* __restrict__ U, const double* __restrict__ aux,
     const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
@@ -288,10 +299,11 @@ __global__ void __launch_bounds__(128) flux_pending_kernel(
     const int64_t q = list[i];
     int64_t cells[6];
     unsigned flips;
-    interface_cells<NDIM, DIR>(q, G, cells, flips);
+    interface_cells<NDIM, DIR, GH>(q, G, cells, flips);
     double out[NVAR];
     unsigned fl[NVAR][2];
-    interface_flux<NDIM, DIR, false, kFluxChar>(U, aux, G.ncell, cells, flips, alpha, nal, S, out, fl, status);
+    interface_flux<NDIM, DIR, false, kFluxChar, GH>(U, aux, G.ncell, cells, flips, alpha, nal, S, out, fl, status,
+                                                   GhostCells{G.gU, G.gaux, G.gfh});
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
   }
@@ -316,11 +328,13 @@ __global__ void __launch_bounds__(128) flux_pending_kernel(
 // ---------------------------------------------------------------------------
 constexpr int kDiffFirst = 0, kDiffAcc = 1, kDiffRhs = 5;
 
-template <int NDIM, int DIR, int MODE>
+// GRAV (last direction only): the body-force source of Sec. 4.3.2,
+// S = (0, rho g, rho u.g), is added from the stage input Usrc.
+template <int NDIM, int DIR, int MODE, bool GRAV = false>
 __global__ void __launch_bounds__(256) diff_kernel(
     const double* __restrict__ Fhat, double* __restrict__ R,
     const double* Un, const double* Uk,   // not restrict: stage 3 writes Uout = Un in place
-    double* Uout, const double* __restrict__ dt_ptr, Grid G) {
+    double* Uout, const double* __restrict__ dt_ptr, Grid G, const double* Usrc) {
   constexpr bool stage = MODE >= 2 && MODE <= 4;
   constexpr bool acc = DIR > 0;   // R holds the earlier directions' sum
   constexpr int NVAR = NDIM + 2;
@@ -363,12 +377,28 @@ __global__ void __launch_bounds__(256) diff_kernel(
     if (acc)
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) s[v] = fma(rd, s[v], R[v * ncell + cc]);
+    double src[NVAR];
+    if (GRAV) {
+      const double rho = Usrc[cc];
+      double w = 0.0;
+      src[0] = 0.0;
+#pragma unroll
+      for (int k = 0; k < NDIM; ++k) {
+        src[1 + k] = rho * G.grav[k];
+        w = fma(Usrc[(1 + k) * ncell + cc], G.grav[k], w);
+      }
+      src[NVAR - 1] = w;
+      // L = s / dx_0 + S: a stage takes c (s + dx_0 S) with c = dt / dx_0
+      if (stage)
+#pragma unroll
+        for (int v = 1; v < NVAR; ++v) s[v] = fma(G.dx[0], src[v], s[v]);
+    }
     if (MODE == kDiffFirst || MODE == kDiffAcc) {
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = s[v];
     } else if (MODE == kDiffRhs) {
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = s[v] * G.inv_dx[0];
+      for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = GRAV ? fma(s[v], G.inv_dx[0], src[v]) : s[v] * G.inv_dx[0];
     } else {
       double o[NVAR];
 #pragma unroll
@@ -495,6 +525,39 @@ Scheme make_scheme(double gamma, double H, double eps, int b_l, int b_u, int var
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-state ghost cells: one thread per face slot, the cell pass's formulas
+// on the face states (kGhostSlots entries per field).
+// ---------------------------------------------------------------------------
+template <int NDIM>
+__global__ void ghost_cell_kernel(GhostStates gs, unsigned mask, double* __restrict__ gU,
+                                  double* __restrict__ gaux, double* __restrict__ gfh, double gamma,
+                                  int* __restrict__ status) {
+  constexpr int NVAR = NDIM + 2;
+  const int slot = threadIdx.x;
+  if (slot >= kGhostSlots || !((mask >> slot) & 1u)) return;
+  double Uc[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) gU[v * kGhostSlots + slot] = Uc[v] = gs.U[slot][v];
+  double uh[NDIM], cs, ep;
+  if (!cell_primitives<NDIM>(gU, kGhostSlots, slot, gamma, gaux, uh, cs, ep) && status)
+    atomicOr(status, kStatusNonphysical);
+  store_flux_half<NDIM, 0>(Uc, uh, gaux[NDIM * kGhostSlots + slot], ep, gfh, kGhostSlots, slot);
+}
+
+cudaError_t launch_ghost_cells(int ndim, const GhostStates& gs, unsigned mask, const Grid& G, double gamma,
+                               cudaStream_t st) {
+  double* gU = const_cast<double*>(G.gU);
+  double* gaux = const_cast<double*>(G.gaux);
+  double* gfh = const_cast<double*>(G.gfh);
+  switch (ndim) {
+    case 1: ghost_cell_kernel<1><<<1, 32, 0, st>>>(gs, mask, gU, gaux, gfh, gamma, nullptr); break;
+    case 2: ghost_cell_kernel<2><<<1, 32, 0, st>>>(gs, mask, gU, gaux, gfh, gamma, nullptr); break;
+    default: ghost_cell_kernel<3><<<1, 32, 0, st>>>(gs, mask, gU, gaux, gfh, gamma, nullptr); break;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static inline int blocks_for(int64_t n, int threads, int cap) {
@@ -522,20 +585,24 @@ static int flux_launch(int blocks, int threads, int pblocks, cudaStream_t st, co
                        const double* aux, const double* fh, const unsigned long long* alpha, double* Fhat,
                        uint8_t* flags, uint32_t* list, unsigned* count, int* status, const Grid& G,
                        const Scheme& S) {
-  if (flags) {
-    flux_kernel<NDIM, DIR, true><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
-    return 1;
-  }
-  if (!list) {
-    flux_kernel<NDIM, DIR, false><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
+  const bool gh = G.bc[DIR] == TENO_BC_DIRICHLET;
+  if (flags || !list) {
+    if (flags && gh) flux_kernel<NDIM, DIR, true, true><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
+    else if (flags) flux_kernel<NDIM, DIR, true, false><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
+    else if (gh) flux_kernel<NDIM, DIR, false, true><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
+    else flux_kernel<NDIM, DIR, false, false><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
     return 1;
   }
   if (G.bc[DIR] == TENO_BC_REFLECTIVE)
-    flux_closed_kernel<NDIM, DIR, true><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
+    flux_closed_kernel<NDIM, DIR, 1><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
+  else if (gh)
+    flux_closed_kernel<NDIM, DIR, 2><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
   else
-    flux_closed_kernel<NDIM, DIR, false><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G,
-                                                                     S);
-  flux_pending_kernel<NDIM, DIR><<<pblocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
+    flux_closed_kernel<NDIM, DIR, 0><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
+  if (gh)
+    flux_pending_kernel<NDIM, DIR, true><<<pblocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
+  else
+    flux_pending_kernel<NDIM, DIR, false><<<pblocks, threads, 0, st>>>(U, aux, alpha, Fhat, list, count, status, G, S);
   return 2;
 }
 
@@ -565,39 +632,47 @@ cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, c
   return cudaGetLastError();
 }
 
+template <int NDIM, int DIR, bool GRAV>
+static void diff_launch_last(int blocks, int threads, cudaStream_t st, const double* Fhat, double* R,
+                             const double* Un, const double* Uk, double* Uout, const double* dt, const Grid& G,
+                             int mode, const double* Usrc) {
+  switch (mode) {
+    case 0: diff_kernel<NDIM, DIR, kDiffRhs, GRAV><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G, Usrc); break;
+    case 2: diff_kernel<NDIM, DIR, 2, GRAV><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G, Usrc); break;
+    case 3: diff_kernel<NDIM, DIR, 3, GRAV><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G, Usrc); break;
+    default: diff_kernel<NDIM, DIR, 4, GRAV><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G, Usrc); break;
+  }
+}
+
 template <int NDIM, int DIR>
 static void diff_launch(int blocks, int threads, cudaStream_t st, const double* Fhat,
                         double* R, const double* Un, const double* Uk, double* Uout,
-                        const double* dt, const Grid& G, int mode) {
+                        const double* dt, const Grid& G, int mode, const double* Usrc) {
   // the first of several directions starts R; a middle one adds to it
   if (DIR < NDIM - 1) {
-    if (DIR == 0) diff_kernel<NDIM, DIR, kDiffFirst><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G);
-    else diff_kernel<NDIM, DIR, kDiffAcc><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G);
+    if (DIR == 0) diff_kernel<NDIM, DIR, kDiffFirst><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G, Usrc);
+    else diff_kernel<NDIM, DIR, kDiffAcc><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G, Usrc);
     return;
   }
-  switch (mode) {
-    case 0: diff_kernel<NDIM, DIR, kDiffRhs><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
-    case 2: diff_kernel<NDIM, DIR, 2><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
-    case 3: diff_kernel<NDIM, DIR, 3><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
-    default: diff_kernel<NDIM, DIR, 4><<<blocks, threads, 0, st>>>(Fhat, R, Un, Uk, Uout, dt, G); break;
-  }
+  if (G.has_grav) diff_launch_last<NDIM, DIR, true>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
+  else diff_launch_last<NDIM, DIR, false>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
 }
 
 cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
                         const double* Un, const double* Uk, double* Uout,
                         const double* dt, const Grid& G, int mode,
-                        int nsm, cudaStream_t st) {
+                        int nsm, cudaStream_t st, const double* Usrc) {
   if (mode != 0 && (mode < 2 || mode > 4)) return cudaErrorInvalidValue;
   const int threads = 256;
   const int blocks = blocks_for(G.ncell, threads, nsm * 16);
-  if (ndim == 1) diff_launch<1, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
+  if (ndim == 1) diff_launch<1, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
   else if (ndim == 2) {
-    if (dir == 0) diff_launch<2, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
-    else diff_launch<2, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
+    if (dir == 0) diff_launch<2, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
+    else diff_launch<2, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
   } else {
-    if (dir == 0) diff_launch<3, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
-    else if (dir == 1) diff_launch<3, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
-    else diff_launch<3, 2>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode);
+    if (dir == 0) diff_launch<3, 0>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
+    else if (dir == 1) diff_launch<3, 1>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
+    else diff_launch<3, 2>(blocks, threads, st, Fhat, R, Un, Uk, Uout, dt, G, mode, Usrc);
   }
   return cudaGetLastError();
 }
@@ -646,7 +721,7 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
     if (launch_flux(g->ndim, d, U, aux, fh, alpha, Fhat, nullptr, list, count + d, status, G, S, nsm, st,
                     nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
-    if (launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt, G, mode, nsm, st) != cudaSuccess)
+    if (launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt, G, mode, nsm, st, U) != cudaSuccess)
       return TENO_ERR_CUDA;
   }
   return TENO_OK;

@@ -53,7 +53,8 @@ constexpr size_t kPendingCountOffset = 9 * sizeof(unsigned long long);
 constexpr size_t kAlphaAndCountBytes = kPendingCountOffset + 3 * sizeof(unsigned);
 
 // The difference of direction `dir` (called for dir = 0..ndim-1 in order,
-// each after that direction's fluxes are in Fhat).  R carries the unscaled
+// each after that direction's fluxes are in Fhat; Usrc = the state whose
+// right-hand side this is, for the body-force source when G.has_grav).  R carries the unscaled
 // partial sum between the calls (see diff_kernel).  mode 0: the last
 // direction writes L(U) into R; 2, 3, 4: the last direction writes the
 // SSP-RK3 stage (eq. 4.1-4.3) into Uout, with dt read from the device word
@@ -61,7 +62,19 @@ constexpr size_t kAlphaAndCountBytes = kPendingCountOffset + 3 * sizeof(unsigned
 cudaError_t launch_diff(int ndim, int dir, const double* Fhat, double* R,
                         const double* Un, const double* Uk, double* Uout,
                         const double* dt, const Grid& G, int mode,
-                        int nsm, cudaStream_t st);
+                        int nsm, cudaStream_t st, const double* Usrc);
+
+// The fixed-state (TENO_BC_DIRICHLET) ghost cells: the conservative states of
+// the six faces (slot 2 d + side, unused slots ignored per `mask` bit) into
+// the ghost block G.gU and their primitives and half fluxes into G.gaux,
+// G.gfh (the cell pass's formulas, kGhostSlots entries per field).
+struct GhostStates {
+  double U[6][5];
+};
+cudaError_t launch_ghost_cells(int ndim, const GhostStates& gs, unsigned mask, const Grid& G, double gamma,
+                               cudaStream_t st);
+// doubles of the ghost block for an ndim grid
+inline int ghost_block_doubles(int ndim) { return 6 * ((ndim + 2) + aux_fields(ndim) + ndim * (ndim + 1)); }
 
 cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
                       double cfl, double dt_fixed, double* t_dev, double t_end,

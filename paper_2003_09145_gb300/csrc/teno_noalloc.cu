@@ -71,6 +71,8 @@ bool grid_valid(const teno_grid* g) {
   if (!std::isfinite(g->gamma) || !std::isfinite(g->H) || !std::isfinite(g->eps)) return false;
   if (g->b_l < 0 || g->b_u > 15 || g->b_u <= g->b_l) return false;
   if (!teno::scheme_fields_ok(g)) return false;
+  for (int k = 0; k < g->ndim; ++k)
+    if (!std::isfinite(g->grav[k])) return false;
   return true;
 }
 
@@ -102,6 +104,10 @@ size_t scratch_needed(const teno_grid* g) {
 
 extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, double* dUdt,
                                         void* stream) {
+  // fixed-state faces need a ghost block this variant does not hold
+  if (g && g->ndim >= 1 && g->ndim <= 3)
+    for (int k = 0; k < g->ndim; ++k)
+      if (g->bc[k] == TENO_BC_DIRICHLET) return TENO_ERR_UNSUPPORTED;
   if (!grid_valid(g) || !U || !dUdt || U == dUdt) return TENO_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(U) % 16 || reinterpret_cast<uintptr_t>(dUdt) % 16)
     return TENO_ERR_INVALID_ARG;
@@ -129,6 +135,10 @@ extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, dou
     G.rdx[k] = G.dx[0] / G.dx[k];
   }
   G.ncell = int64_t(ncell);
+  for (int k = 0; k < g->ndim; ++k) {
+    G.grav[k] = g->grav[k];
+    if (g->grav[k] != 0.0) G.has_grav = 1;
+  }
   const teno::Scheme S = teno::scheme_of(g);
 
   int nsm = 0, dev = 0;
@@ -146,8 +156,8 @@ extern "C" teno_status teno_rhs_noalloc(const teno_grid* g, const double* U, dou
     if (teno::launch_flux(g->ndim, d, U, aux, nullptr, alpha, Fhat, nullptr, nullptr, nullptr, status, G, S, nsm, st,
                           nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
-    if (teno::launch_diff(g->ndim, d, Fhat, dUdt, nullptr, nullptr, nullptr, nullptr, G, 0, nsm,
-                          st) != cudaSuccess)
+    if (teno::launch_diff(g->ndim, d, Fhat, dUdt, nullptr, nullptr, nullptr, nullptr, G, 0, nsm, st,
+                          U) != cudaSuccess)
       return TENO_ERR_CUDA;
   }
   return TENO_OK;

@@ -206,6 +206,33 @@ def riemann_2d(n: int = 2048, split=(0.8, 0.8), states=QUADRANTS_LAX_LIU_3,
                    x0=(0.0, 0.0))
 
 
+def rayleigh_taylor(nx: int = 128, ny: int = 512, t_end: float = 1.95, perturb: bool = True) -> Problem:
+    """Sec. 4.3.2's Rayleigh-Taylor instability (eq. 4.12): [0, 0.25] x [0, 1],
+    gamma = 5/3, heavy fluid (rho 2, p = 2y + 1) below y = 1/2 and light fluid
+    (rho 1, p = y + 3/2) above, v = -0.025 c cos(8 pi x) with c = sqrt(gamma
+    p / rho) (perturb = False: at rest, a hydrostatic state); reflecting left
+    and right walls, fixed states (rho, u, v, p) = (2, 0, 0, 1) at the bottom
+    and (1, 0, 0, 2.5) at the top; the body force adds rho to the y momentum
+    and rho v to the energy (grav = (0, 1)).  extra: grav, bc_state (the
+    conservative ghost states, [axis][side])."""
+    gamma = 5.0 / 3.0
+    dx = (0.25 / nx, 1.0 / ny)
+    x = (np.arange(nx) + 0.5) * dx[0]
+    y = (np.arange(ny) + 0.5) * dx[1]
+    X, Y = np.meshgrid(x, y, indexing="xy")            # [ny][nx]
+    low = Y < 0.5
+    rho = np.where(low, 2.0, 1.0)
+    p = np.where(low, 2.0 * Y + 1.0, Y + 1.5)
+    c = np.sqrt(gamma * p / rho)
+    v = -0.025 * c * np.cos(8.0 * np.pi * X) if perturb else np.zeros_like(X)
+    U0 = prim_to_cons(rho, [np.zeros_like(X), v], p, gamma)
+    bottom = prim_to_cons(np.array(2.0), [np.array(0.0), np.array(0.0)], np.array(1.0), gamma)
+    top = prim_to_cons(np.array(1.0), [np.array(0.0), np.array(0.0)], np.array(2.5), gamma)
+    bc_state = [None, [bottom.reshape(-1).tolist(), top.reshape(-1).tolist()]]
+    return Problem("rayleigh_taylor", U0, (nx, ny), dx, (2, 3), t_end, 0.5, gamma, (0.0, 0.0),
+                   {"grav": (0.0, 1.0), "bc_state": bc_state})
+
+
 def riemann_2d_config3(n: int = 1024, t_end: float = 0.3) -> Problem:
     """Sec. 4.3.1's first case (eq. 4.14): the states of QUADRANTS_LAX_LIU_3 split
     at (0.5, 0.5), integrated to t = 0.3 on 1024^2 in the paper."""
