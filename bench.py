@@ -159,7 +159,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-FLUX_KERNEL_SOURCES = ("teno_device.cuh", "teno_flux.cuh", "teno_kernels.cu")
+FLUX_KERNEL_SOURCES = ("teno_cert.cuh", "teno_device.cuh", "teno_flux.cuh", "teno_kernels.cu")
 
 
 def _source_hash() -> str:

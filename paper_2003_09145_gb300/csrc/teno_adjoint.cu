@@ -457,15 +457,16 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
     double acc[NVAR], Fsum[NVAR];
     for (int v = 0; v < NVAR; ++v) acc[v] = Fsum[v] = 0.0;
     const int idl = int(id), ndl = int(nd);
-    // a cell whose six interfaces are all kept: the P-weighted Fbar sum as
-    // one stencil on Rbar.  Interior cells (slot j's interface qd = id+3-j)
-    // always qualify.  With periodic ends and at least six cells every cell
-    // does: qd and the Rbar stencil wrap modulo nd, and faces 0 and nd --
-    // one physical face computed twice, each copy with its own Fbar -- both
-    // add their terms to the slot whose wrapped interface is 0 (their Fbar
-    // sum is the wrapped difference the stencil already holds).
+    // the P-weighted Fbar sum over the six slots as one stencil on Rbar.
+    // Interior cells (slot j's interface qd = id+3-j) always take it; with
+    // periodic ends and at least six cells every cell does: qd and the Rbar
+    // stencil wrap modulo nd, and faces 0 and nd -- one physical face
+    // computed twice, each copy with its own Fbar -- both add their terms to
+    // the slot whose wrapped interface is 0 (their Fbar sum is the wrapped
+    // difference the stencil already holds).  Other cells (transmissive ends,
+    // short periodic lines) gather slot by slot.
     const bool wrap = bc == 0 && ndl >= 6;
-    bool fast = wrap || (idl >= 3 && idl <= ndl - 4);
+    const bool fast = wrap || (idl >= 3 && idl <= ndl - 4);
     // slot j's interface: id + 3 - j, in [1, nd-1] for an interior cell,
     // wrapped into [0, nd) otherwise (reached only when `wrap`)
     auto slot_face = [idl, ndl](int j) {
@@ -475,13 +476,9 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
       return x;
     };
     if (fast) {
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int x = slot_face(j);
-        fast = fast && pending[q0 + (int64_t)x * sd] == 0 && (x != 0 || pending[q0 + (int64_t)ndl * sd] == 0);
-      }
-    }
-    if (fast) {
+      // every slot's P_j Fbar term through the stencil; a pending slot then
+      // takes its term back out and adds its own contribution instead (the
+      // branch is short, so the rare pending slots cost the warp little)
       const int toff[6] = {-3, -2, -1, 1, 2, 3};
       for (int v = 0; v < NVAR; ++v) {
         const double* r = Rbar + v * ncell + line;
@@ -500,7 +497,18 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
         const int x = slot_face(j);
         for (int copy = 0; copy < 2; ++copy) {
           if (copy == 1 && x != 0) break;
-          const int64_t q = q0 + (int64_t)(copy == 0 ? x : ndl) * sd;
+          const int qd = copy == 0 ? x : ndl;
+          const int64_t q = q0 + (int64_t)qd * sd;
+          if (pending[q]) {
+            const double Pj = c_adjP[j];
+            for (int v = 0; v < NVAR; ++v) {
+              const double ra = (qd < ndl) ? Rbar[v * ncell + line + (int64_t)qd * cstride] : 0.0;
+              const double rb = (qd >= 1) ? Rbar[v * ncell + line + (int64_t)(qd - 1) * cstride] : 0.0;
+              Fsum[v] = fma(-Pj, ra - rb, Fsum[v]);
+              acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
+            }
+            continue;
+          }
           for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
           if (j == 2)
             for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(NVAR + v) * nifc + q];

@@ -32,8 +32,22 @@ def row(config, quantity, value, bound, note=""):
     print(f"| {config} | {quantity} | {value} | {bound} | {note} |", flush=True)
 
 
-def rhs_pair(P, scheme=None):
-    grid = api.EulerGrid(P.n, P.dx, P.bc, scheme or api.Scheme(gamma=P.gamma))
+def _oracle_extra(kw):
+    out = {}
+    if kw.get("grav") is not None:
+        out["grav"] = tuple(kw["grav"]) + (0.0,) * (3 - len(kw["grav"]))
+    if kw.get("bc_state") is not None:
+        st = np.zeros((3, 2, 5))
+        for k, faces in enumerate(kw["bc_state"]):
+            if faces is not None:
+                for side in range(2):
+                    st[k, side, :len(faces[side])] = faces[side]
+        out["bc_state"] = st
+    return out
+
+
+def rhs_pair(P, scheme=None, kw=None):
+    grid = api.EulerGrid(P.n, P.dx, P.bc, scheme or api.Scheme(gamma=P.gamma), **(kw or {}))
     U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
     a, fl = api.rhs(grid, U, want_flags=True)
     b = api.rhs(grid, U, want_flags=False)
@@ -41,9 +55,10 @@ def rhs_pair(P, scheme=None):
     return a.cpu().numpy(), fl.cpu().numpy(), b.cpu().numpy()
 
 
-def rhs_rows(name, P):
-    a, fl, b = rhs_pair(P)
-    params = oracle.Params(gamma=P.gamma)
+def rhs_rows(name, P, scheme="lad", extra=None):
+    kw = dict(extra or {})
+    a, fl, b = rhs_pair(P, api.Scheme(gamma=P.gamma, scheme=scheme), kw)
+    params = oracle.Params(gamma=P.gamma, scheme=scheme, **_oracle_extra(kw))
     err_a, rep = compare_rhs(P.U0, P.n, P.dx, P.bc, a, fl, oracle, params)
     err_b, _ = compare_rhs(P.U0, P.n, P.dx, P.bc, b, fl, oracle, params)
     fs = flux_scale(P.U0, P.n, P.dx, P.gamma)
@@ -54,15 +69,16 @@ def rhs_rows(name, P):
         "counted", f"allowed delta {rep.allowed_delta}, m {rep.allowed_m}, unexplained {len(rep.unexplained)}")
 
 
-def steps_row(name, P, steps):
-    grid = api.EulerGrid(P.n, P.dx, P.bc, api.Scheme(gamma=P.gamma))
+def steps_row(name, P, steps, extra=None):
+    kw = dict(extra or {})
+    grid = api.EulerGrid(P.n, P.dx, P.bc, api.Scheme(gamma=P.gamma), **kw)
     solver = api.Solver(grid, cfl=P.cfl)
     U = torch.from_numpy(np.ascontiguousarray(P.U0)).cuda()
     for _ in range(steps):
         solver.step(U, P.t_end)
     Ug = U.cpu().numpy()
     Uo, t, k = oracle.euler_run(np.array(P.U0), P.n, P.dx, P.bc, P.t_end, sigma=P.cfl, max_steps=steps,
-                                params=oracle.Params(gamma=P.gamma))
+                                params=oracle.Params(gamma=P.gamma, **_oracle_extra(kw)))
     row(name, f"{k} RK3 steps (t = {t:.4g}): rel. L1", f"{rel_l1_err(Ug, Uo):.2e}", "1e-10",
         f"t GPU - t oracle = {solver.t.item() - t:.1e}")
 
@@ -76,7 +92,13 @@ def main():
     rhs_rows("2 Shu-Osher, N=4096", inputs.shu_osher(4096))
     steps_row("2 Shu-Osher, N=4096", inputs.shu_osher(4096), 100)
     rhs_rows("3 four-quadrant, 2048^2", inputs.riemann_2d(n=2048))
-    steps_row("3 four-quadrant, 128^2", inputs.riemann_2d(n=128, t_end=10.0), 20)
+    steps_row("3 four-quadrant, 2048^2", inputs.riemann_2d(n=2048, t_end=10.0), 20)
+    for sch in ("teno5", "teno5a", "wenoz"):
+        rhs_rows(f"3 four-quadrant, 2048^2, {sch}", inputs.riemann_2d(n=2048), scheme=sch)
+    R = inputs.rayleigh_taylor(128, 512)
+    rt = {"grav": R.extra["grav"], "bc_state": R.extra["bc_state"]}
+    rhs_rows("Rayleigh-Taylor 128x512 (Sec. 4.3.2)", R, extra=rt)
+    steps_row("Rayleigh-Taylor 128x512 (Sec. 4.3.2)", R, 20, extra=rt)
 
     # 4: batched tubes against the oracle, and bit for bit against single problems
     B = inputs.tube_batch(nprob=4096, seed=20200320)
@@ -105,7 +127,7 @@ def main():
 
     # 5: 3D turbulence
     rhs_rows("5 turbulence, 256^3", inputs.solenoidal_turbulence(n=256))
-    steps_row("5 turbulence, 24^3", inputs.solenoidal_turbulence(n=24, t_end=10.0), 6)
+    steps_row("5 turbulence, 256^3", inputs.solenoidal_turbulence(n=256, t_end=10.0), 2)
     P = inputs.solenoidal_turbulence(n=16)
     dt = oracle.euler_dt(P.U0, P.n, P.dx, 0.5)
     grid = api.EulerGrid(P.n, P.dx, P.bc)
