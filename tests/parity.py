@@ -130,11 +130,11 @@ def rel_l1_err(a: np.ndarray, b: np.ndarray) -> float:
     return worst
 
 
-def compare_rhs(U, n, dx, bc, gpu_rhs, gpu_flags, oracle, params=None):
+def compare_rhs(U, n, dx, bc, gpu_rhs, gpu_flags, oracle, params=None, max_examined=2000):
     """Full-grid comparison.  Returns (relative max error vs the forced-flag
     oracle, FlagReport)."""
     R_or, fl_or = oracle.euler_rhs(U, n, dx, bc, params, want_flags=True)
-    rep = classify_flags(U, n, dx, bc, gpu_flags, fl_or, oracle, params)
+    rep = classify_flags(U, n, dx, bc, gpu_flags, fl_or, oracle, params, max_examined)
     if rep.mismatched:
         R_ref = oracle.euler_rhs(U, n, dx, bc, params, flags_in=gpu_flags)
     else:
