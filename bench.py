@@ -362,6 +362,68 @@ def bench_schemes(api, lib, device, steps: int, workloads) -> dict:
     return out
 
 
+# The paper's Tab. 2: average wall time of one time step (s) on its CPU
+# workstation, per scheme (WENO-Z, TENO5, TENO5-A, TENO5-LAD).
+PAPER_TAB2_S = {
+    "rt128x512": {"wenoz": 0.14, "teno5": 0.15, "teno5a": 0.20, "lad": 0.16},
+    "rt256x1024": {"wenoz": 0.59, "teno5": 0.67, "teno5a": 0.88, "lad": 0.70},
+    "cfg3_1024": {"wenoz": 2.57, "teno5": 2.89, "teno5a": 3.71, "lad": 2.99},
+    "cfg12_1024": {"wenoz": 2.56, "teno5": 2.85, "teno5a": 3.68, "lad": 2.99},
+    "cfg12_2048": {"wenoz": 11.9, "teno5": 13.1, "teno5a": 17.8, "lad": 13.7},
+}
+
+
+def bench_tab2(api, device, max_steps_2048: int = 300) -> dict:
+    """The paper's Tab. 2 workloads on this GPU: the Rayleigh-Taylor problem
+    (Sec. 4.3.2) at 128x512 and 256x1024 to t = 1.95, the 2D Riemann
+    configurations 3 (to t = 0.3) and 12 (to t = 0.25) at 1024^2, and
+    configuration 12 at 2048^2 for its first `max_steps_2048` steps; each
+    under the four schemes, ms per step averaged over the run (event-timed)
+    beside the paper's seconds per step."""
+    import torch
+    from paper_2003_09145_gb300 import inputs
+    cases = [("rt128x512", lambda: inputs.rayleigh_taylor(128, 512), None),
+             ("rt256x1024", lambda: inputs.rayleigh_taylor(256, 1024), None),
+             ("cfg3_1024", lambda: inputs.riemann_2d_config3(1024), None),
+             ("cfg12_1024", lambda: inputs.riemann_2d_config12(1024), None),
+             ("cfg12_2048", lambda: inputs.riemann_2d_config12(2048), max_steps_2048)]
+    out = {}
+    for name, make, cap in cases:
+        P = make()
+        row = {}
+        for sch in ("lad", "teno5", "teno5a", "wenoz"):
+            grid = api.EulerGrid(P.n, P.dx, P.bc, api.Scheme(gamma=P.gamma, scheme=sch), grav=P.extra.get("grav"),
+                                 bc_state=P.extra.get("bc_state"))
+            solver = api.Solver(grid, device=device, cfl=P.cfl)
+            U = torch.from_numpy(P.U0).to(device)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0 = time.perf_counter()
+            e0.record()
+            k, limit, bad = 0, cap or 200000, None
+            # in chunks, with a wall-clock budget per run (a run whose steps
+            # shrink towards zero must not hold the GPU); a non-physical
+            # state (the status word) ends the run
+            while k < limit and float(solver.t.item()) < P.t_end and time.perf_counter() - w0 < 120.0:
+                k += solver.run(U, P.t_end, max_steps=min(500, limit - k))
+                if solver.status() != 0:
+                    bad = {"by_step": k, "t": float(solver.t.item())}
+                    break
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            print(f"tab2 {name} {sch}: {k} steps to t = {float(solver.t.item()):.4f}, {ms:.3f} ms/step",
+                  file=sys.stderr, flush=True)
+            row[sch] = {"steps": k, "t": float(solver.t.item()), "ms_per_step": ms,
+                        "complete": bool(cap is not None or float(solver.t.item()) >= P.t_end),
+                        "nonphysical": bad,
+                        "paper_s_per_step": PAPER_TAB2_S[name][sch],
+                        "speedup_vs_paper": PAPER_TAB2_S[name][sch] / (ms * 1e-3)}
+            del solver, U
+        out[name] = row
+    return out
+
+
 def fp64_probe(api, device) -> float:
     """Measured FP64 FMA throughput (flop/s) of this GPU."""
     import torch
@@ -454,7 +516,7 @@ def main() -> None:
     ap.add_argument("--n", type=int, default=N_CELLS_1D, help="cells per axis (default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint / 2D / scheme forms")
-    ap.add_argument("--form", choices=["riemann2d", "adjoint"], default=None,
+    ap.add_argument("--form", choices=["riemann2d", "adjoint", "tab2"], default=None,
                     help="run only this form and print its record (profiling aid)")
     ap.add_argument("--warm-steps", type=int, default=400, help="untimed steps before the riemann2d form")
     args = ap.parse_args()
@@ -481,6 +543,9 @@ def main() -> None:
 
     if args.form == "riemann2d":
         print(json.dumps(bench_riemann2d(api, lib, device, args.steps, args.warm_steps, peak)), flush=True)
+        return
+    if args.form == "tab2":
+        print(json.dumps(bench_tab2(api, device)), flush=True)
         return
     if args.form == "adjoint":
         P = inputs.solenoidal_turbulence(n=args.n)

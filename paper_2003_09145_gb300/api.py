@@ -182,13 +182,20 @@ class Solver:
         of t (steps after t_end are no-ops)."""
         k = 0
         chunk = chunk or 64
+        t_prev = float(self.t.item())
         while k < max_steps:
             n = min(chunk, max_steps - k)
             for _ in range(n):
                 self.step(U, t_end, dt_fixed)
             k += n
-            if float(self.t.item()) >= t_end:
+            t_now = float(self.t.item())
+            if t_now >= t_end:
                 break
+            if not t_now > t_prev:
+                # no step advanced the time (dt = 0: a non-physical state,
+                # which the status word reports): stop instead of spinning
+                break
+            t_prev = t_now
         return k
 
     def status(self) -> int:
