@@ -5,23 +5,32 @@
 // eq. 2.14 is piecewise constant, so with delta fixed the reconstruction is
 // linear and L(U) is differentiable almost everywhere.  The global
 // Lax-Friedrichs speed alpha_{d,s} = max_cells |lambda_s| is differentiated
-// through its arg-max cell (lowest linear index on ties).
+// through its arg-max cell (lowest linear index on ties), which the cell
+// pass finds along with the maximum.
 //
-// teno_rhs_adjoint, per direction d:
-//   adj_kept_kernel  : one thread per interface: the forward pass's certified
-//                      FP32 test; where it keeps every stencil, the closed-form
-//                      interface VJP (teno_adjoint_core.cuh) with Fbar from
-//                      Rbar (eq. 2.2); the rest is marked pending;
-//   adj_general_kernel: the pending interfaces, compacted per warp: the
-//                      selections by the forward pass's binary64 decisions,
-//                      then the general VJP.  Both write the six cells'
-//                      contributions to a buffer and sum d/dalpha per block
-//                      (fixed order);
-//   adj_gather_kernel: one thread per cell sums the contributions of every
-//                      (interface, stencil slot) that maps to it (boundary
-//                      ghost copies included) -- deterministic, no atomics;
-//   adj_alpha_kernel : sums the block partials in a fixed order and adds the
-//                      alpha terms at the arg-max cells.
+// One right-hand-side adjoint (adjoint_sequence):
+//   cell pass        : primitives, speeds and their arg-max cells (skipped
+//                      where the recomputed forward stage already made them);
+//   per direction d:
+//     adj_kept_kernel  : one thread per interface: the forward pass's certified
+//                        FP32 test; where it keeps every stencil, the
+//                        closed-form interface VJP (teno_adjoint_core.cuh)
+//                        with Fbar from Rbar (eq. 2.2): U~bar and the adjoints
+//                        of the two Roe cells' parameters go to kb_d; the
+//                        rest is marked pending;
+//     list passes      : the pending interfaces in one list, index order;
+//     adj_general_kernel: the listed interfaces: the selections by the forward
+//                        pass's binary64 decisions, then the general VJP; the
+//                        six cells' contributions go to contrib_d;
+//   adj_gather_kernel: one thread per cell sums, over every direction, the
+//                      contributions of every (interface, stencil slot) that
+//                      maps to it (boundary ghost copies included) and applies
+//                      the per-cell maps once: A_d(U_c)^T to the P-weighted
+//                      Fbar of each direction, the Roe-parameter map to the
+//                      summed parameter adjoints -- deterministic, no atomics;
+//                      it writes out = a X + b Y + (the adjoint);
+//   adj_alpha_kernel : sums the per-block d/dalpha in a fixed order and adds
+//                      the alpha terms at the arg-max cells.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -40,26 +49,6 @@ using teno::Grid;
 using teno::Scheme;
 
 constexpr int kAdjThreads = 128;
-
-// Lowest linear cell index at which |lambda_kind| (direction d) equals the
-// reduced maximum alpha (same rounding as the forward cell pass).
-template <int NDIM>
-__global__ void argmax_kernel(const double* __restrict__ U, const unsigned long long* __restrict__ alpha,
-                              unsigned long long* __restrict__ argidx, int64_t ncell, double gamma,
-                              double* __restrict__ scratch_aux) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    double uh[NDIM], cs, ep;
-    teno::cell_primitives<NDIM>(U, ncell, c, gamma, scratch_aux, uh, cs, ep);
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-      const double lam[3] = {fabs(fma(2.0, uh[d], -cs)), fabs(2.0 * uh[d]), fabs(fma(2.0, uh[d], cs))};
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (teno::dbits(lam[k]) == alpha[d * 3 + k]) atomicMin(&argidx[d * 3 + k], (unsigned long long)c);
-    }
-  }
-}
 
 // Geometry of interface q of direction DIR: its index id along DIR, the
 // linear index of its line's cell 0 and the six stencil cells (ghosts mapped).
@@ -144,9 +133,9 @@ __device__ __forceinline__ void add_alpha(const double (&ab)[NVAR], double (&asu
 // One thread per interface: the forward pass's certified FP32 test (the
 // same device code teno_rhs / teno_rk3_step run).  Where it keeps every
 // stencil, the interface part of the closed-form VJP: U~bar and the
-// Roe-parameter terms of cells i and i+1 go to kb[15][nifc] (the flux
-// Jacobians are applied per cell by the gather); elsewhere the interface is
-// marked pending for adj_general_kernel.
+// adjoints of the Roe parameters of cells i and i+1 go to kb[3 nvar][nifc]
+// (the flux Jacobians and the Roe-parameter maps are applied per cell by the
+// gather); elsewhere the interface is marked pending for adj_general_kernel.
 #ifndef TENO_ADJ_KEPT_MINBLOCKS
 #define TENO_ADJ_KEPT_MINBLOCKS 3   // 168 registers: 12 warps per SM
 #endif
@@ -214,13 +203,13 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     if (!kept) continue;
     double Fb[NVAR];
     interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
-    double Utb[NVAR], roeA[NVAR], roeB[NVAR], ab[NVAR];
-    teno_adj::interface_vjp_kept_ifc<NDIM, DIR>(R, Ut, fa, S.gamma, Fb, Utb, roeA, roeB, ab);
+    double Utb[NVAR], pa[NVAR], pb[NVAR], ab[NVAR];
+    teno_adj::interface_vjp_kept_roe<NDIM, DIR>(R, Ut, fa, S.gamma, Fb, Utb, pa, pb, ab);
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) {
       kb[(int64_t)v * I.nifc + q] = Utb[v];
-      kb[(int64_t)(NVAR + v) * I.nifc + q] = roeA[v];
-      kb[(int64_t)(2 * NVAR + v) * I.nifc + q] = roeB[v];
+      kb[(int64_t)(NVAR + v) * I.nifc + q] = pa[v];
+      kb[(int64_t)(2 * NVAR + v) * I.nifc + q] = pb[v];
     }
     add_alpha<NVAR>(ab, asum);
   }
@@ -385,27 +374,37 @@ __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
 // for U~ = sum_j M_j U_j (indexed by a warp-uniform slot number).
 __constant__ double c_adjP[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
 __constant__ double c_adjM[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
-// sum_j P_j (Rbar_{id+3-j} - Rbar_{id+2-j}) as one stencil on Rbar: the
-// weights of Rbar_{id+t} for t = -3, -2, -1, 1, 2, 3 (t = 0 cancels)
-__constant__ double c_adjW[6] = {-1.0 / 60.0, 9.0 / 60.0, -45.0 / 60.0, 45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0};
+
+// What the gather reads per direction, and its output.
+struct GatherArgs {
+  const double* kb[3];              // [3 nvar][nifc_d]: U~bar, Roe-parameter adjoints of cells i, i+1
+  const double* contrib[3];         // [6 nvar][nifc_d]: the pending interfaces' contributions
+  const unsigned char* pending[3];  // [nifc_d]
+  double fscale[3];                 // scale / dx_d
+  double* out;                      // out = a X + b Y + the adjoint (X, Y nullable; out may be X or Y)
+  const double* X;
+  const double* Y;
+  double a, b;
+};
 
 // The share of interface q's slot j at the cell that slot maps to: the
-// pending interface's own contribution, or for a kept one M_j U~bar_q (plus
-// the Roe terms at j = 2, 3) into acc and P_j Fbar_q into Fsum.
+// pending interface's own contribution, or for a kept one M_j U~bar_q into
+// acc, its Roe-parameter adjoints (j = 2: cell i, j = 3: cell i+1) into rp
+// and fs P_j Fbar_q into Fsum.
 template <int NVAR>
 __device__ __forceinline__ void gather_slot(int j, int64_t q, int64_t qd, const double* __restrict__ contrib,
                                             const double* __restrict__ kb,
                                             const unsigned char* __restrict__ pending,
                                             const double* __restrict__ Rbar, int64_t nifc, int64_t ncell,
-                                            int64_t line, int64_t nd, int64_t cstride,
-                                            double (&acc)[NVAR], double (&Fsum)[NVAR]) {
-  const double Pj = c_adjP[j], Mj = c_adjM[j];
+                                            int64_t line, int64_t nd, int64_t cstride, double fs,
+                                            double (&acc)[NVAR], double (&rp)[NVAR], double (&Fsum)[NVAR]) {
   if (pending[q]) {
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
     return;
   }
-  // P_j (Rbar_qd [qd < n] - Rbar_{qd-1} [qd >= 1]); the 1/dx follows per cell
+  const double Pj = c_adjP[j] * fs, Mj = c_adjM[j];
+  // P_j (Rbar_qd [qd < n] - Rbar_{qd-1} [qd >= 1]) fs
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) {
     const double ra = (qd < nd) ? Rbar[v * ncell + line + qd * cstride] : 0.0;
@@ -415,27 +414,25 @@ __device__ __forceinline__ void gather_slot(int j, int64_t q, int64_t qd, const 
   }
   if (j == 2)
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(NVAR + v) * nifc + q];
+    for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(NVAR + v) * nifc + q];
   if (j == 3)
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+    for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
 }
 
-// Ubar_c += sum over (interface, slot j) whose stencil point maps to cell c
-// (boundary ghost copies included): the pending interfaces' contributions,
-// M_j U~bar and the Roe terms of the kept ones, and A(U_c)^T applied once to
-// sum_j P_j Fbar of the kept ones.  Deterministic, no atomics.
-#ifndef TENO_ADJ_GATHER_MINBLOCKS
-#define TENO_ADJ_GATHER_MINBLOCKS 3   // 80 registers: measured fastest of 1-3
-#endif
+// Direction DIR's share at cell c (indices i0, i1, i2): acc += the M-weighted
+// U~bar and the pending contributions, rp += the Roe-parameter adjoints,
+// and acc += A_DIR(U_c)^T applied to the fs P-weighted Fbar sum.
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_kernel(const double* __restrict__ U,
-                                                         const double* __restrict__ Rbar, double scale,
-                                                         const double* __restrict__ kb,
-                                                         const double* __restrict__ contrib,
-                                                         const unsigned char* __restrict__ pending,
-                                                         double* __restrict__ Ubar, Grid G, double gamma) {
+__device__ __forceinline__ void gather_dir(const Grid& G, int64_t c, int64_t i0, int64_t i1, int64_t i2,
+                                           const double* __restrict__ Rbar, const GatherArgs& A,
+                                           const double (&Uc)[NDIM + 2], const teno_adj::CellPrim<NDIM>& P,
+                                           double gamma, double (&acc)[NDIM + 2], double (&rp)[NDIM + 2]) {
   constexpr int NVAR = NDIM + 2;
+  const double* __restrict__ kb = A.kb[DIR];
+  const double* __restrict__ contrib = A.contrib[DIR];
+  const unsigned char* __restrict__ pending = A.pending[DIR];
+  const double fs = A.fscale[DIR];
   const int64_t ncell = G.ncell;
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
   const int64_t nifc = m0 * m1 * (G.n[2] + (DIR == 2));
@@ -443,81 +440,72 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
   const int64_t cstride = (DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1]);
   const int64_t nd = G.n[DIR];
   const int bc = G.bc[DIR];
-  const double fscale = scale * G.inv_dx[DIR];
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i0 = c % G.n[0];
-    const int64_t r = c / G.n[0];
-    const int64_t i1 = r % G.n[1];
-    const int64_t i2 = r / G.n[1];
-    const int64_t id = (DIR == 0) ? i0 : (DIR == 1 ? i1 : i2);
-    // interface-grid index of this line's interface 0, and the line's cell 0
-    const int64_t q0 = (i2 * m1 + i1) * m0 + i0 - id * sd;
-    const int64_t line = c - id * cstride;
-    double acc[NVAR], Fsum[NVAR];
-    for (int v = 0; v < NVAR; ++v) acc[v] = Fsum[v] = 0.0;
-    const int idl = int(id), ndl = int(nd);
-    // the P-weighted Fbar sum over the six slots as one stencil on Rbar.
-    // Interior cells (slot j's interface qd = id+3-j) always take it; with
-    // periodic ends and at least six cells every cell does: qd and the Rbar
-    // stencil wrap modulo nd, and faces 0 and nd -- one physical face
-    // computed twice, each copy with its own Fbar -- both add their terms to
-    // the slot whose wrapped interface is 0 (their Fbar sum is the wrapped
-    // difference the stencil already holds).  Other cells (transmissive ends,
-    // short periodic lines) gather slot by slot.
-    const bool wrap = bc == 0 && ndl >= 6;
-    const bool fast = wrap || (idl >= 3 && idl <= ndl - 4);
-    // slot j's interface: id + 3 - j, in [1, nd-1] for an interior cell,
-    // wrapped into [0, nd) otherwise (reached only when `wrap`)
-    auto slot_face = [idl, ndl](int j) {
-      int x = idl + 3 - j;
-      if (x < 0) x += ndl;
-      else if (x >= ndl) x -= ndl;
-      return x;
-    };
-    if (fast) {
-      // every slot's P_j Fbar term through the stencil; a pending slot then
-      // takes its term back out and adds its own contribution instead (the
-      // branch is short, so the rare pending slots cost the warp little)
-      const int toff[6] = {-3, -2, -1, 1, 2, 3};
-      for (int v = 0; v < NVAR; ++v) {
-        const double* r = Rbar + v * ncell + line;
-        double f = 0.0;
+  const int64_t id = (DIR == 0) ? i0 : (DIR == 1 ? i1 : i2);
+  // interface-grid index of this line's interface 0, and the line's cell 0
+  const int64_t q0 = (i2 * m1 + i1) * m0 + i0 - id * sd;
+  const int64_t line = c - id * cstride;
+  double Fsum[NVAR];
 #pragma unroll
-        for (int t = 0; t < 6; ++t) {
-          int y = idl + toff[t];
-          if (y < 0) y += ndl;
-          else if (y >= ndl) y -= ndl;
-          f = fma(c_adjW[t], r[(int64_t)y * cstride], f);
-        }
-        Fsum[v] = f;
-      }
-      for (int j = 0; j < 6; ++j) {
-        const double Mj = c_adjM[j];
-        const int x = slot_face(j);
-        for (int copy = 0; copy < 2; ++copy) {
-          if (copy == 1 && x != 0) break;
-          const int qd = copy == 0 ? x : ndl;
-          const int64_t q = q0 + (int64_t)qd * sd;
-          if (pending[q]) {
-            const double Pj = c_adjP[j];
-            for (int v = 0; v < NVAR; ++v) {
-              const double ra = (qd < ndl) ? Rbar[v * ncell + line + (int64_t)qd * cstride] : 0.0;
-              const double rb = (qd >= 1) ? Rbar[v * ncell + line + (int64_t)(qd - 1) * cstride] : 0.0;
-              Fsum[v] = fma(-Pj, ra - rb, Fsum[v]);
-              acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
-            }
-            continue;
+  for (int v = 0; v < NVAR; ++v) Fsum[v] = 0.0;
+  const int idl = int(id), ndl = int(nd);
+  // The P-weighted Fbar sum over the six slots as one stencil on Rbar:
+  // sum_j P_j (Rbar_{id+3-j} - Rbar_{id+2-j}) =
+  //   ((Rbar_{id+3} - Rbar_{id-3}) - 9 (Rbar_{id+2} - Rbar_{id-2}) + 45 (Rbar_{id+1} - Rbar_{id-1})) / 60.
+  // Interior cells (slot j's interface qd = id+3-j) always take it; with
+  // periodic ends and at least six cells every cell does: qd and the Rbar
+  // stencil wrap modulo nd, and faces 0 and nd -- one physical face
+  // computed twice, each copy with its own Fbar -- both add their terms to
+  // the slot whose wrapped interface is 0 (their Fbar sum is the wrapped
+  // difference the stencil already holds).  Other cells (transmissive ends,
+  // short periodic lines) gather slot by slot.
+  const bool wrap = bc == 0 && ndl >= 6;
+  const bool fast = wrap || (idl >= 3 && idl <= ndl - 4);
+  if (fast) {
+    auto wrapped = [ndl](int y) { return y < 0 ? y + ndl : (y >= ndl ? y - ndl : y); };
+    const int64_t o1p = wrapped(idl + 1) * cstride, o1m = wrapped(idl - 1) * cstride;
+    const int64_t o2p = wrapped(idl + 2) * cstride, o2m = wrapped(idl - 2) * cstride;
+    const int64_t o3p = wrapped(idl + 3) * cstride, o3m = wrapped(idl - 3) * cstride;
+    const double w1 = fs * (1.0 / 60.0), w9 = fs * (-9.0 / 60.0), w45 = fs * (45.0 / 60.0);
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) {
+      const double* r = Rbar + v * ncell + line;
+      Fsum[v] = fma(w45, r[o1p] - r[o1m], fma(w9, r[o2p] - r[o2m], w1 * (r[o3p] - r[o3m])));
+    }
+    // every kept slot adds M_j U~bar (and at j = 2, 3 its Roe-parameter
+    // adjoints); a pending slot takes its P_j Fbar term back out of the
+    // stencil and adds its own contribution instead (a short branch: the
+    // rare pending slots cost the warp little)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const double Mj = c_adjM[j];
+      const int x = wrapped(idl + 3 - j);
+      for (int copy = 0; copy < 2; ++copy) {
+        if (copy == 1 && x != 0) break;
+        const int qd = copy == 0 ? x : ndl;
+        const int64_t q = q0 + (int64_t)qd * sd;
+        if (pending[q]) {
+          const double Pj = c_adjP[j] * fs;
+#pragma unroll
+          for (int v = 0; v < NVAR; ++v) {
+            const double ra = (qd < ndl) ? Rbar[v * ncell + line + (int64_t)qd * cstride] : 0.0;
+            const double rb = (qd >= 1) ? Rbar[v * ncell + line + (int64_t)(qd - 1) * cstride] : 0.0;
+            Fsum[v] = fma(-Pj, ra - rb, Fsum[v]);
+            acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
           }
-          for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
-          if (j == 2)
-            for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(NVAR + v) * nifc + q];
-          if (j == 3)
-            for (int v = 0; v < NVAR; ++v) acc[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+          continue;
         }
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
+        if (j == 2)
+#pragma unroll
+          for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(NVAR + v) * nifc + q];
+        if (j == 3)
+#pragma unroll
+          for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
       }
     }
-    for (int j = 0; j < 6 && !fast; ++j) {
+  } else {
+    for (int j = 0; j < 6; ++j) {
       // interfaces qd in [0, nd] whose point j, ghost(qd - 3 + j), is cell id
       if (bc == 0) {
         // x = qd - 3 + j ranges over [j - 3, nd + j - 3]; x = id (mod nd)
@@ -526,8 +514,8 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
         while (x < j - 3) x += ndl;
         for (; x <= ndl + j - 3; x += ndl) {
           const int qd = x + 3 - j;
-          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride,
-                            acc, Fsum);
+          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride, fs,
+                            acc, rp, Fsum);
         }
       } else {
         // transmissive: points below 0 map to cell 0, points above nd-1 to nd-1
@@ -540,55 +528,113 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
           const int x = qd - 3 + j;
           const int mapped = x < 0 ? 0 : (x >= ndl ? ndl - 1 : x);
           if (mapped != idl) continue;
-          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride,
-                            acc, Fsum);
+          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride, fs,
+                            acc, rp, Fsum);
         }
       }
     }
-    double Uc[NVAR], AF[NVAR];
-    for (int v = 0; v < NVAR; ++v) {
-      Uc[v] = U[v * ncell + c];
-      Fsum[v] *= fscale;
-    }
-    teno_adj::flux_vjp<NDIM, DIR>(Uc, gamma, Fsum, AF);
-    for (int v = 0; v < NVAR; ++v) Ubar[v * ncell + c] += acc[v] + AF[v];
+  }
+  teno_adj::flux_vjp_acc<NDIM, DIR>(Uc, P, gamma, Fsum, acc);
+}
+
+template <int NDIM, int DIR>
+__device__ __forceinline__ void gather_dirs(const Grid& G, int64_t c, int64_t i0, int64_t i1, int64_t i2,
+                                            const double* __restrict__ Rbar, const GatherArgs& A,
+                                            const double (&Uc)[NDIM + 2], const teno_adj::CellPrim<NDIM>& P,
+                                            double gamma, double (&acc)[NDIM + 2], double (&rp)[NDIM + 2]) {
+  if constexpr (DIR < NDIM) {
+    gather_dir<NDIM, DIR>(G, c, i0, i1, i2, Rbar, A, Uc, P, gamma, acc, rp);
+    gather_dirs<NDIM, DIR + 1>(G, c, i0, i1, i2, Rbar, A, Uc, P, gamma, acc, rp);
   }
 }
 
-// Sum the per-block d/dalpha in a fixed order (one block of kAlphaThreads:
-// strided partial sums, then a tree) and add its effect at the arg-max cells
-// (one thread: the three kinds may share a cell).
+// out_c = a X_c + b Y_c + sum over directions and over the (interface, slot)
+// pairs whose stencil point maps to cell c (boundary ghost copies included)
+// of: the pending interfaces' contributions, M_j U~bar of the kept ones,
+// A_d(U_c)^T applied once per direction to sum_j P_j Fbar of the kept ones,
+// and the Roe-parameter map of cell c applied once to the sum of its
+// parameter adjoints.  Deterministic, no atomics.
+#ifndef TENO_ADJ_GATHER_MINBLOCKS
+#define TENO_ADJ_GATHER_MINBLOCKS 2
+#endif
+template <int NDIM>
+__global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_kernel(
+    const double* __restrict__ U, const double* __restrict__ aux, const double* __restrict__ Rbar,
+    const GatherArgs A, const Grid G, double gamma) {
+  constexpr int NVAR = NDIM + 2;
+  const int64_t ncell = G.ncell;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = c % G.n[0];
+    const int64_t r = c / G.n[0];
+    const int64_t i1 = r % G.n[1];
+    const int64_t i2 = r / G.n[1];
+    double Uc[NVAR], acc[NVAR], rp[NVAR];
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) {
+      Uc[v] = U[v * ncell + c];
+      acc[v] = rp[v] = 0.0;
+    }
+    teno_adj::CellPrim<NDIM> P;
+    teno_adj::cell_prim<NDIM>(Uc, gamma, P);
+    gather_dirs<NDIM, 0>(G, c, i0, i1, i2, Rbar, A, Uc, P, gamma, acc, rp);
+    // the Roe-parameter map of cell c: sqrt(rho) from the cell pass,
+    // H = (E + p) / rho
+    const double sx = aux[(NDIM + 1) * ncell + c];
+    const double Hx = (Uc[NVAR - 1] + P.p) * P.ir;
+    teno_adj::roe_param_vjp_acc<NDIM>(P, sx, Hx, gamma, rp, acc);
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) {
+      double o = acc[v];
+      if (A.X) o = fma(A.a, A.X[v * ncell + c], o);
+      if (A.Y) o = fma(A.b, A.Y[v * ncell + c], o);
+      A.out[v * ncell + c] = o;
+    }
+  }
+}
+
+// Sum the per-block d/dalpha of every direction in a fixed order (one block
+// of kAlphaThreads: strided partial sums, then a tree) and add their effect
+// at the arg-max cells (one thread: several speeds may share a cell).
+// apart: [ndim][nblocks][3].
 constexpr int kAlphaThreads = 256;
 template <int NDIM>
 __global__ void __launch_bounds__(kAlphaThreads) adj_alpha_kernel(const double* __restrict__ apart, int nblocks,
-                                 const unsigned long long* __restrict__ argidx, int dir,
+                                 const unsigned long long* __restrict__ argidx,
                                  const double* __restrict__ U, double* __restrict__ Ubar, int64_t ncell,
                                  double gamma) {
   constexpr int NVAR = NDIM + 2;
   __shared__ double red[kAlphaThreads][3];
-  double s[3] = {0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblocks; b += kAlphaThreads)
-    for (int k = 0; k < 3; ++k) s[k] += apart[b * 3 + k];
-  for (int k = 0; k < 3; ++k) red[threadIdx.x][k] = s[k];
-  __syncthreads();
-  for (int w = kAlphaThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int k = 0; k < 3; ++k) red[threadIdx.x][k] += red[threadIdx.x + w][k];
+  __shared__ double tot[NDIM][3];
+  for (int d = 0; d < NDIM; ++d) {
+    const double* ap = apart + (int64_t)d * nblocks * 3;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += kAlphaThreads)
+      for (int k = 0; k < 3; ++k) s[k] += ap[b * 3 + k];
+    for (int k = 0; k < 3; ++k) red[threadIdx.x][k] = s[k];
+    __syncthreads();
+    for (int w = kAlphaThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+        for (int k = 0; k < 3; ++k) red[threadIdx.x][k] += red[threadIdx.x + w][k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; ++k) tot[d][k] = red[0][k];
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
-  for (int k = 0; k < 3; ++k) s[k] = red[0][k];
-  for (int k = 0; k < 3; ++k) {
-    const unsigned long long c = argidx[dir * 3 + k];
-    if (c >= (unsigned long long)ncell) continue;
-    double Uc[NVAR], g[NVAR];
-    for (int v = 0; v < NVAR; ++v) {
-      Uc[v] = U[v * ncell + c];
-      g[v] = 0.0;
+  for (int d = 0; d < NDIM; ++d)
+    for (int k = 0; k < 3; ++k) {
+      const unsigned long long c = argidx[d * 3 + k];
+      if (c >= (unsigned long long)ncell) continue;
+      double Uc[NVAR], g[NVAR];
+      for (int v = 0; v < NVAR; ++v) {
+        Uc[v] = U[v * ncell + c];
+        g[v] = 0.0;
+      }
+      teno_adj::wave_speed_grad<NDIM>(Uc, d, k, gamma, tot[d][k], g);
+      for (int v = 0; v < NVAR; ++v) Ubar[v * ncell + c] += g[v];
     }
-    teno_adj::wave_speed_grad<NDIM>(Uc, dir, k, gamma, s[k], g);
-    for (int v = 0; v < NVAR; ++v) Ubar[v * ncell + c] += g[v];
-  }
 }
 
 __global__ void set_value_kernel(double* p, double v) {
@@ -650,34 +696,49 @@ int adj_blocks(int nsm) { return nsm * 8; }
 int adj_list_blocks(int nsm) { return nsm * 4 < 8 * kListThreads ? nsm * 4 : 8 * kListThreads; }
 
 struct AdjLayout {
-  // header: [0] status, [8] dt, [64] alpha bits (9 x 8), [136] pending-list counters of the
-  // recomputed forward stages (3 x 4), [160] arg-max (9 x 8)
-  size_t status = 0, dt = 8, alpha = 64, argidx = 160;
-  size_t aux = 0, fh = 0, kb = 0, contrib = 0, pending = 0, list = 0, lcount = 0, apart = 0, R = 0, U1 = 0, U2 = 0,
-         B1 = 0, B2 = 0, total = 0;
+  // header: [0] status, [8] dt; per stage s (the RK3 adjoint's three stage
+  // inputs; one for a right-hand-side adjoint): the LF speeds (9 x 8) with
+  // the pending-list counters of its forward recomputation after them at
+  // alpha + 128 s, its arg-max cells (9 x 8) at argidx + 128 s
+  static constexpr size_t kStage = 128;
+  size_t status = 0, dt = 8, alpha = 64, argidx = 512;
+  size_t aux = 0, aux_bytes = 0, cand = 0, fh = 0, kb = 0, kb_bytes = 0, contrib = 0, contrib_bytes = 0,
+         pending = 0, pending_bytes = 0, list = 0, lcount = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0,
+         total = 0;
 };
 
 AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   AdjLayout L;
   const size_t ncell = size_t(g->n[0] * g->n[1] * g->n[2]);
   const int nvar = g->ndim + 2;
+  const int nstage = op == TENO_OP_RK3_ADJOINT ? 3 : 1;
   int64_t maxifc = 0;
   for (int d = 0; d < g->ndim; ++d) maxifc = nifc_of(g, d) > maxifc ? nifc_of(g, d) : maxifc;
-  size_t off = kAlign;
+  size_t off = 1024;
+  // the cell pass's primitives of every stage input
   L.aux = off;
-  off += round_up(sizeof(double) * teno::aux_fields(g->ndim) * ncell);
+  L.aux_bytes = round_up(sizeof(double) * teno::aux_fields(g->ndim) * ncell);
+  off += nstage * L.aux_bytes;
+  L.cand = off;   // the cell pass's per-block arg-max candidates
+  off += round_up(sizeof(unsigned long long) * 18 * size_t(teno::cell_blocks(int64_t(ncell), nsm)));
+  // per direction: the kept interfaces' terms, the pending ones'
+  // contributions (the first also the forward recomputation's interface
+  // fluxes) and the pending marks
   L.kb = off;
-  off += round_up(sizeof(double) * 3 * nvar * size_t(maxifc));
+  L.kb_bytes = round_up(sizeof(double) * 3 * nvar * size_t(maxifc));
+  off += g->ndim * L.kb_bytes;
   L.contrib = off;
-  off += round_up(sizeof(double) * 6 * nvar * size_t(maxifc));
+  L.contrib_bytes = round_up(sizeof(double) * 6 * nvar * size_t(maxifc));
+  off += g->ndim * L.contrib_bytes;
   L.pending = off;
-  off += round_up(size_t(maxifc));
+  L.pending_bytes = round_up(size_t(maxifc));
+  off += g->ndim * L.pending_bytes;
   L.list = off;   // pending list (recomputed forward stages; the adjoint's general pass)
   off += round_up(sizeof(uint32_t) * size_t(maxifc));
   L.lcount = off;   // the general pass's per-block counts, offsets and total
   off += round_up(sizeof(int) * (2 * size_t(adj_list_blocks(nsm)) + 1));
-  L.apart = off;
-  off += round_up(sizeof(double) * 3 * 2 * size_t(adj_blocks(nsm)));
+  L.apart = off;   // [ndim][2 blocks][3]: d/dalpha per block of the kept and general passes
+  off += round_up(sizeof(double) * 3 * 2 * size_t(adj_blocks(nsm)) * g->ndim);
   if (op == TENO_OP_RK3_ADJOINT) {
     // half fluxes of the recomputed forward stages (two-pass fluxes)
     L.fh = off;
@@ -734,8 +795,7 @@ template <int NDIM, int DIR>
 void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const double* aux,
                     const unsigned long long* alpha, const double* Rbar, double scale, double* kb,
                     double* contrib, unsigned char* pending, uint32_t* list, int* lcount, double* apart,
-                    int* status, double* Ubar, const unsigned long long* argidx,
-                    const Grid& G, const Scheme& S) {
+                    int* status, const Grid& G, const Scheme& S) {
   adj_kept_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
                                                           status, G, S);
   int64_t nifc = 1;
@@ -749,52 +809,70 @@ void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const d
   adj_scatter_kernel<<<lblk, kListThreads, 0, st>>>(pending, nifc, boff, list);
   adj_general_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, contrib, list, total,
                                                              apart + 3 * nblk, status, G, S);
-  int64_t gb = (G.ncell + 255) / 256;
-  if (gb > int64_t(nsm) * 16) gb = int64_t(nsm) * 16;
-  adj_gather_kernel<NDIM, DIR><<<unsigned(gb), 256, 0, st>>>(U, Rbar, scale, kb, contrib, pending, Ubar, G,
-                                                              S.gamma);
-  adj_alpha_kernel<NDIM><<<1, kAlphaThreads, 0, st>>>(apart, 2 * nblk, argidx, DIR, U, Ubar, G.ncell, S.gamma);
 }
 
-// Ubar += scale * J(U)^T Rbar
-teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, const double* U,
-                             const double* Rbar, double* Ubar, double scale, cudaStream_t st) {
+template <int NDIM>
+void launch_adj_all(int nblk, int nsm, cudaStream_t st, const double* U, const double* aux,
+                    const unsigned long long* alpha, const unsigned long long* argidx, const double* Rbar,
+                    double scale, const AdjLayout& L, char* ws, int* status, GatherArgs A, const Grid& G,
+                    const Scheme& S) {
+  auto* list = reinterpret_cast<uint32_t*>(ws + L.list);
+  auto* lcount = reinterpret_cast<int*>(ws + L.lcount);
+  double* apart = reinterpret_cast<double*>(ws + L.apart);
+  for (int d = 0; d < NDIM; ++d) {
+    double* kb = reinterpret_cast<double*>(ws + L.kb + d * L.kb_bytes);
+    double* contrib = reinterpret_cast<double*>(ws + L.contrib + d * L.contrib_bytes);
+    auto* pending = reinterpret_cast<unsigned char*>(ws + L.pending + d * L.pending_bytes);
+    double* ap = apart + 6 * nblk * d;
+    if (d == 0) launch_adj_dir<NDIM, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, ap, status, G, S);
+    if constexpr (NDIM > 1)
+      if (d == 1) launch_adj_dir<NDIM, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, ap, status, G, S);
+    if constexpr (NDIM > 2)
+      if (d == 2) launch_adj_dir<NDIM, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, ap, status, G, S);
+    A.kb[d] = kb;
+    A.contrib[d] = contrib;
+    A.pending[d] = pending;
+    A.fscale[d] = scale * G.inv_dx[d];
+  }
+  int64_t gb = (G.ncell + 255) / 256;
+  if (gb > int64_t(nsm) * 16) gb = int64_t(nsm) * 16;
+  adj_gather_kernel<NDIM><<<unsigned(gb), 256, 0, st>>>(U, aux, Rbar, A, G, S.gamma);
+  adj_alpha_kernel<NDIM><<<1, kAlphaThreads, 0, st>>>(apart, 2 * nblk, argidx, U, A.out, G.ncell, S.gamma);
+}
+
+// out = a X + b Y + scale J(U)^T Rbar (X, Y nullable; out may alias X or Y,
+// not Rbar or U), with stage slot `stage` of the workspace.  With `cell`
+// the cell pass of U comes first; without it, the forward recomputation of
+// that stage has left its primitives, speeds and arg-max cells there.
+teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, int stage, bool cell,
+                             const double* U, const double* Rbar, double scale, double* out, const double* X,
+                             double a, const double* Y, double b, cudaStream_t st) {
   const Grid G = make_grid(g);
   const Scheme S = teno::scheme_of(g);
   const int nsm = sm_count();
   const int nblk = adj_blocks(nsm);
   int* status = reinterpret_cast<int*>(ws + L.status);
-  auto* alpha = reinterpret_cast<unsigned long long*>(ws + L.alpha);
-  auto* argidx = reinterpret_cast<unsigned long long*>(ws + L.argidx);
-  double* aux = reinterpret_cast<double*>(ws + L.aux);
-  double* kb = reinterpret_cast<double*>(ws + L.kb);
-  double* contrib = reinterpret_cast<double*>(ws + L.contrib);
-  double* apart = reinterpret_cast<double*>(ws + L.apart);
-  auto* pending = reinterpret_cast<unsigned char*>(ws + L.pending);
-  auto* list = reinterpret_cast<uint32_t*>(ws + L.list);
-  auto* lcount = reinterpret_cast<int*>(ws + L.lcount);
-  if (cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
-  if (cudaMemsetAsync(argidx, 0xff, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
-  if (teno::launch_cell(g->ndim, U, aux, nullptr, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
-    return TENO_ERR_CUDA;
-  int64_t cb = (G.ncell + 255) / 256;
-  if (cb > int64_t(nsm) * 16) cb = int64_t(nsm) * 16;
-  // the arg-max pass rewrites aux with the same values (same formulas)
-  switch (g->ndim) {
-    case 1: argmax_kernel<1><<<unsigned(cb), 256, 0, st>>>(U, alpha, argidx, G.ncell, g->gamma, aux); break;
-    case 2: argmax_kernel<2><<<unsigned(cb), 256, 0, st>>>(U, alpha, argidx, G.ncell, g->gamma, aux); break;
-    default: argmax_kernel<3><<<unsigned(cb), 256, 0, st>>>(U, alpha, argidx, G.ncell, g->gamma, aux); break;
+  auto* alpha = reinterpret_cast<unsigned long long*>(ws + L.alpha + stage * AdjLayout::kStage);
+  auto* argidx = reinterpret_cast<unsigned long long*>(ws + L.argidx + stage * AdjLayout::kStage);
+  double* aux = reinterpret_cast<double*>(ws + L.aux + stage * L.aux_bytes);
+  if (cell) {
+    auto* cand = reinterpret_cast<unsigned long long*>(ws + L.cand);
+    if (cudaMemsetAsync(alpha, 0, sizeof(unsigned long long) * 9, st) != cudaSuccess) return TENO_ERR_CUDA;
+    if (teno::launch_cell(g->ndim, U, aux, nullptr, alpha, status, G.ncell, g->gamma, nsm, st, cand) !=
+            cudaSuccess ||
+        teno::launch_argmax_finish(g->ndim, cand, G.ncell, nsm, argidx, st) != cudaSuccess)
+      return TENO_ERR_CUDA;
   }
-  for (int d = 0; d < g->ndim; ++d) {
-    if (g->ndim == 1) launch_adj_dir<1, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
-    else if (g->ndim == 2 && d == 0) launch_adj_dir<2, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
-    else if (g->ndim == 2) launch_adj_dir<2, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
-    else if (d == 0) launch_adj_dir<3, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
-    else if (d == 1) launch_adj_dir<3, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
-    else launch_adj_dir<3, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, apart, status, Ubar, argidx, G, S);
-    if (cudaGetLastError() != cudaSuccess) return TENO_ERR_CUDA;
-  }
-  return TENO_OK;
+  GatherArgs A{};
+  A.out = out;
+  A.X = X;
+  A.a = a;
+  A.Y = Y;
+  A.b = b;
+  if (g->ndim == 1) launch_adj_all<1>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S);
+  else if (g->ndim == 2) launch_adj_all<2>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S);
+  else launch_adj_all<3>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S);
+  return cudaGetLastError() == cudaSuccess ? TENO_OK : TENO_ERR_CUDA;
 }
 
 teno_status lincomb(double* out, double a, const double* x, double b, const double* y, int64_t n,
@@ -823,8 +901,8 @@ teno_status teno_rhs_adjoint(const teno_grid* g, const double* U, const double* 
   if (!is_dev(U) || !is_dev(dUdt_bar) || !is_dev(U_bar)) return TENO_ERR_INVALID_ARG;
   const AdjLayout L = adj_layout(g, TENO_OP_RHS_ADJOINT, sm_count());
   if (!ws || !al(ws, kAlign) || ws_bytes < L.total || !is_dev(ws)) return TENO_ERR_WORKSPACE;
-  return adjoint_sequence(g, L, static_cast<char*>(ws), U, dUdt_bar, U_bar, 1.0,
-                          static_cast<cudaStream_t>(stream));
+  return adjoint_sequence(g, L, static_cast<char*>(ws), 0, true, U, dUdt_bar, 1.0, U_bar, U_bar, 1.0, nullptr,
+                          0.0, static_cast<cudaStream_t>(stream));
 }
 
 teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double dt, const double* Ubar_next,
@@ -846,27 +924,39 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double 
   double* B2 = reinterpret_cast<double*>(w + L.B2);
   double* dtp = reinterpret_cast<double*>(w + L.dt);
 
-  // forward stages of the step (eq. 4.1-4.2) with the given dt
+  // forward stages of the step (eq. 4.1-4.2) with the given dt; each keeps
+  // its stage input's primitives, speeds and arg-max cells for the reverse
+  // pass (stage slots 0 and 1)
+  auto* cand = reinterpret_cast<unsigned long long*>(w + L.cand);
+  const int nsm = sm_count();
+  const int64_t ncell = int64_t(g->n[0]) * g->n[1] * g->n[2];
   set_value_kernel<<<1, 1, 0, st>>>(dtp, dt);
   if (cudaGetLastError() != cudaSuccess) return TENO_ERR_CUDA;
   teno_status s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.fh, L.contrib, L.list, U_n, R,
-                                      2, U_n, nullptr, U1, st);
+                                      2, U_n, nullptr, U1, st, cand);
   if (s != TENO_OK) return s;
-  s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.fh, L.contrib, L.list, U1, R, 3, U_n, U1,
-                          U2, st);
+  if (teno::launch_argmax_finish(g->ndim, cand, ncell, nsm, reinterpret_cast<unsigned long long*>(w + L.argidx),
+                                 st) != cudaSuccess)
+    return TENO_ERR_CUDA;
+  s = teno::forward_stage(g, w, L.status, L.dt, L.alpha + AdjLayout::kStage, L.aux + L.aux_bytes, L.fh, L.contrib,
+                          L.list, U1, R, 3, U_n, U1, U2, st, cand);
   if (s != TENO_OK) return s;
+  if (teno::launch_argmax_finish(g->ndim, cand, ncell, nsm,
+                                 reinterpret_cast<unsigned long long*>(w + L.argidx + AdjLayout::kStage),
+                                 st) != cudaSuccess)
+    return TENO_ERR_CUDA;
 
-  // reverse of eq. 4.3: B2 = 2/3 Ubar' + 2/3 dt J(U2)^T Ubar';  Ubar_n = 1/3 Ubar'
-  if ((s = lincomb(B2, 2.0 / 3.0, Ubar_next, 0.0, nullptr, ntot, st)) != TENO_OK) return s;
-  if ((s = adjoint_sequence(g, L, w, U2, Ubar_next, B2, 2.0 / 3.0 * dt, st)) != TENO_OK) return s;
-  if ((s = lincomb(Ubar_n, 1.0 / 3.0, Ubar_next, 0.0, nullptr, ntot, st)) != TENO_OK) return s;
-  // reverse of eq. 4.2: B1 = 1/4 B2 + 1/4 dt J(U1)^T B2;  Ubar_n += 3/4 B2
-  if ((s = lincomb(B1, 0.25, B2, 0.0, nullptr, ntot, st)) != TENO_OK) return s;
-  if ((s = adjoint_sequence(g, L, w, U1, B2, B1, 0.25 * dt, st)) != TENO_OK) return s;
-  if ((s = lincomb(Ubar_n, 1.0, Ubar_n, 0.75, B2, ntot, st)) != TENO_OK) return s;
+  // reverse of eq. 4.3: B2 = 2/3 Ubar' + 2/3 dt J(U2)^T Ubar'
+  if ((s = adjoint_sequence(g, L, w, 2, true, U2, Ubar_next, 2.0 / 3.0 * dt, B2, Ubar_next, 2.0 / 3.0, nullptr,
+                            0.0, st)) != TENO_OK)
+    return s;
+  // Ubar_n = 1/3 Ubar' + 3/4 B2 (eq. 4.3 and 4.2 reach U^n directly)
+  if ((s = lincomb(Ubar_n, 1.0 / 3.0, Ubar_next, 0.75, B2, ntot, st)) != TENO_OK) return s;
+  // reverse of eq. 4.2: B1 = 1/4 B2 + 1/4 dt J(U1)^T B2
+  if ((s = adjoint_sequence(g, L, w, 1, false, U1, B2, 0.25 * dt, B1, B2, 0.25, nullptr, 0.0, st)) != TENO_OK)
+    return s;
   // reverse of eq. 4.1: Ubar_n += B1 + dt J(U_n)^T B1
-  if ((s = lincomb(Ubar_n, 1.0, Ubar_n, 1.0, B1, ntot, st)) != TENO_OK) return s;
-  return adjoint_sequence(g, L, w, U_n, B1, Ubar_n, dt, st);
+  return adjoint_sequence(g, L, w, 0, false, U_n, B1, dt, Ubar_n, Ubar_n, 1.0, B1, 1.0, st);
 }
 
 }  // extern "C"

@@ -314,6 +314,42 @@ TENO_HD inline void flux_vjp(const double (&U)[NDIM + 2], double gamma, const do
   out[E] = ud * G[E] + t;
 }
 
+// The point quantities of one cell that its per-cell adjoint terms share:
+// 1/rho, u, |u|^2/2 and p (eq. 4.7).
+template <int NDIM>
+struct CellPrim {
+  double ir, u[NDIM], hq, p;
+};
+
+template <int NDIM>
+TENO_HD inline void cell_prim(const double (&U)[NDIM + 2], double gamma, CellPrim<NDIM>& P) {
+  P.ir = recip(U[0]);
+  double q = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    P.u[k] = U[1 + k] * P.ir;
+    q = fma(P.u[k], P.u[k], q);
+  }
+  P.hq = 0.5 * q;
+  P.p = (gamma - 1.0) * fma(-U[0], P.hq, U[NDIM + 1]);
+}
+
+// acc += A(U)^T G, the product of flux_vjp, from the cell's CellPrim.
+template <int NDIM, int DIR>
+TENO_HD inline void flux_vjp_acc(const double (&U)[NDIM + 2], const CellPrim<NDIM>& P, double gamma,
+                                 const double (&G)[NDIM + 2], double (&acc)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  constexpr int E = NDIM + 1;
+  double GU = G[0] * U[0];
+  for (int v = 1; v < NV; ++v) GU = fma(G[v], U[v], GU);
+  const double sc = P.ir * fma(P.p, G[E], GU);
+  const double ud = P.u[DIR];
+  const double t = (gamma - 1.0) * fma(ud, G[E], G[1 + DIR]);
+  acc[0] = fma(ud, G[0] - sc, fma(P.hq, t, acc[0]));
+  for (int k = 0; k < NDIM; ++k) acc[1 + k] = fma(ud, G[1 + k], fma(-t, P.u[k], acc[1 + k]));
+  acc[1 + DIR] += sc;
+  acc[E] = fma(ud, G[E], acc[E] + t);
+}
+
 // Roe state of cells i (a) and i+1 (b) with the point quantities its
 // derivative needs.
 template <int NDIM>
@@ -400,11 +436,15 @@ TENO_HD inline void roe_point_vjp(double ir, const double (&u)[NDIM], double q, 
 // i+1, U~ and Fbar, returns U~bar, the Roe-parameter terms of cells i (roeA)
 // and i+1 (roeB), and dJ/dalpha (ab[1] receives the whole derivative with
 // respect to a_mid; the other middle entries are zero).
+// The Roe-parameter terms are returned as the adjoints of cell a's and cell
+// b's own parameters, pa and pb = (d/dsqrt(rho), d/du_0..d/du_{NDIM-1},
+// d/dH); roe_param_vjp turns them into conservative terms, so that a cell
+// reached by several interfaces applies that per-cell map once to their sum.
 template <int NDIM, int DIR>
-TENO_HD inline void interface_vjp_kept_ifc(const RoeState<NDIM>& R, const double (&Ut)[NDIM + 2],
+TENO_HD inline void interface_vjp_kept_roe(const RoeState<NDIM>& R, const double (&Ut)[NDIM + 2],
                                            const double (&alpha)[NDIM + 2], double gamma,
                                            const double (&Fb)[NDIM + 2], double (&Utb)[NDIM + 2],
-                                           double (&roeA)[NDIM + 2], double (&roeB)[NDIM + 2],
+                                           double (&pa)[NDIM + 2], double (&pb)[NDIM + 2],
                                            double (&ab)[NDIM + 2]) {
   constexpr int NV = NDIM + 2;
   constexpr int E = NDIM + 1;
@@ -479,14 +519,57 @@ TENO_HD inline void interface_vjp_kept_ifc(const RoeState<NDIM>& R, const double
   for (int k = 0; k < NDIM; ++k) Dsum = fma(R.ua[k] - R.ub[k], utb[k], Dsum);
   const double tS = iS * iS * Dsum;
   const double saS = sa * iS, sbS = sb * iS;
-  double uab[NDIM], ubb[NDIM];
+  pa[0] = sb * tS;
+  pb[0] = -sa * tS;
   for (int k = 0; k < NDIM; ++k) {
-    uab[k] = saS * utb[k];
-    ubb[k] = sbS * utb[k];
+    pa[1 + k] = saS * utb[k];
+    pb[1 + k] = sbS * utb[k];
   }
+  pa[E] = saS * Hbar;
+  pb[E] = sbS * Hbar;
+}
+
+// out += dJ/dU at one cell from the adjoints p = (d/dsqrt(rho), d/du, d/dH)
+// of its Roe parameters (ir = 1/rho, q = |u|^2, sx = sqrt(rho), Hx = (E+p)/rho).
+template <int NDIM>
+TENO_HD inline void roe_param_vjp(double ir, const double (&u)[NDIM], double q, double sx, double Hx,
+                                  double gamma, const double (&p)[NDIM + 2], double (&out)[NDIM + 2]) {
+  double uxb[NDIM];
+  for (int k = 0; k < NDIM; ++k) uxb[k] = p[1 + k];
+  roe_point_vjp<NDIM>(ir, u, q, sx, Hx, gamma, p[0], p[NDIM + 1], uxb, out);
+}
+
+// acc += dJ/dU at one cell from the adjoints rp = (d/dsqrt(rho), d/du,
+// d/dH) of its Roe parameters, as roe_param_vjp, from the cell's CellPrim
+// (sx = sqrt(rho), Hx = (E+p)/rho).
+template <int NDIM>
+TENO_HD inline void roe_param_vjp_acc(const CellPrim<NDIM>& P, double sx, double Hx, double gamma,
+                                      const double (&rp)[NDIM + 2], double (&acc)[NDIM + 2]) {
+  constexpr int E = NDIM + 1;
+  const double gm1 = gamma - 1.0;
+  double uub = 0.0;
+  for (int k = 0; k < NDIM; ++k) uub = fma(P.u[k], rp[1 + k], uub);
+  const double hb = rp[E] * P.ir;
+  acc[0] += fma(0.5 * sx * P.ir, rp[0], fma(hb, fma(gm1, P.hq, -Hx), -P.ir * uub));
+  const double ghb = gm1 * hb;
+  for (int k = 0; k < NDIM; ++k) acc[1 + k] += fma(P.ir, rp[1 + k], -ghb * P.u[k]);
+  acc[E] = fma(gamma, hb, acc[E]);
+}
+
+// The interface part of the all-kept VJP with the Roe-parameter terms of
+// cells i (roeA) and i+1 (roeB) in conservative form.
+template <int NDIM, int DIR>
+TENO_HD inline void interface_vjp_kept_ifc(const RoeState<NDIM>& R, const double (&Ut)[NDIM + 2],
+                                           const double (&alpha)[NDIM + 2], double gamma,
+                                           const double (&Fb)[NDIM + 2], double (&Utb)[NDIM + 2],
+                                           double (&roeA)[NDIM + 2], double (&roeB)[NDIM + 2],
+                                           double (&ab)[NDIM + 2]) {
+  constexpr int NV = NDIM + 2;
+  double pa[NV], pb[NV];
+  interface_vjp_kept_roe<NDIM, DIR>(R, Ut, alpha, gamma, Fb, Utb, pa, pb, ab);
   for (int v = 0; v < NV; ++v) roeA[v] = roeB[v] = 0.0;
-  roe_point_vjp<NDIM>(R.ira, R.ua, R.qa, sa, R.Ha, gamma, sb * tS, saS * Hbar, uab, roeA);
-  roe_point_vjp<NDIM>(R.irb, R.ub, R.qb, sb, R.Hb, gamma, -sa * tS, sbS * Hbar, ubb, roeB);
+  roe_param_vjp<NDIM>(R.ira, R.ua, R.qa, R.sa, R.Ha, gamma, pa, roeA);
+  roe_param_vjp<NDIM>(R.irb, R.ub, R.qb, R.sb, R.Hb, gamma, pb, roeB);
 }
 
 // The whole all-kept VJP of one interface, as interface_vjp (same inputs and

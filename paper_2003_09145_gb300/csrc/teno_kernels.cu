@@ -53,17 +53,28 @@ __device__ __forceinline__ void store_flux_half(const double (&Uc)[NDIM + 2], co
 #ifndef TENO_CELL_MINBLOCKS
 #define TENO_CELL_MINBLOCKS 2   // 128 registers, 16 warps per SM: measured 0.1 ms per step
 #endif                          // faster than 3 (80 registers) or 4 (64)
-template <int NDIM>
+// With ARG, every block also writes, per speed, its largest value and the
+// lowest cell index attaining it to cand[block][9][2] (value bits, index):
+// the arg-max cells through which the adjoint differentiates the global
+// speeds (argmax_finish_kernel reduces the candidates).
+template <int NDIM, bool ARG>
 __global__ void __launch_bounds__(256, TENO_CELL_MINBLOCKS) cell_kernel(const double* __restrict__ U,
                                                    double* __restrict__ aux,
                                                    double* __restrict__ fh,
                                                    unsigned long long* __restrict__ alpha,
                                                    int* __restrict__ status,
-                                                   int64_t ncell, double gamma) {
+                                                   int64_t ncell, double gamma,
+                                                   unsigned long long* __restrict__ cand) {
   constexpr int NVAR = NDIM + 2;
   unsigned long long lam[NDIM][3];   // bit patterns of the running maxima (>= 0)
+  long long arg[NDIM][3];            // (ARG) the first cell of this thread attaining each
 #pragma unroll
-  for (int d = 0; d < NDIM; ++d) lam[d][0] = lam[d][1] = lam[d][2] = 0ull;
+  for (int d = 0; d < NDIM; ++d)
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      lam[d][s] = 0ull;
+      arg[d][s] = ncell;
+    }
   bool bad = false;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -80,35 +91,101 @@ __global__ void __launch_bounds__(256, TENO_CELL_MINBLOCKS) cell_kernel(const do
     // max|u| is kept as max|u/2| and doubled (exactly) below
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      lam[d][0] = max_abs_bits(lam[d][0], fma(2.0, uh[d], -cs));
-      lam[d][1] = max_abs_bits(lam[d][1], uh[d]);
-      lam[d][2] = max_abs_bits(lam[d][2], fma(2.0, uh[d], cs));
+      const double x[3] = {fma(2.0, uh[d], -cs), uh[d], fma(2.0, uh[d], cs)};
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        if constexpr (ARG) {
+          const unsigned long long m = max_abs_bits(lam[d][s], x[s]);
+          if (m != lam[d][s]) arg[d][s] = c;
+          lam[d][s] = m;
+        } else {
+          lam[d][s] = max_abs_bits(lam[d][s], x[s]);
+        }
+      }
     }
   }
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) lam[d][1] = dbits(2.0 * __longlong_as_double(static_cast<long long>(lam[d][1])));
-  // warp max on bit patterns (all values are >= 0)
+  // warp max on bit patterns (all values are >= 0); with ARG the lowest
+  // index among the lanes holding the maximum
   __shared__ unsigned long long red[8][NDIM * 3];
+  __shared__ long long rarg[ARG ? 8 : 1][NDIM * 3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d)
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       unsigned long long v = lam[d][s];
+      long long a = arg[d][s];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        if constexpr (ARG) {
+          const long long b = __shfl_xor_sync(0xffffffffu, a, o);
+          if (w > v || (w == v && b < a)) a = b;
+        }
         v = v > w ? v : w;
       }
-      if (lane == 0) red[warp][d * 3 + s] = v;
+      if (lane == 0) {
+        red[warp][d * 3 + s] = v;
+        if constexpr (ARG) rarg[warp][d * 3 + s] = a;
+      }
     }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStatusNonphysical);
   __syncthreads();
   if (threadIdx.x < NDIM * 3) {
     unsigned long long v = 0;
+    long long a = ncell;
     const int nw = blockDim.x >> 5;
-    for (int w = 0; w < nw; ++w) v = v > red[w][threadIdx.x] ? v : red[w][threadIdx.x];
+    for (int w = 0; w < nw; ++w) {
+      const unsigned long long x = red[w][threadIdx.x];
+      if constexpr (ARG) {
+        const long long b = rarg[w][threadIdx.x];
+        if (x > v || (x == v && b < a)) a = b;
+      }
+      v = v > x ? v : x;
+    }
     atomicMax(&alpha[threadIdx.x], v);
+    if constexpr (ARG) {
+      cand[(blockIdx.x * 9 + threadIdx.x) * 2] = v;
+      cand[(blockIdx.x * 9 + threadIdx.x) * 2 + 1] = static_cast<unsigned long long>(a);
+    }
+  }
+}
+
+// The arg-max cells of the nine LF speeds from the cell pass's per-block
+// candidates: the largest value of each speed and the lowest cell index
+// attaining it (entries of unused directions stay as they are).
+constexpr int kArgThreads = 256;
+__global__ void __launch_bounds__(kArgThreads) argmax_finish_kernel(const unsigned long long* __restrict__ cand,
+                                                                    int nblocks, int nspeed,
+                                                                    unsigned long long* __restrict__ argidx) {
+  __shared__ unsigned long long sv[kArgThreads];
+  __shared__ unsigned long long sa[kArgThreads];
+  for (int k = 0; k < nspeed; ++k) {
+    unsigned long long v = 0, a = ~0ull;
+    for (int b = threadIdx.x; b < nblocks; b += kArgThreads) {
+      const unsigned long long x = cand[(b * 9 + k) * 2], i = cand[(b * 9 + k) * 2 + 1];
+      if (x > v || (x == v && i < a)) {
+        v = x;
+        a = i;
+      }
+    }
+    sv[threadIdx.x] = v;
+    sa[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = kArgThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        const unsigned long long x = sv[threadIdx.x + w], i = sa[threadIdx.x + w];
+        if (x > sv[threadIdx.x] || (x == sv[threadIdx.x] && i < sa[threadIdx.x])) {
+          sv[threadIdx.x] = x;
+          sa[threadIdx.x] = i;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) argidx[k] = sa[0];
+    __syncthreads();
   }
 }
 
@@ -567,16 +644,32 @@ static inline int blocks_for(int64_t n, int threads, int cap) {
   return static_cast<int>(b);
 }
 
+int cell_blocks(int64_t ncell, int nsm) { return blocks_for(ncell, 256, nsm * 8); }
+
 cudaError_t launch_cell(int ndim, const double* U, double* aux, double* fh,
                         unsigned long long* alpha, int* status, int64_t ncell,
-                        double gamma, int nsm, cudaStream_t st) {
+                        double gamma, int nsm, cudaStream_t st, unsigned long long* cand) {
   const int threads = 256;
-  const int blocks = blocks_for(ncell, threads, nsm * 8);
-  switch (ndim) {
-    case 1: cell_kernel<1><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma); break;
-    case 2: cell_kernel<2><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma); break;
-    default: cell_kernel<3><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma); break;
+  const int blocks = cell_blocks(ncell, nsm);
+  if (cand) {
+    switch (ndim) {
+      case 1: cell_kernel<1, true><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma, cand); break;
+      case 2: cell_kernel<2, true><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma, cand); break;
+      default: cell_kernel<3, true><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma, cand); break;
+    }
+    return cudaGetLastError();
   }
+  switch (ndim) {
+    case 1: cell_kernel<1, false><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma, nullptr); break;
+    case 2: cell_kernel<2, false><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma, nullptr); break;
+    default: cell_kernel<3, false><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, status, ncell, gamma, nullptr); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmax_finish(int ndim, const unsigned long long* cand, int64_t ncell, int nsm,
+                                 unsigned long long* argidx, cudaStream_t st) {
+  argmax_finish_kernel<<<1, kArgThreads, 0, st>>>(cand, cell_blocks(ncell, nsm), 3 * ndim, argidx);
   return cudaGetLastError();
 }
 
@@ -691,7 +784,7 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
                           size_t alpha_off, size_t aux_off, size_t fh_off, size_t fhat_off, size_t list_off,
                           const double* U, double* R, int mode, const double* Un, const double* Uk,
-                          double* Uout, cudaStream_t st) {
+                          double* Uout, cudaStream_t st, unsigned long long* cand) {
   Grid G;
   for (int k = 0; k < 3; ++k) {
     G.n[k] = g->n[k];
@@ -715,7 +808,7 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
   double* fh = fh_off ? reinterpret_cast<double*>(ws + fh_off) : nullptr;
   unsigned* count = reinterpret_cast<unsigned*>(ws + alpha_off + kPendingCountOffset);
   if (cudaMemsetAsync(alpha, 0, kAlphaAndCountBytes, st) != cudaSuccess) return TENO_ERR_CUDA;
-  if (launch_cell(g->ndim, U, aux, fh, alpha, status, G.ncell, g->gamma, nsm, st) != cudaSuccess)
+  if (launch_cell(g->ndim, U, aux, fh, alpha, status, G.ncell, g->gamma, nsm, st, cand) != cudaSuccess)
     return TENO_ERR_CUDA;
   for (int d = 0; d < g->ndim; ++d) {
     if (launch_flux(g->ndim, d, U, aux, fh, alpha, Fhat, nullptr, list, count + d, status, G, S, nsm, st,

@@ -29,10 +29,16 @@ inline Scheme scheme_of(const teno_grid* g) {
 
 // Primitives (aux) and LF speeds of every cell; with `fh` (nullable) also
 // the half physical fluxes F_d/2 without their mass component,
-// [ndim][nvar - 1][ncell].
+// [ndim][nvar - 1][ncell]; with `cand` (nullable, 18 words per block of
+// cell_blocks) the per-block arg-max candidates of the speeds.
+int cell_blocks(int64_t ncell, int nsm);
 cudaError_t launch_cell(int ndim, const double* U, double* aux, double* fh,
                         unsigned long long* alpha, int* status, int64_t ncell,
-                        double gamma, int nsm, cudaStream_t st);
+                        double gamma, int nsm, cudaStream_t st, unsigned long long* cand = nullptr);
+// argidx[3 d + s] = the lowest cell index at which speed s of direction d
+// attains its maximum, from the candidates of a launch_cell with `cand`.
+cudaError_t launch_argmax_finish(int ndim, const unsigned long long* cand, int64_t ncell, int nsm,
+                                 unsigned long long* argidx, cudaStream_t st);
 
 // The interface fluxes of direction `dir` into Fhat.  With `flags`, or
 // without a pending list or the cell pass's half fluxes `fh`, one pass; with
@@ -86,10 +92,10 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 // the pending counters after them), the per-cell primitives, the half
 // fluxes, the interface-flux buffer and the pending list (fh_off or list_off
 // 0: one-pass fluxes); R holds the partial sums of the multi-dimensional
-// difference.
+// difference; `cand` (nullable) as for launch_cell.
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
                           size_t alpha_off, size_t aux_off, size_t fh_off, size_t fhat_off, size_t list_off,
                           const double* U, double* R, int mode, const double* Un, const double* Uk,
-                          double* Uout, cudaStream_t st);
+                          double* Uout, cudaStream_t st, unsigned long long* cand = nullptr);
 
 }  // namespace teno

@@ -1,11 +1,45 @@
 // adjoint_core_host.cpp -- test helper: the adjoint core's interface VJPs
 // (teno_adjoint_core.cuh, plain binary64 host code) behind a C interface for
 // the CPU tests.  3D, nvar = 5; arrays row-major as declared.
+#include <cmath>
 #include <cstring>
 
 #include "teno_adjoint_core.cuh"
 
 namespace {
+
+// The all-kept VJP assembled as the adjoint kernels assemble it: the kept
+// pass's interface part with the Roe-parameter adjoints of cells i and i+1
+// (interface_vjp_kept_roe), then per point the gather's per-cell maps
+// (flux_vjp_acc with P_j Fbar, M_j U~bar, and roe_param_vjp_acc at j = 2, 3).
+template <int DIR>
+void split(const double (&Up)[6][5], const double (&alpha)[5], double gamma, const double (&Fb)[5],
+           double (&Ub)[6][5], double (&Ab)[5]) {
+  const double P[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
+  const double M[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+  double Ut[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int v = 0; v < 5; ++v)
+    for (int j = 0; j < 6; ++j) Ut[v] += M[j] * Up[j][v];
+  teno_adj::RoeState<3> R;
+  teno_adj::roe_from_conservative<3>(Up[2], Up[3], gamma, R);
+  double Utb[5], pa[5], pb[5];
+  teno_adj::interface_vjp_kept_roe<3, DIR>(R, Ut, alpha, gamma, Fb, Utb, pa, pb, Ab);
+  for (int j = 0; j < 6; ++j) {
+    teno_adj::CellPrim<3> C;
+    teno_adj::cell_prim<3>(Up[j], gamma, C);
+    double G[5];
+    for (int v = 0; v < 5; ++v) {
+      Ub[j][v] = M[j] * Utb[v];
+      G[v] = P[j] * Fb[v];
+    }
+    teno_adj::flux_vjp_acc<3, DIR>(Up[j], C, gamma, G, Ub[j]);
+    if (j == 2 || j == 3) {
+      const double sx = std::sqrt(Up[j][0]);
+      const double Hx = (Up[j][4] + C.p) * C.ir;
+      teno_adj::roe_param_vjp_acc<3>(C, sx, Hx, gamma, j == 2 ? pa : pb, Ub[j]);
+    }
+  }
+}
 
 template <int DIR>
 void run(int kept, const double* up, const double* al, double gamma, const double* fb, double* ub, double* ab) {
@@ -13,7 +47,9 @@ void run(int kept, const double* up, const double* al, double gamma, const doubl
   std::memcpy(Up, up, sizeof(Up));
   std::memcpy(alpha, al, sizeof(alpha));
   std::memcpy(Fb, fb, sizeof(Fb));
-  if (kept) {
+  if (kept == 2) {
+    split<DIR>(Up, alpha, gamma, Fb, Ub, Ab);
+  } else if (kept) {
     teno_adj::interface_vjp_kept<3, DIR>(Up, alpha, gamma, Fb, Ub, Ab);
   } else {
     const unsigned sel[5][2] = {{7u, 7u}, {7u, 7u}, {7u, 7u}, {7u, 7u}, {7u, 7u}};
@@ -35,6 +71,22 @@ extern "C" void adj_flux_vjp3(int dir, const double* u, double gamma, const doub
   std::memcpy(out, O, sizeof(O));
 }
 
+// acc += A(U)^T G through the cell's shared primitives (flux_vjp_acc)
+extern "C" void adj_flux_vjp_acc3(int dir, const double* u, double gamma, const double* g, double* acc) {
+  double U[5], G[5], A[5];
+  std::memcpy(U, u, sizeof(U));
+  std::memcpy(G, g, sizeof(G));
+  std::memcpy(A, acc, sizeof(A));
+  teno_adj::CellPrim<3> C;
+  teno_adj::cell_prim<3>(U, gamma, C);
+  if (dir == 0) teno_adj::flux_vjp_acc<3, 0>(U, C, gamma, G, A);
+  else if (dir == 1) teno_adj::flux_vjp_acc<3, 1>(U, C, gamma, G, A);
+  else teno_adj::flux_vjp_acc<3, 2>(U, C, gamma, G, A);
+  std::memcpy(acc, A, sizeof(A));
+}
+
+// kept: 0 = the general VJP with every stencil selected, 1 = the all-kept
+// closed form, 2 = the closed form split as the kernels split it
 extern "C" void adj_interface_vjp3(int dir, int kept, const double* up, const double* al, double gamma,
                                    const double* fb, double* ub, double* ab) {
   if (dir == 0) run<0>(kept, up, al, gamma, fb, ub, ab);

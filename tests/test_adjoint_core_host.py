@@ -30,6 +30,8 @@ def lib():
     L.adj_interface_vjp3.restype = None
     L.adj_flux_vjp3.argtypes = [ctypes.c_int, P, ctypes.c_double, P, P]
     L.adj_flux_vjp3.restype = None
+    L.adj_flux_vjp_acc3.argtypes = [ctypes.c_int, P, ctypes.c_double, P, P]
+    L.adj_flux_vjp_acc3.restype = None
     return L
 
 
@@ -119,6 +121,25 @@ def test_kept_closed_form_equals_general_vjp(lib, d):
 
 
 @pytest.mark.parametrize("d", [0, 1, 2])
+def test_split_kept_form_equals_general_vjp(lib, d):
+    """The all-kept VJP as the kernels assemble it -- the kept pass's
+    interface part with the adjoints of the two Roe cells' parameters, then
+    per point the gather's maps (A(U_j)^T P_j Fbar, M_j U~bar, the Roe
+    parameters' map at points 2 and 3) -- against the general VJP."""
+    rng = np.random.default_rng(400 + d)
+    for _ in range(20):
+        Up = _state(rng)
+        a0, am, aE = rng.uniform(0.5, 3.0, 3)
+        alpha = np.array([a0, am, am, am, aE])
+        Fb = rng.standard_normal(5)
+        ub_s, ab_s = _vjp(lib, d, 2, Up, alpha, Fb)
+        ub_k, ab_k = _vjp(lib, d, 1, Up, alpha, Fb)
+        ub_g, _ = _vjp(lib, d, 0, Up, alpha, Fb)
+        assert np.abs(ub_s - ub_g).max() <= 1e-12 * np.abs(ub_g).max()
+        assert np.array_equal(ab_s, ab_k)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
 def test_kept_vjp_matches_central_differences(lib, d):
     rng = np.random.default_rng(200 + d)
     Up = _state(rng)
@@ -162,3 +183,8 @@ def test_flux_jacobian_transpose_matches_central_differences(lib, d):
             Um[v] -= h
             fd = G @ (flux(Up) - flux(Um)) / (2 * h)
             assert abs(out[v] - fd) <= 1e-7 * max(1.0, abs(fd)), v
+        # the gather's form: acc += A(U)^T G through the cell's shared primitives
+        acc0 = rng.standard_normal(5)
+        acc = acc0.copy()
+        lib.adj_flux_vjp_acc3(d, _p(np.ascontiguousarray(U)), GAMMA, _p(np.ascontiguousarray(G)), _p(acc))
+        assert np.abs((acc - acc0) - out).max() <= 1e-13 * max(1.0, np.abs(out).max())
