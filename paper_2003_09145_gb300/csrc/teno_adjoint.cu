@@ -200,7 +200,13 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     }
     const bool kept = S.keep_idx >= 0 && teno::cert_keep<NDIM>(C, S);
     pending[q] = kept ? 0 : 1;
-    if (!kept) continue;
+    if (!kept) {
+      // a pending interface's terms come from adj_general_kernel; zeros
+      // here let the gather add kb for every interface alike
+#pragma unroll
+      for (int v = 0; v < 3 * NVAR; ++v) kb[(int64_t)v * I.nifc + q] = 0.0;
+      continue;
+    }
     double Fb[NVAR];
     interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
     double Utb[NVAR], pa[NVAR], pb[NVAR], ab[NVAR];
@@ -318,8 +324,9 @@ __global__ void __launch_bounds__(kListThreads) adj_scatter_kernel(const unsigne
 
 // The listed interfaces, one thread each: the selections by the forward
 // pass's own binary64 decisions, then the general VJP (or the closed form
-// where every stencil is kept after all); the six cells' contributions go to
-// contrib[6 nvar][nifc].
+// where every stencil is kept after all); the six cells' contributions, less
+// the all-kept flux term P_j A(U_j)^T Fbar that the gather adds for every
+// interface, go to contrib[6 nvar][nifc].
 template <int NDIM, int DIR>
 __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
     const double* __restrict__ U, const double* __restrict__ aux,
@@ -358,9 +365,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
     interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
     double Ub[6][NVAR], ab[NVAR];
     if (all_kept)
-      teno_adj::interface_vjp_kept<NDIM, DIR>(Up, fa, S.gamma, Fb, Ub, ab);
+      teno_adj::interface_vjp_kept<NDIM, DIR, true>(Up, fa, S.gamma, Fb, Ub, ab);
     else
-      teno_adj::interface_vjp<NDIM, DIR>(Up, fa, sel, S.gamma, Fb, Ub, ab);
+      teno_adj::interface_vjp<NDIM, DIR, true>(Up, fa, sel, S.gamma, Fb, Ub, ab);
 #pragma unroll
     for (int j = 0; j < 6; ++j)
 #pragma unroll
@@ -377,8 +384,8 @@ __constant__ double c_adjM[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 6
 
 // What the gather reads per direction, and its output.
 struct GatherArgs {
-  const double* kb[3];              // [3 nvar][nifc_d]: U~bar, Roe-parameter adjoints of cells i, i+1
-  const double* contrib[3];         // [6 nvar][nifc_d]: the pending interfaces' contributions
+  const double* kb[3];              // [3 nvar][nifc_d]: U~bar, Roe-parameter adjoints of cells i, i+1 (0 if pending)
+  const double* contrib[3];         // [6 nvar][nifc_d]: the pending interfaces' contributions, flux term excluded
   const unsigned char* pending[3];  // [nifc_d]
   double fscale[3];                 // scale / dx_d
   double* out;                      // out = a X + b Y + the adjoint (X, Y nullable; out may be X or Y)
@@ -387,37 +394,77 @@ struct GatherArgs {
   double a, b;
 };
 
-// The share of interface q's slot j at the cell that slot maps to: the
-// pending interface's own contribution, or for a kept one M_j U~bar_q into
-// acc, its Roe-parameter adjoints (j = 2: cell i, j = 3: cell i+1) into rp
-// and fs P_j Fbar_q into Fsum.
+// Every interface's share at the cell its slot j maps to: M_j U~bar_q into
+// acc and its Roe-parameter adjoints (j = 2: cell i, j = 3: cell i+1) into
+// rp (both zero for a pending interface), and for a pending one its own
+// contribution into acc.
 template <int NVAR>
-__device__ __forceinline__ void gather_slot(int j, int64_t q, int64_t qd, const double* __restrict__ contrib,
-                                            const double* __restrict__ kb,
-                                            const unsigned char* __restrict__ pending,
-                                            const double* __restrict__ Rbar, int64_t nifc, int64_t ncell,
-                                            int64_t line, int64_t nd, int64_t cstride, double fs,
-                                            double (&acc)[NVAR], double (&rp)[NVAR], double (&Fsum)[NVAR]) {
-  if (pending[q]) {
+__device__ __forceinline__ void slot_terms(int j, int64_t q, const double* __restrict__ kb,
+                                           const double* __restrict__ contrib,
+                                           const unsigned char* __restrict__ pending, int64_t nifc,
+                                           double (&acc)[NVAR], double (&rp)[NVAR]) {
+  const double Mj = c_adjM[j];
 #pragma unroll
-    for (int v = 0; v < NVAR; ++v) acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
-    return;
-  }
-  const double Pj = c_adjP[j] * fs, Mj = c_adjM[j];
-  // P_j (Rbar_qd [qd < n] - Rbar_{qd-1} [qd >= 1]) fs
-#pragma unroll
-  for (int v = 0; v < NVAR; ++v) {
-    const double ra = (qd < nd) ? Rbar[v * ncell + line + qd * cstride] : 0.0;
-    const double rb = (qd >= 1) ? Rbar[v * ncell + line + (qd - 1) * cstride] : 0.0;
-    Fsum[v] = fma(Pj, ra - rb, Fsum[v]);
-    acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
-  }
+  for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
   if (j == 2)
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(NVAR + v) * nifc + q];
   if (j == 3)
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+  if (pending[q])
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
+}
+
+// The cells the stencil form does not cover (transmissive ends, periodic
+// lines shorter than six cells): every (interface qd, slot j) whose point j,
+// ghost(qd - 3 + j), is cell id, slot by slot, with fs P_j Fbar_qd into Fsum.
+// Out of line: rare, and the hot loop's code stays small.
+template <int NVAR>
+__device__ __noinline__ void gather_edge(int idl, int ndl, int bc, int64_t q0, int64_t sd, int64_t line,
+                                         int64_t cstride, int64_t ncell, int64_t nifc, double fs,
+                                         const double* __restrict__ Rbar, const double* __restrict__ kb,
+                                         const double* __restrict__ contrib,
+                                         const unsigned char* __restrict__ pending, double (&acc)[NVAR],
+                                         double (&rp)[NVAR], double (&Fsum)[NVAR]) {
+  for (int j = 0; j < 6; ++j) {
+    int lo, hi, step;
+    if (bc == 0) {
+      // x = qd - 3 + j ranges over [j - 3, nd + j - 3]; x = id (mod nd)
+      int x = idl;
+      while (x - ndl >= j - 3) x -= ndl;
+      while (x < j - 3) x += ndl;
+      lo = x + 3 - j;
+      hi = ndl;
+      step = ndl;
+    } else {
+      // transmissive: points below 0 map to cell 0, points above nd-1 to nd-1
+      lo = idl + 3 - j;
+      hi = idl + 3 - j;
+      if (idl == 0) lo = 0;
+      if (idl == ndl - 1) hi = ndl;
+      if (lo < 0) lo = 0;
+      if (hi > ndl) hi = ndl;
+      step = 1;
+    }
+    for (int qd = lo; qd <= hi; qd += step) {
+      if (bc != 0) {
+        const int x = qd - 3 + j;
+        const int mapped = x < 0 ? 0 : (x >= ndl ? ndl - 1 : x);
+        if (mapped != idl) continue;
+      }
+      const int64_t q = q0 + (int64_t)qd * sd;
+      const double Pj = c_adjP[j] * fs;
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) {
+        const double ra = (qd < ndl) ? Rbar[v * ncell + line + (int64_t)qd * cstride] : 0.0;
+        const double rb = (qd >= 1) ? Rbar[v * ncell + line + (int64_t)(qd - 1) * cstride] : 0.0;
+        Fsum[v] = fma(Pj, ra - rb, Fsum[v]);
+      }
+      slot_terms<NVAR>(j, q, kb, contrib, pending, nifc, acc, rp);
+    }
+  }
 }
 
 // Direction DIR's share at cell c (indices i0, i1, i2): acc += the M-weighted
@@ -438,29 +485,24 @@ __device__ __forceinline__ void gather_dir(const Grid& G, int64_t c, int64_t i0,
   const int64_t nifc = m0 * m1 * (G.n[2] + (DIR == 2));
   const int64_t sd = (DIR == 0) ? 1 : (DIR == 1 ? m0 : m0 * m1);   // interface-grid stride along DIR
   const int64_t cstride = (DIR == 0) ? 1 : (DIR == 1 ? G.n[0] : G.n[0] * G.n[1]);
-  const int64_t nd = G.n[DIR];
   const int bc = G.bc[DIR];
   const int64_t id = (DIR == 0) ? i0 : (DIR == 1 ? i1 : i2);
   // interface-grid index of this line's interface 0, and the line's cell 0
   const int64_t q0 = (i2 * m1 + i1) * m0 + i0 - id * sd;
   const int64_t line = c - id * cstride;
   double Fsum[NVAR];
-#pragma unroll
-  for (int v = 0; v < NVAR; ++v) Fsum[v] = 0.0;
-  const int idl = int(id), ndl = int(nd);
-  // The P-weighted Fbar sum over the six slots as one stencil on Rbar:
-  // sum_j P_j (Rbar_{id+3-j} - Rbar_{id+2-j}) =
+  const int idl = int(id), ndl = int(G.n[DIR]);
+  // Interior cells (slot j's interface qd = id+3-j) take the P-weighted Fbar
+  // sum over the six slots as one stencil on Rbar:
+  //   sum_j P_j (Rbar_{id+3-j} - Rbar_{id+2-j}) =
   //   ((Rbar_{id+3} - Rbar_{id-3}) - 9 (Rbar_{id+2} - Rbar_{id-2}) + 45 (Rbar_{id+1} - Rbar_{id-1})) / 60.
-  // Interior cells (slot j's interface qd = id+3-j) always take it; with
-  // periodic ends and at least six cells every cell does: qd and the Rbar
-  // stencil wrap modulo nd, and faces 0 and nd -- one physical face
+  // With periodic ends and at least six cells every cell does: qd and the
+  // Rbar stencil wrap modulo nd, and faces 0 and nd -- one physical face
   // computed twice, each copy with its own Fbar -- both add their terms to
   // the slot whose wrapped interface is 0 (their Fbar sum is the wrapped
-  // difference the stencil already holds).  Other cells (transmissive ends,
-  // short periodic lines) gather slot by slot.
+  // difference the stencil already holds).
   const bool wrap = bc == 0 && ndl >= 6;
-  const bool fast = wrap || (idl >= 3 && idl <= ndl - 4);
-  if (fast) {
+  if (wrap || (idl >= 3 && idl <= ndl - 4)) {
     auto wrapped = [ndl](int y) { return y < 0 ? y + ndl : (y >= ndl ? y - ndl : y); };
     const int64_t o1p = wrapped(idl + 1) * cstride, o1m = wrapped(idl - 1) * cstride;
     const int64_t o2p = wrapped(idl + 2) * cstride, o2m = wrapped(idl - 2) * cstride;
@@ -471,68 +513,17 @@ __device__ __forceinline__ void gather_dir(const Grid& G, int64_t c, int64_t i0,
       const double* r = Rbar + v * ncell + line;
       Fsum[v] = fma(w45, r[o1p] - r[o1m], fma(w9, r[o2p] - r[o2m], w1 * (r[o3p] - r[o3m])));
     }
-    // every kept slot adds M_j U~bar (and at j = 2, 3 its Roe-parameter
-    // adjoints); a pending slot takes its P_j Fbar term back out of the
-    // stencil and adds its own contribution instead (a short branch: the
-    // rare pending slots cost the warp little)
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-      const double Mj = c_adjM[j];
       const int x = wrapped(idl + 3 - j);
-      for (int copy = 0; copy < 2; ++copy) {
-        if (copy == 1 && x != 0) break;
-        const int qd = copy == 0 ? x : ndl;
-        const int64_t q = q0 + (int64_t)qd * sd;
-        if (pending[q]) {
-          const double Pj = c_adjP[j] * fs;
-#pragma unroll
-          for (int v = 0; v < NVAR; ++v) {
-            const double ra = (qd < ndl) ? Rbar[v * ncell + line + (int64_t)qd * cstride] : 0.0;
-            const double rb = (qd >= 1) ? Rbar[v * ncell + line + (int64_t)(qd - 1) * cstride] : 0.0;
-            Fsum[v] = fma(-Pj, ra - rb, Fsum[v]);
-            acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
-          }
-          continue;
-        }
-#pragma unroll
-        for (int v = 0; v < NVAR; ++v) acc[v] = fma(Mj, kb[(int64_t)v * nifc + q], acc[v]);
-        if (j == 2)
-#pragma unroll
-          for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(NVAR + v) * nifc + q];
-        if (j == 3)
-#pragma unroll
-          for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
-      }
+      slot_terms<NVAR>(j, q0 + (int64_t)x * sd, kb, contrib, pending, nifc, acc, rp);
+      if (x == 0 && bc == 0) slot_terms<NVAR>(j, q0 + (int64_t)ndl * sd, kb, contrib, pending, nifc, acc, rp);
     }
   } else {
-    for (int j = 0; j < 6; ++j) {
-      // interfaces qd in [0, nd] whose point j, ghost(qd - 3 + j), is cell id
-      if (bc == 0) {
-        // x = qd - 3 + j ranges over [j - 3, nd + j - 3]; x = id (mod nd)
-        int x = idl;
-        while (x - ndl >= j - 3) x -= ndl;
-        while (x < j - 3) x += ndl;
-        for (; x <= ndl + j - 3; x += ndl) {
-          const int qd = x + 3 - j;
-          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride, fs,
-                            acc, rp, Fsum);
-        }
-      } else {
-        // transmissive: points below 0 map to cell 0, points above nd-1 to nd-1
-        int lo = idl + 3 - j, hi = idl + 3 - j;
-        if (idl == 0) lo = 0;
-        if (idl == ndl - 1) hi = ndl;
-        if (lo < 0) lo = 0;
-        if (hi > ndl) hi = ndl;
-        for (int qd = lo; qd <= hi; ++qd) {
-          const int x = qd - 3 + j;
-          const int mapped = x < 0 ? 0 : (x >= ndl ? ndl - 1 : x);
-          if (mapped != idl) continue;
-          gather_slot<NVAR>(j, q0 + qd * sd, qd, contrib, kb, pending, Rbar, nifc, ncell, line, nd, cstride, fs,
-                            acc, rp, Fsum);
-        }
-      }
-    }
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) Fsum[v] = 0.0;
+    gather_edge<NVAR>(idl, ndl, bc, q0, sd, line, cstride, ncell, nifc, fs, Rbar, kb, contrib, pending, acc, rp,
+                      Fsum);
   }
   teno_adj::flux_vjp_acc<NDIM, DIR>(Uc, P, gamma, Fsum, acc);
 }
@@ -550,10 +541,10 @@ __device__ __forceinline__ void gather_dirs(const Grid& G, int64_t c, int64_t i0
 
 // out_c = a X_c + b Y_c + sum over directions and over the (interface, slot)
 // pairs whose stencil point maps to cell c (boundary ghost copies included)
-// of: the pending interfaces' contributions, M_j U~bar of the kept ones,
-// A_d(U_c)^T applied once per direction to sum_j P_j Fbar of the kept ones,
-// and the Roe-parameter map of cell c applied once to the sum of its
-// parameter adjoints.  Deterministic, no atomics.
+// of: M_j U~bar of the kept interfaces, the pending interfaces' contributions,
+// A_d(U_c)^T applied once per direction to sum_j P_j Fbar of all of them, and
+// the Roe-parameter map of cell c applied once to the sum of its parameter
+// adjoints.  Deterministic, no atomics.
 #ifndef TENO_ADJ_GATHER_MINBLOCKS
 #define TENO_ADJ_GATHER_MINBLOCKS 2
 #endif

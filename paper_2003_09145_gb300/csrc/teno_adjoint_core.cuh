@@ -52,7 +52,11 @@ TENO_HD inline void lin_weights(unsigned sel, double a[5]) {
   a[4] = -1.0 / 6.0 * o2;
 }
 
-template <int NDIM, int DIR>
+// With EXCL_P the flux term of the all-kept form, P_j A(U_j)^T Fbar
+// (P = (1,-8,37,37,-8,1)/60), is left out of every point's result: the
+// adjoint's gather adds that term for every interface alike, through one
+// stencil on the right-hand-side adjoint per cell.
+template <int NDIM, int DIR, bool EXCL_P = false>
 TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double (&alpha)[NDIM + 2],
                                   const unsigned (&sel)[NDIM + 2][2], double gamma,
                                   const double (&Fb)[NDIM + 2], double (&Ub)[6][NDIM + 2],
@@ -231,6 +235,11 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   sbb += (Hb - H) / S * Hbar;
 
   // per point: primitives -> conservative
+  if (EXCL_P) {
+    const double Pk[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
+    for (int j = 0; j < 6; ++j)
+      for (int k = 0; k < NV; ++k) Fbar[j][k] -= Pk[j] * Fb[k];
+  }
   for (int j = 0; j < 6; ++j) {
     double rhob = 0.0, Eb = 0.0, pb = 0.0, ub_[NDIM];
     for (int k = 0; k < NDIM; ++k) ub_[k] = 0.0;
@@ -573,8 +582,9 @@ TENO_HD inline void interface_vjp_kept_ifc(const RoeState<NDIM>& R, const double
 }
 
 // The whole all-kept VJP of one interface, as interface_vjp (same inputs and
-// outputs): the interface part plus P_j A(U_j)^T Fbar at every point.
-template <int NDIM, int DIR>
+// outputs): the interface part plus P_j A(U_j)^T Fbar at every point (left
+// out with EXCL_P, as in interface_vjp).
+template <int NDIM, int DIR, bool EXCL_P = false>
 TENO_HD inline void interface_vjp_kept(const double (&Up)[6][NDIM + 2], const double (&alpha)[NDIM + 2],
                                        double gamma, const double (&Fb)[NDIM + 2],
                                        double (&Ub)[6][NDIM + 2], double (&ab)[NDIM + 2]) {
@@ -591,10 +601,14 @@ TENO_HD inline void interface_vjp_kept(const double (&Up)[6][NDIM + 2], const do
   double Utb[NV], roeA[NV], roeB[NV];
   interface_vjp_kept_ifc<NDIM, DIR>(R, Ut, alpha, gamma, Fb, Utb, roeA, roeB, ab);
   for (int j = 0; j < 6; ++j) {
-    double G[NV];
-    for (int v = 0; v < NV; ++v) G[v] = P[j] * Fb[v];
-    flux_vjp<NDIM, DIR>(Up[j], gamma, G, Ub[j]);
-    for (int v = 0; v < NV; ++v) Ub[j][v] += M[j] * Utb[v];
+    if (EXCL_P) {
+      for (int v = 0; v < NV; ++v) Ub[j][v] = M[j] * Utb[v];
+    } else {
+      double G[NV];
+      for (int v = 0; v < NV; ++v) G[v] = P[j] * Fb[v];
+      flux_vjp<NDIM, DIR>(Up[j], gamma, G, Ub[j]);
+      for (int v = 0; v < NV; ++v) Ub[j][v] += M[j] * Utb[v];
+    }
   }
   for (int v = 0; v < NV; ++v) {
     Ub[2][v] += roeA[v];

@@ -85,6 +85,30 @@ extern "C" void adj_flux_vjp_acc3(int dir, const double* u, double gamma, const 
   std::memcpy(acc, A, sizeof(A));
 }
 
+// The general VJP with selections sel[5][2] (delta bits), whole (excl = 0)
+// or without the all-kept flux term P_j A(U_j)^T Fbar (excl = 1).
+template <int DIR>
+void sel_run(int excl, const double* up, const double* al, const unsigned* sl, double gamma, const double* fb,
+             double* ub, double* ab) {
+  double Up[6][5], alpha[5], Fb[5], Ub[6][5], Ab[5];
+  unsigned sel[5][2];
+  std::memcpy(Up, up, sizeof(Up));
+  std::memcpy(alpha, al, sizeof(alpha));
+  std::memcpy(Fb, fb, sizeof(Fb));
+  std::memcpy(sel, sl, sizeof(sel));
+  if (excl) teno_adj::interface_vjp<3, DIR, true>(Up, alpha, sel, gamma, Fb, Ub, Ab);
+  else teno_adj::interface_vjp<3, DIR, false>(Up, alpha, sel, gamma, Fb, Ub, Ab);
+  std::memcpy(ub, Ub, sizeof(Ub));
+  std::memcpy(ab, Ab, sizeof(Ab));
+}
+
+extern "C" void adj_interface_vjp3_sel(int dir, int excl, const double* up, const double* al, const unsigned* sel,
+                                       double gamma, const double* fb, double* ub, double* ab) {
+  if (dir == 0) sel_run<0>(excl, up, al, sel, gamma, fb, ub, ab);
+  else if (dir == 1) sel_run<1>(excl, up, al, sel, gamma, fb, ub, ab);
+  else sel_run<2>(excl, up, al, sel, gamma, fb, ub, ab);
+}
+
 // kept: 0 = the general VJP with every stencil selected, 1 = the all-kept
 // closed form, 2 = the closed form split as the kernels split it
 extern "C" void adj_interface_vjp3(int dir, int kept, const double* up, const double* al, double gamma,

@@ -32,6 +32,9 @@ def lib():
     L.adj_flux_vjp3.restype = None
     L.adj_flux_vjp_acc3.argtypes = [ctypes.c_int, P, ctypes.c_double, P, P]
     L.adj_flux_vjp_acc3.restype = None
+    L.adj_interface_vjp3_sel.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_uint),
+                                         ctypes.c_double, P, P, P]
+    L.adj_interface_vjp3_sel.restype = None
     return L
 
 
@@ -137,6 +140,34 @@ def test_split_kept_form_equals_general_vjp(lib, d):
         ub_g, _ = _vjp(lib, d, 0, Up, alpha, Fb)
         assert np.abs(ub_s - ub_g).max() <= 1e-12 * np.abs(ub_g).max()
         assert np.array_equal(ab_s, ab_k)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_general_vjp_without_flux_term(lib, d):
+    """The pending interfaces' contributions leave out P_j A(U_j)^T Fbar (the
+    gather adds it for every interface through one stencil): with any
+    selections, the reduced VJP plus that term (A^T from flux_vjp) is the
+    whole VJP."""
+    rng = np.random.default_rng(500 + d)
+    P = np.array([1, -8, 37, 37, -8, 1]) / 60.0
+    for _ in range(20):
+        Up = np.ascontiguousarray(_state(rng))
+        alpha = np.ascontiguousarray(rng.uniform(0.5, 3.0, 5))
+        Fb = np.ascontiguousarray(rng.standard_normal(5))
+        sel = np.ascontiguousarray(rng.integers(1, 8, (5, 2)).astype(np.uint32))
+        out = {}
+        for excl in (0, 1):
+            ub, ab = np.zeros((6, 5)), np.zeros(5)
+            lib.adj_interface_vjp3_sel(d, excl, _p(Up), _p(alpha), sel.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)),
+                                       GAMMA, _p(Fb), _p(ub), _p(ab))
+            out[excl] = (ub, ab)
+        back = out[1][0].copy()
+        for j in range(6):
+            AF = np.zeros(5)
+            lib.adj_flux_vjp3(d, _p(np.ascontiguousarray(Up[j])), GAMMA, _p(np.ascontiguousarray(P[j] * Fb)), _p(AF))
+            back[j] += AF
+        assert np.abs(back - out[0][0]).max() <= 1e-12 * np.abs(out[0][0]).max()
+        assert np.array_equal(out[0][1], out[1][1])
 
 
 @pytest.mark.parametrize("d", [0, 1, 2])
