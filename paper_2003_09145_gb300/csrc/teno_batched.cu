@@ -138,14 +138,14 @@ __global__ void __launch_bounds__(BLOCK) batched_stage_kernel(BatchArgs A, Schem
       } else {
         s_dt = A.dtv[p];
       }
-      s_idx = 1.0 / dxp;
+      s_idx = (1.0 / dxp) / teno::kFluxScale;   // the fluxes are stored as kFluxScale F^
     }
     __syncthreads();
     const double dt = s_dt;
     if (!(dt > 0.0)) continue;
     const double alpha[3] = {s_alpha[0], s_alpha[1], s_alpha[2]};
     const double nal[3] = {-2.0 * s_alpha[0], -2.0 * s_alpha[1], -2.0 * s_alpha[2]};
-    const double cdt = dt * s_idx;   // dt / dx, as the grid path's stage coefficient
+    const double cdt = dt * s_idx;   // dt / (30 dx), as the grid path's stage coefficient
 
     // (B) fluxes tile by tile, difference fused with the stage update
     for (int64_t i0 = 0; i0 < n; i0 += BLOCK - 1) {

@@ -121,10 +121,17 @@ __device__ __forceinline__ bool cert_keep(const CertIfc<NDIM>& C, const Scheme& 
 // cell_flux_half gives F_d(U)/2 of one cell (eq. 4.7) from its half u_d and
 // half p -- the grid path stores it per cell and direction, the one-pass
 // path forms it per stencil point, with the same rounding; closed_point adds
-// point j to F~ and U~ (sums start at zero); closed_out forms F^.  The mass
-// component of F_d/2 is m_d/2: closed_point takes it as m_d with the weights
-// P/2 (the same products, since halving is exact), so the half fluxes need
-// only the momentum and energy components (v = 1..nvar-1).
+// point j to F~ and U~; closed_out forms F^.
+//
+// The sums are kept in integer weights, 30 F~ = sum_j c_j F_j/2 with
+// c = (1,-8,37,37,-8,1) and 60 U~ = sum_j m_j U_j with m = (1,-5,10,-10,5,-1),
+// so that point 0 enters by assignment and point 5 by an add (a multiply
+// fewer per component than with the fractional weights), and every interface
+// flux is stored as 30 F^ (kFluxScale): the speeds enter closed_out halved,
+// 30 a U~ = (a/2) 60 U~, and the difference pass divides by 30 together with
+// dx (Grid::inv_dx_f).  The mass component of F_d/2 is m_d/2: closed_point
+// sums c_j m_d and closed_out halves it, so the half fluxes need only the
+// momentum and energy components (v = 1..nvar-1).
 // ---------------------------------------------------------------------------
 // cell_flux_half_ep takes E + p as given (the cell pass has it);
 // cell_flux_half forms it as E + 2 (p/2), the same value, since the
@@ -149,20 +156,31 @@ __device__ __forceinline__ void cell_flux_half(const double (&Uc)[NDIM + 2], dou
   cell_flux_half_ep<NDIM, DIR>(Uc, un, pn, fma(2.0, pn, Uc[NVAR - 1]), Fh);
 }
 
-// (Fhj[0] is not read: the mass term is P[j] m_d = (P2[j]/2) m_d.)
+// (Fhj[0] is not read: the mass sum is sum_j c_j m_d.)
 template <int NDIM, int DIR>
 __device__ __forceinline__ void closed_point(int j, const double (&Uj)[NDIM + 2], const double (&Fhj)[NDIM + 2],
                                              double (&Ft)[NDIM + 2], double (&Ut)[NDIM + 2]) {
   constexpr int NVAR = NDIM + 2;
-  const double P2[6] = {1.0 / 30.0, -8.0 / 30.0, 37.0 / 30.0, 37.0 / 30.0, -8.0 / 30.0, 1.0 / 30.0};
-  const double P1[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
-  const double Mw[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+  const double C[6] = {1.0, -8.0, 37.0, 37.0, -8.0, 1.0};
+  const double Mw[6] = {1.0, -5.0, 10.0, -10.0, 5.0, -1.0};
 #pragma unroll
   for (int v = 0; v < NVAR; ++v) {
-    Ft[v] = v == 0 ? fma(P1[j], Uj[1 + DIR], Ft[0]) : fma(P2[j], Fhj[v], Ft[v]);
-    Ut[v] = fma(Mw[j], Uj[v], Ut[v]);
+    const double f = v == 0 ? Uj[1 + DIR] : Fhj[v];
+    if (j == 0) {
+      Ft[v] = f;
+      Ut[v] = Uj[v];
+    } else if (j == 5) {
+      Ft[v] += f;
+      Ut[v] -= Uj[v];
+    } else {
+      Ft[v] = fma(C[j], f, Ft[v]);
+      Ut[v] = fma(Mw[j], Uj[v], Ut[v]);
+    }
   }
 }
+
+// The factor by which interface fluxes are stored (see above).
+constexpr double kFluxScale = 30.0;
 
 template <int NDIM, int DIR>
 __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const double (&Ut)[NDIM + 2],
@@ -174,17 +192,19 @@ __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const d
   // corrections g0 = d0 l_0.U~, gE = dE l_E.U~ enter only as
   //   gs = g0 + gE = (d0 + dE) A + (d0 - dE) B,
   //   gd = gE - g0 = -((d0 - dE) A + (d0 + dE) B)      (ngd = -gd below).
+  // Ut is 60 U~ and Ft 30 F~ (F~'s mass component 60 F~_0): with the halved
+  // speeds every term below is 30 times its value.
   double Sx = -Ut[NVAR - 1];
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) Sx = fma(R.u[k], Ut[1 + k], Sx);
   const double A = fma(R.hb2, Ut[0], -R.hb1 * Sx);
   const double B = fma(R.u[DIR], Ut[0], -Ut[1 + DIR]) * R.hic;
-  const double amid = -nal[1];
-  const double d0 = nal[1] - nal[0], dE = nal[1] - nal[NVAR - 1];
+  const double amid = -0.5 * nal[1];
+  const double d0 = 0.5 * (nal[1] - nal[0]), dE = 0.5 * (nal[1] - nal[NVAR - 1]);
   const double sg = d0 + dE, df = d0 - dE;
   const double gs = fma(sg, A, df * B);
   const double ngd = fma(df, A, sg * B);
-  out[0] = fma(amid, Ut[0], Ft[0]) + gs;
+  out[0] = fma(0.5, Ft[0], fma(amid, Ut[0], gs));
 #pragma unroll
   for (int k = 0; k < NDIM; ++k) {
     double o = fma(R.u[k], gs, fma(amid, Ut[1 + k], Ft[1 + k]));
@@ -234,8 +254,6 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
   CertIfc<NDIM> C;
   cert_begin<NDIM, DIR>(R, alpha, C);
   double Ft[NVAR], Ut[NVAR];
-#pragma unroll
-  for (int v = 0; v < NVAR; ++v) Ft[v] = Ut[v] = 0.0;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     const int64_t c = cells[j];
@@ -340,8 +358,6 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
       if (keep) {
         double Ft[NVAR], Ut[NVAR];
 #pragma unroll
-        for (int v = 0; v < NVAR; ++v) Ft[v] = Ut[v] = 0.0;
-#pragma unroll
         for (int j = 0; j < 6; ++j) {
           double Fhj[NVAR];
           cell_flux_half<NDIM, DIR>(Ux[j], un[j], pn[j], Fhj);
@@ -395,7 +411,10 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
       fchar[s] = teno5_lad<WITH_FLAGS>(vm[5][s], vm[4][s], vm[3][s], vm[2][s], vm[1][s], hp, S, fl[s][1]);
     }
     // back-projection F^ = R f^char, columns r_0 = (1, u - c e_n, H - u_n c),
-    // r_1 = (1, u, q2/2), r_t = (0, e_t, u_t), r_{nvar-1} = (1, u + c e_n, H + u_n c)
+    // r_1 = (1, u, q2/2), r_t = (0, e_t, u_t), r_{nvar-1} = (1, u + c e_n, H + u_n c),
+    // stored as kFluxScale F^ like the closed form's
+#pragma unroll
+    for (int s = 0; s < NVAR; ++s) fchar[s] *= kFluxScale;
     const double sa = fchar[0] + fchar[NVAR - 1];
     const double da = fchar[NVAR - 1] - fchar[0];
     const double rho_f = sa + fchar[1];

@@ -392,7 +392,9 @@ __global__ void __launch_bounds__(128) flux_pending_kernel(
 // L(U) = (t_0 + r_1 t_1 + r_2 t_2) / dx_0: R carries the unscaled partial
 // sum and 1/dx_0 is applied once (in the stage's coefficient, or at the end
 // of a plain right-hand side), one FP64 instruction fewer per element than
-// scaling every direction -- the passes are bound by FP64 issue.
+// scaling every direction -- the passes are bound by FP64 issue.  The
+// fluxes arrive as kFluxScale F^ (teno_flux.cuh), so that factor is
+// divided out with dx_0 (dx_0 below stands for kFluxScale dx_0).
 // MODE (a template argument, so that every load of a cell is issued before
 // its stores):
 //   kDiffFirst  R = t_0                        (first of several directions)
@@ -419,6 +421,9 @@ __global__ void __launch_bounds__(256) diff_kernel(
   const int64_t m0 = G.n[0] + (DIR == 0), m1 = G.n[1] + (DIR == 1);
   const int64_t nifc = m0 * m1 * (G.n[2] + (DIR == 2));
   const double rd = G.rdx[DIR];
+  // the interface fluxes are stored as kFluxScale F^: the last direction
+  // divides by it together with dx_0
+  const double idf = G.inv_dx[0] / kFluxScale;
   double c = 0.0;
   if (stage) {
     const double dt = *dt_ptr;
@@ -431,7 +436,7 @@ __global__ void __launch_bounds__(256) diff_kernel(
           Uout[e] = Un[e];
       return;
     }
-    c = dt * G.inv_dx[0];
+    c = dt * idf;
   }
   // The interface left of cell c = (i2 n1 + i1) n0 + i0 is (i2 m1 + i1) m0 + i0:
   // x: c plus the row index c / n0 (one more interface per row); y: c plus
@@ -465,17 +470,17 @@ __global__ void __launch_bounds__(256) diff_kernel(
         w = fma(Usrc[(1 + k) * ncell + cc], G.grav[k], w);
       }
       src[NVAR - 1] = w;
-      // L = s / dx_0 + S: a stage takes c (s + dx_0 S) with c = dt / dx_0
+      // L = s / (30 dx_0) + S: a stage takes c (s + 30 dx_0 S) with c = dt / (30 dx_0)
       if (stage)
 #pragma unroll
-        for (int v = 1; v < NVAR; ++v) s[v] = fma(G.dx[0], src[v], s[v]);
+        for (int v = 1; v < NVAR; ++v) s[v] = fma(kFluxScale * G.dx[0], src[v], s[v]);
     }
     if (MODE == kDiffFirst || MODE == kDiffAcc) {
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = s[v];
     } else if (MODE == kDiffRhs) {
 #pragma unroll
-      for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = GRAV ? fma(s[v], G.inv_dx[0], src[v]) : s[v] * G.inv_dx[0];
+      for (int v = 0; v < NVAR; ++v) R[v * ncell + cc] = GRAV ? fma(s[v], idf, src[v]) : s[v] * idf;
     } else {
       double o[NVAR];
 #pragma unroll
