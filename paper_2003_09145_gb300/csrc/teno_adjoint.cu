@@ -94,18 +94,25 @@ __device__ __forceinline__ void field_speeds(const unsigned long long* __restric
 }
 
 // Fbar of interface id of a line: R_c = -(F^_{c+1/2} - F^_{c-1/2})/dx gives
-// dJ/dF^_id = (Rbar_id [id < n] - Rbar_{id-1} [id >= 1]) / dx (eq. 2.2).
+// dJ/dF^_id = (Rbar_id [id < n] - Rbar_{id-1} [id >= 1]) / dx (eq. 2.2);
+// without fscale the bracket alone.
+template <int NVAR>
+__device__ __forceinline__ void interface_fbar(const double* __restrict__ Rbar, int64_t ncell, int64_t base,
+                                               int64_t id, int64_t nd, int64_t stride_d, double (&Fb)[NVAR]) {
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    const double ra = id < nd ? Rbar[v * ncell + base + id * stride_d] : 0.0;
+    const double rb = id >= 1 ? Rbar[v * ncell + base + (id - 1) * stride_d] : 0.0;
+    Fb[v] = ra - rb;
+  }
+}
 template <int NVAR>
 __device__ __forceinline__ void interface_fbar(const double* __restrict__ Rbar, int64_t ncell, int64_t base,
                                                int64_t id, int64_t nd, int64_t stride_d, double fscale,
                                                double (&Fb)[NVAR]) {
+  interface_fbar<NVAR>(Rbar, ncell, base, id, nd, stride_d, Fb);
 #pragma unroll
-  for (int v = 0; v < NVAR; ++v) {
-    double a = 0.0;
-    if (id < nd) a += Rbar[v * ncell + base + id * stride_d];
-    if (id >= 1) a -= Rbar[v * ncell + base + (id - 1) * stride_d];
-    Fb[v] = a * fscale;
-  }
+  for (int v = 0; v < NVAR; ++v) Fb[v] *= fscale;
 }
 
 // Block sum of asum in a fixed order into apart[blockIdx.x].
@@ -149,52 +156,41 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
   const IfcGeom<NDIM, DIR> I(G);
   double fa[NVAR], ha[NVAR], nfa[NVAR];
   field_speeds<NDIM, DIR>(alpha_bits, fa, ha, nfa);
+  // kept_roe_scaled's inputs: 60 U~ in integer weights, Fbar without the
+  // factor scale / dx (carried by the speeds instead); its ab come out times
+  // 60 dx / scale, which adj_alpha_kernel divides out of the block sums
   const double fscale = scale * G.inv_dx[DIR];
-  const double M[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+  const double Mi[6] = {1.0, -5.0, 10.0, -10.0, 5.0, -1.0};
+  const double amid = fscale * fa[1], d0 = fscale * (fa[0] - fa[1]), dE = fscale * (fa[NVAR - 1] - fa[1]);
   double asum[3] = {0.0, 0.0, 0.0};
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < I.nifc;
        q += (int64_t)gridDim.x * blockDim.x) {
     int64_t id, base, cells[6];
     I.locate(q, G, id, base, cells);
-    // Roe state from the cell pass's primitives (u/2, p/2, sqrt(rho), (E+p)/sqrt(rho))
-    double ua[NDIM], ub[NDIM];
+    // The forward pass's Roe state (roe_interface on the cell pass's
+    // primitives) and its certified FP32 test: a pass keeps every stencil
+    // exactly where the forward's closed-form pass did.  U~ is accumulated
+    // over the same stencil loads.
+    const double sr2 = aux[(NDIM + 1) * I.ncell + cells[2]], sr3 = aux[(NDIM + 1) * I.ncell + cells[3]];
+    const double sh2 = aux[(NDIM + 2) * I.ncell + cells[2]], sh3 = aux[(NDIM + 2) * I.ncell + cells[3]];
+    double su2[NDIM], su3[NDIM];
 #pragma unroll
     for (int k = 0; k < NDIM; ++k) {
-      ua[k] = 2.0 * aux[k * I.ncell + cells[2]];
-      ub[k] = 2.0 * aux[k * I.ncell + cells[3]];
+      su2[k] = aux[(NDIM + 3 + k) * I.ncell + cells[2]];
+      su3[k] = aux[(NDIM + 3 + k) * I.ncell + cells[3]];
     }
-    teno_adj::RoeState<NDIM> R;
-    teno_adj::roe_from_primitives<NDIM>(aux[(NDIM + 1) * I.ncell + cells[2]], aux[(NDIM + 1) * I.ncell + cells[3]],
-                                        aux[(NDIM + 2) * I.ncell + cells[2]], aux[(NDIM + 2) * I.ncell + cells[3]],
-                                        ua, ub, S.gamma, R);
-    if (!(R.c2 > 0.0)) atomicOr(status, teno::kStatusNonphysical);
-    // The forward's certified FP32 test on this Roe state (it equals the
-    // forward's own to a few ulps, far inside the test's 2^-20 margins, so a
-    // pass proves the forward's binary64 selections keep every stencil), with
-    // U~ accumulated over the same stencil loads.
     teno::RoeIfc<NDIM> Rf;
-#pragma unroll
-    for (int k = 0; k < NDIM; ++k) Rf.u[k] = R.ut[k];
-    Rf.q2 = R.q2;
-    Rf.H = R.H;
-    Rf.cs = R.c;
-    Rf.b1 = R.b1;
-    Rf.hb1 = 0.5 * R.b1;
-    Rf.hb2 = 0.5 * R.b2;
-    Rf.hic = 0.5 * R.ic;
-    Rf.hud = 0.5 * R.ut[DIR];
+    teno::roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, su2, su3, S, Rf, status);
     teno::CertIfc<NDIM> C;
     teno::cert_begin<NDIM, DIR>(Rf, ha, C);
     double Ut[NVAR];
-#pragma unroll
-    for (int v = 0; v < NVAR; ++v) Ut[v] = 0.0;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       double Uj[NVAR];
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) {
         Uj[v] = U[v * I.ncell + cells[j]];
-        Ut[v] = fma(M[j], Uj[v], Ut[v]);
+        Ut[v] = j == 0 ? Uj[v] : (j == 5 ? Ut[v] - Uj[v] : fma(Mi[j], Uj[v], Ut[v]));
       }
       teno::cert_point<NDIM, DIR>(j, Uj, aux[DIR * I.ncell + cells[j]], aux[NDIM * I.ncell + cells[j]], C);
     }
@@ -207,10 +203,29 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
       for (int v = 0; v < 3 * NVAR; ++v) kb[(int64_t)v * I.nifc + q] = 0.0;
       continue;
     }
+    // the VJP's Roe state: the same average, and the cells' velocity and
+    // enthalpy differences
+    teno_adj::RoeState<NDIM> R;
+    R.sa = sr2;
+    R.sb = sr3;
+    R.iS = teno::recip_pos(sr2 + sr3);
+    R.dH = sh2 * teno::recip_pos(sr2) - sh3 * teno::recip_pos(sr3);
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+      R.duh[k] = aux[k * I.ncell + cells[2]] - aux[k * I.ncell + cells[3]];
+      R.ut[k] = Rf.u[k];
+    }
+    R.q2 = Rf.q2;
+    R.H = Rf.H;
+    R.c = Rf.cs;
+    R.ic = 2.0 * Rf.hic;
+    R.ic2 = R.ic * R.ic;
+    R.b1 = Rf.b1;
+    R.b2 = 2.0 * Rf.hb2;
     double Fb[NVAR];
-    interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
+    interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, Fb);
     double Utb[NVAR], pa[NVAR], pb[NVAR], ab[NVAR];
-    teno_adj::interface_vjp_kept_roe<NDIM, DIR>(R, Ut, fa, S.gamma, Fb, Utb, pa, pb, ab);
+    teno_adj::kept_roe_scaled<NDIM, DIR>(R, Ut, amid, d0, dE, R.iS * (1.0 / 60.0), S.gamma, Fb, Utb, pa, pb, ab);
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) {
       kb[(int64_t)v * I.nifc + q] = Utb[v];
@@ -587,32 +602,37 @@ __global__ void __launch_bounds__(256, TENO_ADJ_GATHER_MINBLOCKS) adj_gather_ker
 // Sum the per-block d/dalpha of every direction in a fixed order (one block
 // of kAlphaThreads: strided partial sums, then a tree) and add their effect
 // at the arg-max cells (one thread: several speeds may share a cell).
-// apart: [ndim][nblocks][3].
+// apart: [ndim][2 nblocks][3], the kept pass's blocks first (their sums in
+// units of 60 dx_d / scale: times kscale[d]), then the general pass's.
+struct AlphaScale {
+  double k[3];
+};
 constexpr int kAlphaThreads = 256;
 template <int NDIM>
 __global__ void __launch_bounds__(kAlphaThreads) adj_alpha_kernel(const double* __restrict__ apart, int nblocks,
-                                 const unsigned long long* __restrict__ argidx,
+                                 AlphaScale kscale, const unsigned long long* __restrict__ argidx,
                                  const double* __restrict__ U, double* __restrict__ Ubar, int64_t ncell,
                                  double gamma) {
   constexpr int NVAR = NDIM + 2;
   __shared__ double red[kAlphaThreads][3];
-  __shared__ double tot[NDIM][3];
-  for (int d = 0; d < NDIM; ++d) {
-    const double* ap = apart + (int64_t)d * nblocks * 3;
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nblocks; b += kAlphaThreads)
-      for (int k = 0; k < 3; ++k) s[k] += ap[b * 3 + k];
-    for (int k = 0; k < 3; ++k) red[threadIdx.x][k] = s[k];
-    __syncthreads();
-    for (int w = kAlphaThreads / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w)
-        for (int k = 0; k < 3; ++k) red[threadIdx.x][k] += red[threadIdx.x + w][k];
+  __shared__ double tot[NDIM][2][3];
+  for (int d = 0; d < NDIM; ++d)
+    for (int h = 0; h < 2; ++h) {
+      const double* ap = apart + ((int64_t)d * 2 + h) * nblocks * 3;
+      double s[3] = {0.0, 0.0, 0.0};
+      for (int b = threadIdx.x; b < nblocks; b += kAlphaThreads)
+        for (int k = 0; k < 3; ++k) s[k] += ap[b * 3 + k];
+      for (int k = 0; k < 3; ++k) red[threadIdx.x][k] = s[k];
+      __syncthreads();
+      for (int w = kAlphaThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+          for (int k = 0; k < 3; ++k) red[threadIdx.x][k] += red[threadIdx.x + w][k];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) tot[d][h][k] = red[0][k];
       __syncthreads();
     }
-    if (threadIdx.x == 0)
-      for (int k = 0; k < 3; ++k) tot[d][k] = red[0][k];
-    __syncthreads();
-  }
   if (threadIdx.x != 0) return;
   for (int d = 0; d < NDIM; ++d)
     for (int k = 0; k < 3; ++k) {
@@ -623,7 +643,8 @@ __global__ void __launch_bounds__(kAlphaThreads) adj_alpha_kernel(const double* 
         Uc[v] = U[v * ncell + c];
         g[v] = 0.0;
       }
-      teno_adj::wave_speed_grad<NDIM>(Uc, d, k, gamma, tot[d][k], g);
+      const double s = fma(kscale.k[d], tot[d][0][k], tot[d][1][k]);
+      teno_adj::wave_speed_grad<NDIM>(Uc, d, k, gamma, s, g);
       for (int v = 0; v < NVAR; ++v) Ubar[v * ncell + c] += g[v];
     }
 }
@@ -828,7 +849,9 @@ void launch_adj_all(int nblk, int nsm, cudaStream_t st, const double* U, const d
   int64_t gb = (G.ncell + 255) / 256;
   if (gb > int64_t(nsm) * 16) gb = int64_t(nsm) * 16;
   adj_gather_kernel<NDIM><<<unsigned(gb), 256, 0, st>>>(U, aux, Rbar, A, G, S.gamma);
-  adj_alpha_kernel<NDIM><<<1, kAlphaThreads, 0, st>>>(apart, 2 * nblk, argidx, U, A.out, G.ncell, S.gamma);
+  AlphaScale ks{};
+  for (int d = 0; d < NDIM; ++d) ks.k[d] = scale * G.inv_dx[d] * (1.0 / 60.0);
+  adj_alpha_kernel<NDIM><<<1, kAlphaThreads, 0, st>>>(apart, nblk, ks, argidx, U, A.out, G.ncell, S.gamma);
 }
 
 // out = a X + b Y + scale J(U)^T Rbar (X, Y nullable; out may alias X or Y,

@@ -362,16 +362,34 @@ TENO_HD inline void flux_vjp_acc(const double (&U)[NDIM + 2], const CellPrim<NDI
 // Roe state of cells i (a) and i+1 (b) with the point quantities its
 // derivative needs.
 template <int NDIM>
+// (roe_from_weighted sets only what interface_vjp_kept_roe reads: sa, sb,
+// iS, duh, dH and the averaged state.)
 struct RoeState {
   double sa, sb, iS, ira, irb, ua[NDIM], ub[NDIM], qa, qb, Ha, Hb;
+  double duh[NDIM], dH;   // (u_a - u_b)/2, H_a - H_b
   double ut[NDIM], q2, H, c2, ic, ic2, c, b1, b2;
 };
+
+// The averaged state from sqrt(rho), (E+p)/sqrt(rho), u and the differences.
+template <int NDIM>
+TENO_HD inline void roe_average(double gamma, RoeState<NDIM>& R) {
+  const double gm1 = gamma - 1.0;
+  R.c2 = gm1 * (R.H - 0.5 * R.q2);
+#ifdef __CUDA_ARCH__
+  R.ic = rsqrt(R.c2);
+#else
+  R.ic = 1.0 / sqrt(R.c2);
+#endif
+  R.ic2 = R.ic * R.ic;
+  R.c = R.c2 * R.ic;
+  R.b1 = gm1 * R.ic2;
+  R.b2 = 0.5 * R.b1 * R.q2;
+}
 
 // From sqrt(rho), (E + p)/sqrt(rho) and u of both cells (one reciprocal each).
 template <int NDIM>
 TENO_HD inline void roe_from_primitives(double sa, double sb, double sha, double shb, const double (&ua)[NDIM],
                                         const double (&ub)[NDIM], double gamma, RoeState<NDIM>& R) {
-  const double gm1 = gamma - 1.0;
   const double rsa = recip(sa), rsb = recip(sb);
   R.sa = sa;
   R.sb = sb;
@@ -390,16 +408,31 @@ TENO_HD inline void roe_from_primitives(double sa, double sb, double sha, double
     R.q2 += R.ut[k] * R.ut[k];
   }
   R.H = (sha + shb) * R.iS;
-  R.c2 = gm1 * (R.H - 0.5 * R.q2);
-#ifdef __CUDA_ARCH__
-  R.ic = rsqrt(R.c2);
-#else
-  R.ic = 1.0 / sqrt(R.c2);
-#endif
-  R.ic2 = R.ic * R.ic;
-  R.c = R.c2 * R.ic;
-  R.b1 = gm1 * R.ic2;
-  R.b2 = 0.5 * R.b1 * R.q2;
+  for (int k = 0; k < NDIM; ++k) R.duh[k] = 0.5 * (ua[k] - ub[k]);
+  R.dH = R.Ha - R.Hb;
+  roe_average<NDIM>(gamma, R);
+}
+
+// The same from the cell pass's primitives: sqrt(rho), (E+p)/sqrt(rho), the
+// half velocities u/2 and the weighted velocities m/sqrt(rho) of both cells
+// (u~ = (w_a + w_b) / (s_a + s_b)); only the fields interface_vjp_kept_roe
+// reads are set.
+template <int NDIM>
+TENO_HD inline void roe_from_weighted(double sa, double sb, double sha, double shb, const double (&uha)[NDIM],
+                                      const double (&uhb)[NDIM], const double (&wa)[NDIM],
+                                      const double (&wb)[NDIM], double gamma, RoeState<NDIM>& R) {
+  R.sa = sa;
+  R.sb = sb;
+  R.dH = sha * recip(sa) - shb * recip(sb);
+  R.iS = recip(sa + sb);
+  R.q2 = 0.0;
+  for (int k = 0; k < NDIM; ++k) {
+    R.duh[k] = uha[k] - uhb[k];
+    R.ut[k] = (wa[k] + wb[k]) * R.iS;
+    R.q2 = fma(R.ut[k], R.ut[k], R.q2);
+  }
+  R.H = (sha + shb) * R.iS;
+  roe_average<NDIM>(gamma, R);
 }
 
 // From the conservative states of both cells.
@@ -449,17 +482,22 @@ TENO_HD inline void roe_point_vjp(double ir, const double (&u)[NDIM], double q, 
 // b's own parameters, pa and pb = (d/dsqrt(rho), d/du_0..d/du_{NDIM-1},
 // d/dH); roe_param_vjp turns them into conservative terms, so that a cell
 // reached by several interfaces applies that per-cell map once to their sum.
+//
+// kept_roe_scaled is the same computation with its inputs scaled: Ut = s U~,
+// Fb = Fbar / f, and the speeds passed as amid = f a_mid, d0 = f (a_0 -
+// a_mid), dE = f (a_E - a_mid), iSx = iS / s (iS = 1/(s_a + s_b)).  Every
+// output is bilinear in (U~, Fbar) except U~bar, which is linear in Fbar
+// alone, so U~bar, pa and pb come out unscaled and ab scaled by s / f.
 template <int NDIM, int DIR>
-TENO_HD inline void interface_vjp_kept_roe(const RoeState<NDIM>& R, const double (&Ut)[NDIM + 2],
-                                           const double (&alpha)[NDIM + 2], double gamma,
-                                           const double (&Fb)[NDIM + 2], double (&Utb)[NDIM + 2],
-                                           double (&pa)[NDIM + 2], double (&pb)[NDIM + 2],
-                                           double (&ab)[NDIM + 2]) {
+TENO_HD inline void kept_roe_scaled(const RoeState<NDIM>& R, const double (&Ut)[NDIM + 2], double amid,
+                                    double d0, double dE, double iSx, double gamma, const double (&Fb)[NDIM + 2],
+                                    double (&Utb)[NDIM + 2], double (&pa)[NDIM + 2], double (&pb)[NDIM + 2],
+                                    double (&ab)[NDIM + 2]) {
   constexpr int NV = NDIM + 2;
   constexpr int E = NDIM + 1;
   constexpr int N = DIR;
   const double gm1 = gamma - 1.0;
-  const double sa = R.sa, sb = R.sb, iS = R.iS, H = R.H;
+  const double sa = R.sa, sb = R.sb, H = R.H;
   const double q2 = R.q2, ic = R.ic, ic2 = R.ic2, c = R.c, b1 = R.b1;
   const double hb1 = 0.5 * b1, hb2 = 0.5 * R.b2, hic = 0.5 * ic;
   const double* ut = R.ut;
@@ -477,8 +515,6 @@ TENO_HD inline void interface_vjp_kept_roe(const RoeState<NDIM>& R, const double
   const double rdn = fma(un, Fb[E], Fb[1 + N]);
   const double rd = c * rdn;
   const double rho0 = rs - rd, rhoE = rs + rd;
-  const double amid = alpha[1];
-  const double d0 = alpha[0] - amid, dE = alpha[E] - amid;
   const double g0 = d0 * l0U, gE = dE * lEU;
 
   // ---- alpha ---------------------------------------------------------------
@@ -524,10 +560,11 @@ TENO_HD inline void interface_vjp_kept_roe(const RoeState<NDIM>& R, const double
   for (int k = 0; k < NDIM; ++k) utb[k] = fma(tq, ut[k], utb[k]);
   // u~ = (sa ua + sb ub)/S and H~ = (sa Ha + sb Hb)/S, S = sa + sb, so
   // d/dsa = sb (x_a - x_b)/S^2 and d/dsb = -sa (x_a - x_b)/S^2 for x = u, H
-  double Dsum = (R.Ha - R.Hb) * Hbar;
-  for (int k = 0; k < NDIM; ++k) Dsum = fma(R.ua[k] - R.ub[k], utb[k], Dsum);
-  const double tS = iS * iS * Dsum;
-  const double saS = sa * iS, sbS = sb * iS;
+  double Du = 0.0;
+  for (int k = 0; k < NDIM; ++k) Du = fma(R.duh[k], utb[k], Du);
+  const double Dsum = fma(2.0, Du, R.dH * Hbar);
+  const double tS = R.iS * iSx * Dsum;
+  const double saS = sa * iSx, sbS = sb * iSx;
   pa[0] = sb * tS;
   pb[0] = -sa * tS;
   for (int k = 0; k < NDIM; ++k) {
@@ -536,6 +573,17 @@ TENO_HD inline void interface_vjp_kept_roe(const RoeState<NDIM>& R, const double
   }
   pa[E] = saS * Hbar;
   pb[E] = sbS * Hbar;
+}
+
+template <int NDIM, int DIR>
+TENO_HD inline void interface_vjp_kept_roe(const RoeState<NDIM>& R, const double (&Ut)[NDIM + 2],
+                                           const double (&alpha)[NDIM + 2], double gamma,
+                                           const double (&Fb)[NDIM + 2], double (&Utb)[NDIM + 2],
+                                           double (&pa)[NDIM + 2], double (&pb)[NDIM + 2],
+                                           double (&ab)[NDIM + 2]) {
+  constexpr int E = NDIM + 1;
+  kept_roe_scaled<NDIM, DIR>(R, Ut, alpha[1], alpha[0] - alpha[1], alpha[E] - alpha[1], R.iS, gamma, Fb, Utb, pa,
+                             pb, ab);
 }
 
 // out += dJ/dU at one cell from the adjoints p = (d/dsqrt(rho), d/du, d/dH)

@@ -109,6 +109,41 @@ extern "C" void adj_interface_vjp3_sel(int dir, int excl, const double* up, cons
   else sel_run<2>(excl, up, al, sel, gamma, fb, ub, ab);
 }
 
+// The kept pass's scaled form (kept_roe_scaled) with U~ times s, Fbar over f
+// and the speeds times f, against the unscaled one: out[0..4] U~bar,
+// out[5..9] pa, out[10..14] pb, out[15..19] ab; both calls' results.
+extern "C" void adj_kept_scaled3(int dir, const double* up, const double* al, double gamma, const double* fb,
+                                 double s, double f, double* plain, double* scaled) {
+  double Up[6][5], alpha[5], Fb[5], Fs[5], Ut[5] = {0, 0, 0, 0, 0}, Us[5];
+  std::memcpy(Up, up, sizeof(Up));
+  std::memcpy(alpha, al, sizeof(alpha));
+  std::memcpy(Fb, fb, sizeof(Fb));
+  const double M[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+  for (int v = 0; v < 5; ++v) {
+    for (int j = 0; j < 6; ++j) Ut[v] += M[j] * Up[j][v];
+    Us[v] = s * Ut[v];
+    Fs[v] = Fb[v] / f;
+  }
+  teno_adj::RoeState<3> R;
+  teno_adj::roe_from_conservative<3>(Up[2], Up[3], gamma, R);
+  double o[4][5];
+  auto run = [&](double* out, bool sc) {
+    if (dir == 0) {
+      if (sc) teno_adj::kept_roe_scaled<3, 0>(R, Us, f * alpha[1], f * (alpha[0] - alpha[1]), f * (alpha[4] - alpha[1]), R.iS / s, gamma, Fs, o[0], o[1], o[2], o[3]);
+      else teno_adj::interface_vjp_kept_roe<3, 0>(R, Ut, alpha, gamma, Fb, o[0], o[1], o[2], o[3]);
+    } else if (dir == 1) {
+      if (sc) teno_adj::kept_roe_scaled<3, 1>(R, Us, f * alpha[1], f * (alpha[0] - alpha[1]), f * (alpha[4] - alpha[1]), R.iS / s, gamma, Fs, o[0], o[1], o[2], o[3]);
+      else teno_adj::interface_vjp_kept_roe<3, 1>(R, Ut, alpha, gamma, Fb, o[0], o[1], o[2], o[3]);
+    } else {
+      if (sc) teno_adj::kept_roe_scaled<3, 2>(R, Us, f * alpha[1], f * (alpha[0] - alpha[1]), f * (alpha[4] - alpha[1]), R.iS / s, gamma, Fs, o[0], o[1], o[2], o[3]);
+      else teno_adj::interface_vjp_kept_roe<3, 2>(R, Ut, alpha, gamma, Fb, o[0], o[1], o[2], o[3]);
+    }
+    std::memcpy(out, o, sizeof(o));
+  };
+  run(plain, false);
+  run(scaled, true);
+}
+
 // kept: 0 = the general VJP with every stencil selected, 1 = the all-kept
 // closed form, 2 = the closed form split as the kernels split it
 extern "C" void adj_interface_vjp3(int dir, int kept, const double* up, const double* al, double gamma,

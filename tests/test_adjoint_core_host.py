@@ -35,6 +35,8 @@ def lib():
     L.adj_interface_vjp3_sel.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.POINTER(ctypes.c_uint),
                                          ctypes.c_double, P, P, P]
     L.adj_interface_vjp3_sel.restype = None
+    L.adj_kept_scaled3.argtypes = [ctypes.c_int, P, P, ctypes.c_double, P, ctypes.c_double, ctypes.c_double, P, P]
+    L.adj_kept_scaled3.restype = None
     return L
 
 
@@ -168,6 +170,25 @@ def test_general_vjp_without_flux_term(lib, d):
             back[j] += AF
         assert np.abs(back - out[0][0]).max() <= 1e-12 * np.abs(out[0][0]).max()
         assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_kept_scaled_form(lib, d):
+    """The kept pass feeds the interface VJP 60 U~ (integer weights) and Fbar
+    without its factor scale / dx, carried by the speeds instead: U~bar and
+    the Roe-parameter adjoints come out unchanged, d/dalpha times s / f."""
+    rng = np.random.default_rng(600 + d)
+    for _ in range(20):
+        Up = np.ascontiguousarray(_state(rng))
+        a0, am, aE = rng.uniform(0.5, 3.0, 3)
+        alpha = np.array([a0, am, am, am, aE])
+        Fb = np.ascontiguousarray(rng.standard_normal(5))
+        s, f = 60.0, float(rng.uniform(0.01, 100.0))
+        plain, scaled = np.zeros((4, 5)), np.zeros((4, 5))
+        lib.adj_kept_scaled3(d, _p(Up), _p(alpha), GAMMA, _p(Fb), s, f, _p(plain), _p(scaled))
+        for r in range(3):
+            assert np.abs(scaled[r] - plain[r]).max() <= 1e-12 * np.abs(plain[r]).max(), r
+        assert np.abs(scaled[3] * f / s - plain[3]).max() <= 1e-12 * np.abs(plain[3]).max()
 
 
 @pytest.mark.parametrize("d", [0, 1, 2])
