@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
   const double fscale = scale * G.inv_dx[DIR];
   const double Mi[6] = {1.0, -5.0, 10.0, -10.0, 5.0, -1.0};
   const double amid = fscale * fa[1], d0 = fscale * (fa[0] - fa[1]), dE = fscale * (fa[NVAR - 1] - fa[1]);
+  const double igm1 = 1.0 / (S.gamma - 1.0);
   double asum[3] = {0.0, 0.0, 0.0};
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < I.nifc;
        q += (int64_t)gridDim.x * blockDim.x) {
@@ -218,10 +219,11 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     R.q2 = Rf.q2;
     R.H = Rf.H;
     R.c = Rf.cs;
-    R.ic = 2.0 * Rf.hic;
-    R.ic2 = R.ic * R.ic;
     R.b1 = Rf.b1;
-    R.b2 = 2.0 * Rf.hb2;
+    R.hb1 = Rf.hb1;
+    R.hb2 = Rf.hb2;
+    R.hic = Rf.hic;
+    R.b1ic2 = (Rf.b1 * Rf.b1) * igm1;   // b1 / c^2 = b1^2 / (gamma - 1)
     double Fb[NVAR];
     interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, Fb);
     double Utb[NVAR], pa[NVAR], pb[NVAR], ab[NVAR];
@@ -232,7 +234,10 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
       kb[(int64_t)(NVAR + v) * I.nifc + q] = pa[v];
       kb[(int64_t)(2 * NVAR + v) * I.nifc + q] = pb[v];
     }
-    add_alpha<NVAR>(ab, asum);
+    // the closed form's d/dalpha: the middle speeds' whole derivative in ab[1]
+    asum[0] += ab[0];
+    asum[1] += ab[1];
+    asum[2] += ab[NVAR - 1];
   }
   block_alpha_sum(asum, apart);
 }

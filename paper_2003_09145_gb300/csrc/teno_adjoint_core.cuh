@@ -368,6 +368,7 @@ struct RoeState {
   double sa, sb, iS, ira, irb, ua[NDIM], ub[NDIM], qa, qb, Ha, Hb;
   double duh[NDIM], dH;   // (u_a - u_b)/2, H_a - H_b
   double ut[NDIM], q2, H, c2, ic, ic2, c, b1, b2;
+  double hb1, hb2, hic, b1ic2;   // b1/2, b2/2, 1/(2c), b1/c^2
 };
 
 // The averaged state from sqrt(rho), (E+p)/sqrt(rho), u and the differences.
@@ -384,6 +385,10 @@ TENO_HD inline void roe_average(double gamma, RoeState<NDIM>& R) {
   R.c = R.c2 * R.ic;
   R.b1 = gm1 * R.ic2;
   R.b2 = 0.5 * R.b1 * R.q2;
+  R.hb1 = 0.5 * R.b1;
+  R.hb2 = 0.5 * R.b2;
+  R.hic = 0.5 * R.ic;
+  R.b1ic2 = R.b1 * R.ic2;
 }
 
 // From sqrt(rho), (E + p)/sqrt(rho) and u of both cells (one reciprocal each).
@@ -498,8 +503,8 @@ TENO_HD inline void kept_roe_scaled(const RoeState<NDIM>& R, const double (&Ut)[
   constexpr int N = DIR;
   const double gm1 = gamma - 1.0;
   const double sa = R.sa, sb = R.sb, H = R.H;
-  const double q2 = R.q2, ic = R.ic, ic2 = R.ic2, c = R.c, b1 = R.b1;
-  const double hb1 = 0.5 * b1, hb2 = 0.5 * R.b2, hic = 0.5 * ic;
+  const double q2 = R.q2, c = R.c, b1 = R.b1;
+  const double hb1 = R.hb1, hb2 = R.hb2, hic = R.hic;
   const double* ut = R.ut;
   const double un = ut[N];
 
@@ -513,21 +518,19 @@ TENO_HD inline void kept_roe_scaled(const RoeState<NDIM>& R, const double (&Ut)[
   double rs = fma(H, Fb[E], Fb[0]);
   for (int k = 0; k < NDIM; ++k) rs = fma(ut[k], Fb[1 + k], rs);
   const double rdn = fma(un, Fb[E], Fb[1 + N]);
-  const double rd = c * rdn;
-  const double rho0 = rs - rd, rhoE = rs + rd;
-  const double g0 = d0 * l0U, gE = dE * lEU;
+  const double rho0 = fma(-c, rdn, rs), rhoE = fma(c, rdn, rs);
 
   // ---- alpha ---------------------------------------------------------------
   double FU = Fb[0] * Ut[0];
   for (int v = 1; v < NV; ++v) FU = fma(Fb[v], Ut[v], FU);
-  for (int s = 0; s < NV; ++s) ab[s] = 0.0;
+  for (int s = 1; s < NV - 1; ++s) ab[s] = 0.0;
   ab[0] = rho0 * l0U;
   ab[E] = rhoE * lEU;
   ab[1] = FU - ab[0] - ab[E];
 
   // ---- U~ bar = a_mid Fb + d0 rho0 l_0 + dE rhoE l_E ---------------------------
-  const double w0 = d0 * rho0, wE = dE * rhoE;
-  const double sX = w0 + wE, dX = w0 - wE;
+  const double wE = dE * rhoE;
+  const double sX = fma(d0, rho0, wE), dX = fma(d0, rho0, -wE);
   const double hb1sX = hb1 * sX, hicdX = hic * dX;
   Utb[0] = fma(amid, Fb[0], fma(hb2, sX, un * hicdX));
   for (int k = 0; k < NDIM; ++k) {
@@ -545,18 +548,21 @@ TENO_HD inline void kept_roe_scaled(const RoeState<NDIM>& R, const double (&Ut)[
   //   b2bar = sX U~_0 / 2,   b1bar = -sX Sx / 2 + q2 b2bar / 2,
   //   cbar  = dX (U~_{1+n} - un U~_0) / (2 c^2) + (gE - g0)(Fb_{1+n} + un Fb_E),
   // and U~_{1+n} - un U~_0 = -2 c B, so the first term of cbar is -dX B / c.
+  // fchar_0 = g0 = d0 l_0.U~ and fchar_E = gE = dE l_E.U~ enter as their
+  // sum fs and difference fd
   double utb[NDIM];
-  const double fs = g0 + gE, fd = gE - g0;
+  const double gE = dE * lEU;
+  const double fs = fma(d0, l0U, gE), fd = fma(-d0, l0U, gE);
   for (int k = 0; k < NDIM; ++k) utb[k] = fma(-hb1sX, Ut[1 + k], Fb[1 + k] * fs);
-  utb[N] += fma(hicdX, Ut[0], c * Fb[E] * fd);
-  const double b2b = 0.5 * sX * Ut[0];
-  const double b1b = fma(0.5 * q2, b2b, -0.5 * sX * Sx);
-  const double cb = fma(-(ic * dX), Bx, fd * rdn);
-  double q2b = hb1 * b2b;
-  const double c2b = fma(-(b1 * ic2), b1b, hic * cb);
+  utb[N] = fma(hicdX, Ut[0], fma(c * Fb[E], fd, utb[N]));
+  const double hsX = 0.5 * sX;
+  const double b2b = hsX * Ut[0];
+  const double b1b = fma(0.5 * q2, b2b, -hsX * Sx);
+  const double cb = fma(-2.0 * hicdX, Bx, fd * rdn);   // ic dX = 2 hic dX
+  const double c2b = fma(-R.b1ic2, b1b, hic * cb);
   const double Hbar = fma(gm1, c2b, Fb[E] * fs);
-  q2b = fma(-0.5 * gm1, c2b, q2b);
-  const double tq = 2.0 * q2b;
+  // twice the q2 adjoint: 2 (b1/2 b2bar - (gamma-1)/2 c2bar)
+  const double tq = fma(-gm1, c2b, b1 * b2b);
   for (int k = 0; k < NDIM; ++k) utb[k] = fma(tq, ut[k], utb[k]);
   // u~ = (sa ua + sb ub)/S and H~ = (sa Ha + sb Hb)/S, S = sa + sb, so
   // d/dsa = sb (x_a - x_b)/S^2 and d/dsb = -sa (x_a - x_b)/S^2 for x = u, H
