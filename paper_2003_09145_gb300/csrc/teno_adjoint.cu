@@ -19,9 +19,11 @@
 //                        of the two Roe cells' parameters go to kb_d; the
 //                        rest is marked pending;
 //     list passes      : the pending interfaces in one list, index order;
-//     adj_general_kernel: the listed interfaces: the selections by the forward
-//                        pass's binary64 decisions, then the general VJP; the
-//                        six cells' contributions go to contrib_d;
+//     adj_select_kernel: the listed interfaces' selections by the forward
+//                        pass's binary64 decisions;
+//     adj_general_kernel: the listed interfaces' general VJP with those
+//                        selections; the six cells' contributions go to
+//                        contrib_d;
 //   adj_gather_kernel: one thread per cell sums, over every direction, the
 //                      contributions of every (interface, stencil slot) that
 //                      maps to it (boundary ghost copies included) and applies
@@ -342,23 +344,112 @@ __global__ void __launch_bounds__(kListThreads) adj_scatter_kernel(const unsigne
   }
 }
 
-// The listed interfaces, one thread each: the selections by the forward
-// pass's own binary64 decisions, then the general VJP (or the closed form
-// where every stencil is kept after all); the six cells' contributions, less
-// the all-kept flux term P_j A(U_j)^T Fbar that the gather adds for every
-// interface, go to contrib[6 nvar][nifc].
+// A stable two-way partition of the list by the selections: the interfaces
+// that keep every stencil after all (the certificate is conservative) first,
+// in list order, then the others -- so that each kind of VJP runs on full
+// warps.  The length n is read on the device; block b takes its fixed,
+// contiguous range of 32-entry chunks, as in the list passes above.
+//   adj_part_count_kernel  : block b counts its all-kept entries;
+//   adj_scan_kernel        : their offsets and total nA;
+//   adj_part_scatter_kernel: all-kept entry k of block b goes to boff[b] + k,
+//                            other entry k to nA + (first index of b - boff[b]) + k.
+__device__ __forceinline__ bool all_kept_sel(uint32_t w, int nvar) { return w == (1u << (6 * nvar)) - 1u; }
+
+__global__ void __launch_bounds__(kListThreads) adj_part_count_kernel(const uint32_t* __restrict__ sel,
+                                                                       const int* __restrict__ count, int nvar,
+                                                                       int* __restrict__ bcount) {
+  __shared__ int wsum[kListThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t n = *count;
+  int64_t c0, c1;
+  chunk_range((n + 31) / 32, c0, c1);
+  int cnt = 0;
+  for (int64_t c = c0 + wid; c < c1; c += kListThreads / 32) {
+    const int64_t i = c * 32 + lane;
+    cnt += __popc(__ballot_sync(0xffffffffu, i < n && all_kept_sel(sel[i], nvar)));
+  }
+  if (lane == 0) wsum[wid] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kListThreads / 32; ++w) t += wsum[w];
+    bcount[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kListThreads) adj_part_scatter_kernel(
+    const uint32_t* __restrict__ list, const uint32_t* __restrict__ sel, const int* __restrict__ count, int nvar,
+    const int* __restrict__ boff, const int* __restrict__ nkept, uint32_t* __restrict__ list2,
+    uint32_t* __restrict__ sel2) {
+  __shared__ int wa[kListThreads / 32], wg[kListThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t n = *count;
+  const int64_t nA = *nkept;
+  int64_t c0, c1;
+  chunk_range((n + 31) / 32, c0, c1);
+  int64_t runA = boff[blockIdx.x];
+  int64_t runG = nA + c0 * 32 - runA;
+  for (int64_t cb = c0; cb < c1; cb += kListThreads / 32) {
+    const int64_t c = cb + wid;
+    const int64_t i = c * 32 + lane;
+    const bool in = c < c1 && i < n;
+    const uint32_t w = in ? sel[i] : 0u;
+    const bool a = in && all_kept_sel(w, nvar);
+    const bool g = in && !a;
+    const unsigned ma = __ballot_sync(0xffffffffu, a), mg = __ballot_sync(0xffffffffu, g);
+    if (lane == 0) {
+      wa[wid] = __popc(ma);
+      wg[wid] = __popc(mg);
+    }
+    __syncthreads();
+    int ba = 0, bg = 0, ta = 0, tg = 0;
+    for (int k = 0; k < kListThreads / 32; ++k) {
+      ba += k < wid ? wa[k] : 0;
+      bg += k < wid ? wg[k] : 0;
+      ta += wa[k];
+      tg += wg[k];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (a) {
+      const int64_t pos = runA + ba + __popc(ma & below);
+      list2[pos] = list[i];
+      sel2[pos] = w;
+    } else if (g) {
+      const int64_t pos = runG + bg + __popc(mg & below);
+      list2[pos] = list[i];
+      sel2[pos] = w;
+    }
+    runA += ta;
+    runG += tg;
+    __syncthreads();
+  }
+}
+
+// The listed interfaces in two passes, so that the VJP runs on full warps
+// (the forward's cutoff decisions branch per field and lane; the VJP with
+// the selections fixed does not branch):
+//   adj_select_kernel: one thread per listed interface: the characteristic
+//                      path of the forward pass (the same binary64 decisions
+//                      its pending pass takes on these very interfaces, as the
+//                      kept pass ran the forward's certificate) -> the ten
+//                      3-bit selections packed into sel[i];
+//   partition passes  : the list reordered, those that keep every stencil
+//                      after all first (below);
+//   adj_general_kernel: one thread per listed interface: the closed-form VJP
+//                      for the first kind, the general VJP with the
+//                      selections for the rest; the six cells' contributions,
+//                      less the all-kept flux term P_j A(U_j)^T Fbar that the
+//                      gather adds for every interface, go to
+//                      contrib[6 nvar][nifc].
 template <int NDIM, int DIR>
-__global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
+__global__ void __launch_bounds__(kAdjThreads) adj_select_kernel(
     const double* __restrict__ U, const double* __restrict__ aux,
-    const unsigned long long* __restrict__ alpha_bits, const double* __restrict__ Rbar, double scale,
-    double* __restrict__ contrib, const uint32_t* __restrict__ list, const int* __restrict__ count,
-    double* __restrict__ apart, int* __restrict__ status, Grid G, Scheme S) {
+    const unsigned long long* __restrict__ alpha_bits, const uint32_t* __restrict__ list,
+    const int* __restrict__ count, uint32_t* __restrict__ sel, int* __restrict__ status, Grid G, Scheme S) {
   constexpr int NVAR = NDIM + 2;
   const IfcGeom<NDIM, DIR> I(G);
   double fa[NVAR], ha[NVAR], nfa[NVAR];
   field_speeds<NDIM, DIR>(alpha_bits, fa, ha, nfa);
-  const double fscale = scale * G.inv_dx[DIR];
-  double asum[3] = {0.0, 0.0, 0.0};
   const int64_t n = *count;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = list[i];
@@ -366,15 +457,38 @@ __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
     I.locate(q, G, id, base, cells);
     double fout[NVAR];
     unsigned fl[NVAR][2];
-    teno::interface_flux<NDIM, DIR, false, teno::kFluxSelect>(U, aux, I.ncell, cells, 0u, ha, nfa, S, fout, fl,
-                                                              status);
+    teno::interface_flux<NDIM, DIR, false, teno::kFluxChar>(U, aux, I.ncell, cells, 0u, ha, nfa, S, fout, fl,
+                                                            status);
+    uint32_t w = 0;
+#pragma unroll
+    for (int f = 0; f < NVAR; ++f) w |= ((fl[f][0] & 7u) | ((fl[f][1] & 7u) << 3)) << (6 * f);
+    sel[i] = w;
+  }
+}
+
+template <int NDIM, int DIR>
+__global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
+    const double* __restrict__ U, const unsigned long long* __restrict__ alpha_bits,
+    const double* __restrict__ Rbar, double scale, double* __restrict__ contrib,
+    const uint32_t* __restrict__ list, const int* __restrict__ count, const int* __restrict__ nkept,
+    const uint32_t* __restrict__ selw, double* __restrict__ apart, Grid G, Scheme S) {
+  constexpr int NVAR = NDIM + 2;
+  const IfcGeom<NDIM, DIR> I(G);
+  double fa[NVAR], ha[NVAR], nfa[NVAR];
+  field_speeds<NDIM, DIR>(alpha_bits, fa, ha, nfa);
+  const double fscale = scale * G.inv_dx[DIR];
+  double asum[3] = {0.0, 0.0, 0.0};
+  const int64_t n = *count, nA = *nkept;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = list[i];
+    int64_t id, base, cells[6];
+    I.locate(q, G, id, base, cells);
+    const uint32_t w = selw[i];
     unsigned sel[NVAR][2];
-    bool all_kept = true;
 #pragma unroll
     for (int f = 0; f < NVAR; ++f) {
-      sel[f][0] = fl[f][0] & 7u;
-      sel[f][1] = fl[f][1] & 7u;
-      all_kept = all_kept && sel[f][0] == 7u && sel[f][1] == 7u;
+      sel[f][0] = (w >> (6 * f)) & 7u;
+      sel[f][1] = (w >> (6 * f + 3)) & 7u;
     }
     double Up[6][NVAR];
 #pragma unroll
@@ -384,7 +498,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
     double Fb[NVAR];
     interface_fbar<NVAR>(Rbar, I.ncell, base, id, I.nd, I.stride_d, fscale, Fb);
     double Ub[6][NVAR], ab[NVAR];
-    if (all_kept)
+    if (i < nA)   // the partition puts the all-kept interfaces first
       teno_adj::interface_vjp_kept<NDIM, DIR, true>(Up, fa, S.gamma, Fb, Ub, ab);
     else
       teno_adj::interface_vjp<NDIM, DIR, true>(Up, fa, sel, S.gamma, Fb, Ub, ab);
@@ -720,8 +834,8 @@ struct AdjLayout {
   static constexpr size_t kStage = 128;
   size_t status = 0, dt = 8, alpha = 64, argidx = 512;
   size_t aux = 0, aux_bytes = 0, cand = 0, fh = 0, kb = 0, kb_bytes = 0, contrib = 0, contrib_bytes = 0,
-         pending = 0, pending_bytes = 0, list = 0, lcount = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0, B2 = 0,
-         total = 0;
+         pending = 0, pending_bytes = 0, list = 0, sel = 0, lcount = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0,
+         B2 = 0, total = 0;
 };
 
 AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
@@ -750,10 +864,15 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
   L.pending = off;
   L.pending_bytes = round_up(size_t(maxifc));
   off += g->ndim * L.pending_bytes;
-  L.list = off;   // pending list (recomputed forward stages; the adjoint's general pass)
-  off += round_up(sizeof(uint32_t) * size_t(maxifc));
-  L.lcount = off;   // the general pass's per-block counts, offsets and total
-  off += round_up(sizeof(int) * (2 * size_t(adj_list_blocks(nsm)) + 1));
+  // pending list (recomputed forward stages; the adjoint's general pass) and
+  // its partitioned copy, the listed interfaces' packed selections and
+  // theirs (each in two halves of 2 maxifc + 2 entries)
+  L.list = off;
+  off += round_up(sizeof(uint32_t) * (2 * size_t(maxifc) + 2));
+  L.sel = off;
+  off += round_up(sizeof(uint32_t) * (2 * size_t(maxifc) + 2));
+  L.lcount = off;   // the list passes' per-block counts, offsets, total and all-kept total
+  off += round_up(sizeof(int) * (2 * size_t(adj_list_blocks(nsm)) + 2));
   L.apart = off;   // [ndim][2 blocks][3]: d/dalpha per block of the kept and general passes
   off += round_up(sizeof(double) * 3 * 2 * size_t(adj_blocks(nsm)) * g->ndim);
   if (op == TENO_OP_RK3_ADJOINT) {
@@ -811,8 +930,8 @@ bool al(const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 
 template <int NDIM, int DIR>
 void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const double* aux,
                     const unsigned long long* alpha, const double* Rbar, double scale, double* kb,
-                    double* contrib, unsigned char* pending, uint32_t* list, int* lcount, double* apart,
-                    int* status, const Grid& G, const Scheme& S) {
+                    double* contrib, unsigned char* pending, uint32_t* list, int* lcount, uint32_t* sel,
+                    double* apart, int* status, const Grid& G, const Scheme& S) {
   adj_kept_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
                                                           status, G, S);
   int64_t nifc = 1;
@@ -824,8 +943,17 @@ void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const d
   adj_count_kernel<<<lblk, kListThreads, 0, st>>>(pending, nifc, bcount);
   adj_scan_kernel<<<1, kListThreads, 0, st>>>(bcount, lblk, boff, total);
   adj_scatter_kernel<<<lblk, kListThreads, 0, st>>>(pending, nifc, boff, list);
-  adj_general_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, contrib, list, total,
-                                                             apart + 3 * nblk, status, G, S);
+  adj_select_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, list, total, sel, status, G, S);
+  // the partition reuses the counts and offsets; its own total (the number
+  // of all-kept entries) goes to the slot after the list's
+  int* nkept = total + 1;
+  uint32_t* list2 = list + (nifc + 1) / 2 * 2;   // second half of the list region
+  uint32_t* sel2 = sel + (nifc + 1) / 2 * 2;
+  adj_part_count_kernel<<<lblk, kListThreads, 0, st>>>(sel, total, NDIM + 2, bcount);
+  adj_scan_kernel<<<1, kListThreads, 0, st>>>(bcount, lblk, boff, nkept);
+  adj_part_scatter_kernel<<<lblk, kListThreads, 0, st>>>(list, sel, total, NDIM + 2, boff, nkept, list2, sel2);
+  adj_general_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, alpha, Rbar, scale, contrib, list2, total, nkept,
+                                                             sel2, apart + 3 * nblk, G, S);
 }
 
 template <int NDIM>
@@ -835,17 +963,18 @@ void launch_adj_all(int nblk, int nsm, cudaStream_t st, const double* U, const d
                     const Scheme& S) {
   auto* list = reinterpret_cast<uint32_t*>(ws + L.list);
   auto* lcount = reinterpret_cast<int*>(ws + L.lcount);
+  auto* sel = reinterpret_cast<uint32_t*>(ws + L.sel);
   double* apart = reinterpret_cast<double*>(ws + L.apart);
   for (int d = 0; d < NDIM; ++d) {
     double* kb = reinterpret_cast<double*>(ws + L.kb + d * L.kb_bytes);
     double* contrib = reinterpret_cast<double*>(ws + L.contrib + d * L.contrib_bytes);
     auto* pending = reinterpret_cast<unsigned char*>(ws + L.pending + d * L.pending_bytes);
     double* ap = apart + 6 * nblk * d;
-    if (d == 0) launch_adj_dir<NDIM, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, ap, status, G, S);
+    if (d == 0) launch_adj_dir<NDIM, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S);
     if constexpr (NDIM > 1)
-      if (d == 1) launch_adj_dir<NDIM, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, ap, status, G, S);
+      if (d == 1) launch_adj_dir<NDIM, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S);
     if constexpr (NDIM > 2)
-      if (d == 2) launch_adj_dir<NDIM, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, ap, status, G, S);
+      if (d == 2) launch_adj_dir<NDIM, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S);
     A.kb[d] = kb;
     A.contrib[d] = contrib;
     A.pending[d] = pending;
