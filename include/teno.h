@@ -323,6 +323,23 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n,
                                   void* stream);
 
 /*
+ * teno_rk3_step_adjoint_staged -- the same reverse step with the stages U1,
+ * U2 of eq. 4.1-4.2 supplied by the caller (as teno_rk3_stage_end wrote
+ * them for this step with dt_fixed = dt) instead of recomputed: the result
+ * equals teno_rk3_step_adjoint's bit for bit when they are.  A rollout that
+ * replays its steps anyway keeps the stages and saves two right-hand-side
+ * evaluations per reverse step.
+ *   U_n, U1, U2 : [in] device, nvar * ncell doubles.
+ *   Ubar_n      : [out] may alias Ubar_next, not U_n, U1 or U2.
+ *   ws          : >= teno_adjoint_workspace_bytes(g, TENO_OP_RK3_ADJOINT).
+ */
+teno_status teno_rk3_step_adjoint_staged(const teno_grid* g, const double* U_n,
+                                         const double* U1, const double* U2,
+                                         double dt, const double* Ubar_next,
+                                         double* Ubar_n, void* ws,
+                                         size_t ws_bytes, void* stream);
+
+/*
  * teno_get_device_status -- waits for `stream`, then returns in *status the
  * status recorded on the device in workspace `ws` since the last call
  * (TENO_OK, TENO_ERR_NONPHYSICAL or TENO_ERR_TIMEOUT) and clears it.

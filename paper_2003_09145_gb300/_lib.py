@@ -92,6 +92,8 @@ SIGNATURES = [
     ("teno_adjoint_workspace_bytes", ctypes.c_size_t, [_GP, ctypes.c_int]),
     ("teno_rhs_adjoint", ctypes.c_int, [_GP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     ("teno_rk3_step_adjoint", ctypes.c_int, [_GP, _VP, ctypes.c_double, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    ("teno_rk3_step_adjoint_staged", ctypes.c_int,
+     [_GP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     ("teno_batch_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(TenoBatch)]),
     ("teno_batch_prepare", ctypes.c_int, [ctypes.POINTER(TenoBatch), ctypes.POINTER(ctypes.c_int64), _VP,
                                           ctypes.c_size_t, _VP]),

@@ -394,23 +394,43 @@ def rhs_adjoint(grid: EulerGrid, U: torch.Tensor, dUdt_bar: torch.Tensor, U_bar:
 
 
 class AdjointStepper:
-    """Reverse of fixed-dt SSP-RK3 steps (``teno_rk3_step_adjoint``)."""
+    """Reverse of fixed-dt SSP-RK3 steps (``teno_rk3_step_adjoint``; with the
+    step's stages U1, U2 given, ``teno_rk3_step_adjoint_staged``)."""
 
     def __init__(self, grid: EulerGrid, device="cuda"):
         self.grid = grid
         nb = grid.lib.teno_adjoint_workspace_bytes(ctypes.byref(grid.c), _lib.OP_RK3_ADJOINT)
         self.ws = alloc_workspace(nb, torch.device(device))
 
-    def step(self, U_n: torch.Tensor, dt: float, Ubar_next: torch.Tensor, Ubar_n: torch.Tensor | None = None):
+    def step(self, U_n: torch.Tensor, dt: float, Ubar_next: torch.Tensor, Ubar_n: torch.Tensor | None = None,
+             stages=None):
         g = self.grid
         out = torch.empty_like(Ubar_next) if Ubar_n is None else Ubar_n
-        st = g.lib.teno_rk3_step_adjoint(ctypes.byref(g.c), _ptr(U_n), float(dt), _ptr(Ubar_next), _ptr(out),
-                                         _ptr(self.ws), self.ws.numel(), _stream_ptr())
-        _lib.check(st, "teno_rk3_step_adjoint")
+        if stages is None:
+            st = g.lib.teno_rk3_step_adjoint(ctypes.byref(g.c), _ptr(U_n), float(dt), _ptr(Ubar_next), _ptr(out),
+                                             _ptr(self.ws), self.ws.numel(), _stream_ptr())
+            _lib.check(st, "teno_rk3_step_adjoint")
+        else:
+            U1, U2 = stages
+            st = g.lib.teno_rk3_step_adjoint_staged(ctypes.byref(g.c), _ptr(U_n), _ptr(U1), _ptr(U2), float(dt),
+                                                    _ptr(Ubar_next), _ptr(out), _ptr(self.ws), self.ws.numel(),
+                                                    _stream_ptr())
+            _lib.check(st, "teno_rk3_step_adjoint_staged")
         return out
 
     def status(self) -> int:
         return device_status(self.ws)
+
+
+def rk3_step_stages(engine: "SlabEngine", U_n: torch.Tensor, dt: float):
+    """One fixed-dt SSP-RK3 step from U_n through the staged entry points
+    (eq. 4.1-4.3), keeping its stages: returns (U1, U2, U_next); U_n is left
+    unchanged."""
+    U1, U2, Un1 = torch.empty_like(U_n), torch.empty_like(U_n), torch.empty_like(U_n)
+    for k, (Uin, Uout) in enumerate(((U_n, U1), (U1, U2), (U2, Un1)), start=1):
+        engine.begin(Uin)
+        engine.end(k, Uin, U_n, Uout, dt_fixed=dt)
+    return U1, U2, Un1
 
 
 class TenoRK3Rollout(torch.autograd.Function):
@@ -419,11 +439,15 @@ class TenoRK3Rollout(torch.autograd.Function):
 
     Forward keeps one state every ``checkpoint_every`` steps; backward replays
     each segment from its checkpoint (storing the segment's states) and runs the
-    step adjoints in reverse (RK-stage checkpointing: the stages themselves are
-    recomputed inside ``teno_rk3_step_adjoint``)."""
+    step adjoints in reverse.  With ``keep_stages`` the replay also keeps each
+    step's stages U1, U2 (three states per step of a segment) and the step
+    adjoints take them (``teno_rk3_step_adjoint_staged``); otherwise they are
+    recomputed inside ``teno_rk3_step_adjoint``.  Both give the same gradient
+    bit for bit."""
 
     @staticmethod
-    def forward(ctx, U0: torch.Tensor, grid: EulerGrid, steps: int, dt: float, checkpoint_every: int = 0):
+    def forward(ctx, U0: torch.Tensor, grid: EulerGrid, steps: int, dt: float, checkpoint_every: int = 0,
+                keep_stages: bool = True):
         k = checkpoint_every if checkpoint_every > 0 else max(1, int(round(steps ** 0.5)))
         solver = Solver(grid, device=U0.device)
         U = U0.detach().clone()
@@ -433,6 +457,7 @@ class TenoRK3Rollout(torch.autograd.Function):
             if (n + 1) % k == 0 and n + 1 < steps:
                 ckpts[n + 1] = U.clone()
         ctx.grid, ctx.steps, ctx.dt, ctx.k, ctx.ckpts, ctx.solver = grid, steps, dt, k, ckpts, solver
+        ctx.keep_stages = bool(keep_stages)
         return U
 
     @staticmethod
@@ -440,23 +465,31 @@ class TenoRK3Rollout(torch.autograd.Function):
         grid, steps, dt, k = ctx.grid, ctx.steps, ctx.dt, ctx.k
         adj = AdjointStepper(grid, device=Ubar.device)
         solver = ctx.solver
+        engine = SlabEngine(grid, device=Ubar.device) if ctx.keep_stages else None
         B = Ubar.detach().contiguous().clone()
         seg_starts = sorted(ctx.ckpts)
         for s0 in reversed(seg_starts):
             s1 = min(s0 + k, steps)
-            states = [ctx.ckpts[s0].clone()]
-            for _ in range(s0, s1 - 1):
-                U = states[-1].clone()
-                solver.step(U, float("inf"), dt_fixed=dt)
-                states.append(U)
+            states, stages = [ctx.ckpts[s0].clone()], []
+            for _ in range(s0, s1):
+                if engine is not None:
+                    U1, U2, Un1 = rk3_step_stages(engine, states[-1], dt)
+                    stages.append((U1, U2))
+                    states.append(Un1)
+                elif len(states) < s1 - s0:
+                    U = states[-1].clone()
+                    solver.step(U, float("inf"), dt_fixed=dt)
+                    states.append(U)
             for n in range(s1 - 1, s0 - 1, -1):
-                adj.step(states[n - s0], dt, B, B)
-        return B, None, None, None, None
+                adj.step(states[n - s0], dt, B, B, stages=stages[n - s0] if engine is not None else None)
+            del states, stages
+        return B, None, None, None, None, None
 
 
-def rollout(U0: torch.Tensor, grid: EulerGrid, steps: int, dt: float, checkpoint_every: int = 0) -> torch.Tensor:
+def rollout(U0: torch.Tensor, grid: EulerGrid, steps: int, dt: float, checkpoint_every: int = 0,
+            keep_stages: bool = True) -> torch.Tensor:
     """Differentiable fixed-dt rollout (see TenoRK3Rollout)."""
-    return TenoRK3Rollout.apply(U0, grid, steps, dt, checkpoint_every)
+    return TenoRK3Rollout.apply(U0, grid, steps, dt, checkpoint_every, keep_stages)
 
 
 # ----------------------------------------------------------------------------

@@ -1031,6 +1031,29 @@ teno_status lincomb(double* out, double a, const double* x, double b, const doub
   return cudaGetLastError() == cudaSuccess ? TENO_OK : TENO_ERR_CUDA;
 }
 
+// The reverse of eq. 4.3 -> 4.2 -> 4.1 from the stage inputs U_n, U1, U2;
+// with `cells`, every stage input gets its cell pass here, otherwise the
+// forward recomputation has left those of U_n and U1 in stage slots 0, 1.
+teno_status reverse_stages(const teno_grid* g, const AdjLayout& L, char* w, const double* U_n, const double* U1,
+                           const double* U2, bool cells, double dt, const double* Ubar_next, double* Ubar_n,
+                           cudaStream_t st) {
+  const int64_t ntot = int64_t(g->ndim + 2) * g->n[0] * g->n[1] * g->n[2];
+  double* B1 = reinterpret_cast<double*>(w + L.B1);
+  double* B2 = reinterpret_cast<double*>(w + L.B2);
+  teno_status s;
+  // reverse of eq. 4.3: B2 = 2/3 Ubar' + 2/3 dt J(U2)^T Ubar'
+  if ((s = adjoint_sequence(g, L, w, 2, true, U2, Ubar_next, 2.0 / 3.0 * dt, B2, Ubar_next, 2.0 / 3.0, nullptr,
+                            0.0, st)) != TENO_OK)
+    return s;
+  // Ubar_n = 1/3 Ubar' + 3/4 B2 (eq. 4.3 and 4.2 reach U^n directly)
+  if ((s = lincomb(Ubar_n, 1.0 / 3.0, Ubar_next, 0.75, B2, ntot, st)) != TENO_OK) return s;
+  // reverse of eq. 4.2: B1 = 1/4 B2 + 1/4 dt J(U1)^T B2
+  if ((s = adjoint_sequence(g, L, w, 1, cells, U1, B2, 0.25 * dt, B1, B2, 0.25, nullptr, 0.0, st)) != TENO_OK)
+    return s;
+  // reverse of eq. 4.1: Ubar_n += B1 + dt J(U_n)^T B1
+  return adjoint_sequence(g, L, w, 0, cells, U_n, B1, dt, Ubar_n, Ubar_n, 1.0, B1, 1.0, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1064,12 +1087,9 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double 
   if (!ws || !al(ws, kAlign) || ws_bytes < L.total || !is_dev(ws)) return TENO_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
-  const int64_t ntot = int64_t(g->ndim + 2) * g->n[0] * g->n[1] * g->n[2];
   double* R = reinterpret_cast<double*>(w + L.R);
   double* U1 = reinterpret_cast<double*>(w + L.U1);
   double* U2 = reinterpret_cast<double*>(w + L.U2);
-  double* B1 = reinterpret_cast<double*>(w + L.B1);
-  double* B2 = reinterpret_cast<double*>(w + L.B2);
   double* dtp = reinterpret_cast<double*>(w + L.dt);
 
   // forward stages of the step (eq. 4.1-4.2) with the given dt; each keeps
@@ -1094,17 +1114,24 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double 
                                  st) != cudaSuccess)
     return TENO_ERR_CUDA;
 
-  // reverse of eq. 4.3: B2 = 2/3 Ubar' + 2/3 dt J(U2)^T Ubar'
-  if ((s = adjoint_sequence(g, L, w, 2, true, U2, Ubar_next, 2.0 / 3.0 * dt, B2, Ubar_next, 2.0 / 3.0, nullptr,
-                            0.0, st)) != TENO_OK)
-    return s;
-  // Ubar_n = 1/3 Ubar' + 3/4 B2 (eq. 4.3 and 4.2 reach U^n directly)
-  if ((s = lincomb(Ubar_n, 1.0 / 3.0, Ubar_next, 0.75, B2, ntot, st)) != TENO_OK) return s;
-  // reverse of eq. 4.2: B1 = 1/4 B2 + 1/4 dt J(U1)^T B2
-  if ((s = adjoint_sequence(g, L, w, 1, false, U1, B2, 0.25 * dt, B1, B2, 0.25, nullptr, 0.0, st)) != TENO_OK)
-    return s;
-  // reverse of eq. 4.1: Ubar_n += B1 + dt J(U_n)^T B1
-  return adjoint_sequence(g, L, w, 0, false, U_n, B1, dt, Ubar_n, Ubar_n, 1.0, B1, 1.0, st);
+  return reverse_stages(g, L, w, U_n, U1, U2, false, dt, Ubar_next, Ubar_n, st);
+}
+
+teno_status teno_rk3_step_adjoint_staged(const teno_grid* g, const double* U_n, const double* U1,
+                                         const double* U2, double dt, const double* Ubar_next, double* Ubar_n,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  if (adjoint_unsupported(g)) return TENO_ERR_UNSUPPORTED;
+  if (!grid_valid(g) || !U_n || !U1 || !U2 || !Ubar_next || !Ubar_n || !(dt >= 0.0) || !std::isfinite(dt))
+    return TENO_ERR_INVALID_ARG;
+  if (!al(U_n, 16) || !al(U1, 16) || !al(U2, 16) || !al(Ubar_next, 16) || !al(Ubar_n, 16))
+    return TENO_ERR_INVALID_ARG;
+  if (Ubar_n == U_n || Ubar_n == U1 || Ubar_n == U2) return TENO_ERR_INVALID_ARG;
+  if (!is_dev(U_n) || !is_dev(U1) || !is_dev(U2) || !is_dev(Ubar_next) || !is_dev(Ubar_n))
+    return TENO_ERR_INVALID_ARG;
+  const AdjLayout L = adj_layout(g, TENO_OP_RK3_ADJOINT, sm_count());
+  if (!ws || !al(ws, kAlign) || ws_bytes < L.total || !is_dev(ws)) return TENO_ERR_WORKSPACE;
+  return reverse_stages(g, L, static_cast<char*>(ws), U_n, U1, U2, true, dt, Ubar_next, Ubar_n,
+                        static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -113,6 +113,7 @@ def test_reflecting_walls_accepted_by_the_forward_path_only(lib):
     assert lib.teno_workspace_bytes(ctypes.byref(g), _lib.OP_RK3) > 0
     assert lib.teno_rhs_adjoint(ctypes.byref(g), None, None, None, None, 0, None) == 2
     assert lib.teno_rk3_step_adjoint(ctypes.byref(g), None, 0.1, None, None, None, 0, None) == 2
+    assert lib.teno_rk3_step_adjoint_staged(ctypes.byref(g), None, None, None, 0.1, None, None, None, 0, None) == 2
     b = _lib.TenoBatch(2, 10, 2, 1.4, 10.0, 4, 10, 1e-6)
     off = (ctypes.c_int64 * 3)(0, 5, 10)
     assert lib.teno_batch_prepare(ctypes.byref(b), off, None, 0, None) == 2

@@ -134,3 +134,59 @@ def test_turbulence_16_rollout_gradient(api, oracle):
     assert float(loss.detach()) == pytest.approx(float(lo.detach()), rel=1e-10)
     rel_l2 = np.linalg.norm(g_gpu - g_or) / np.linalg.norm(g_or)
     assert rel_l2 <= ADJ_RTOL, rel_l2
+
+
+@pytest.mark.parametrize("name", ["2d-mixed", "3d-per", "turb16"])
+def test_staged_step_adjoint_equals_recomputed(api, name):
+    """teno_rk3_step_adjoint_staged with the stages the staged forward entry
+    points wrote (fixed dt) gives teno_rk3_step_adjoint's result bit for bit:
+    the stages are the ones the latter recomputes."""
+    _, U, n, dx, bc = next(c for c in _cases() if c[0] == name)
+    grid = api.EulerGrid(n, dx, bc)
+    Ut = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    Rb = torch.from_numpy(np.random.default_rng(21).standard_normal(U.shape)).cuda()
+    dt = 0.1 * min(dx)
+    adj = api.AdjointStepper(grid)
+    eng = api.SlabEngine(grid)
+    U1, U2, Un1 = api.rk3_step_stages(eng, Ut, dt)
+    ref = Ut.clone()
+    api.Solver(grid).step(ref, float("inf"), dt_fixed=dt)
+    assert torch.equal(Un1, ref)
+    a = adj.step(Ut, dt, Rb)
+    b = adj.step(Ut, dt, Rb, stages=(U1, U2))
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert adj.status() == 0
+
+
+def test_rollout_gradient_same_with_kept_stages(api, oracle):
+    """The rollout's backward with kept stages and with recomputed ones gives
+    the same gradient bit for bit (16^3 turbulence box, 12 steps at CFL 0.5,
+    segments of 5)."""
+    P = inputs.solenoidal_turbulence(n=16)
+    grid = api.EulerGrid(P.n, P.dx, P.bc)
+    dt = oracle.euler_dt(P.U0, P.n, P.dx, 0.5)
+    grads = []
+    for keep in (True, False):
+        U0 = torch.from_numpy(P.U0).cuda().requires_grad_(True)
+        out = api.rollout(U0, grid, 12, dt, checkpoint_every=5, keep_stages=keep)
+        (0.5 * (out ** 2).sum()).backward()
+        grads.append(U0.grad.clone())
+    assert torch.equal(grads[0], grads[1])
+
+
+def test_staged_step_adjoint_argument_checks(api):
+    from paper_2003_09145_gb300 import _lib
+    import ctypes
+    grid = api.EulerGrid((12, 10), (0.1, 0.1), (0, 1))
+    U = torch.ones(4 * 120, dtype=torch.float64, device="cuda")
+    B = torch.zeros_like(U)
+    adj = api.AdjointStepper(grid)
+    c = ctypes.byref(grid.c)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    ws, nb = p(adj.ws), adj.ws.numel()
+    # Ubar_n may not alias a stage input; dt must be finite and >= 0
+    assert grid.lib.teno_rk3_step_adjoint_staged(c, p(U), p(U), p(U), 0.01, p(B), p(U), ws, nb, None) == 1
+    assert grid.lib.teno_rk3_step_adjoint_staged(c, p(U), p(U), p(U), float("nan"), p(B), p(B), ws, nb, None) == 1
+    assert grid.lib.teno_rk3_step_adjoint_staged(c, p(U), None, p(U), 0.01, p(B), p(B), ws, nb, None) == 1
+    assert grid.lib.teno_rk3_step_adjoint_staged(c, p(U), p(U), p(U), 0.01, p(B), p(B), ws, 16, None) == 6
