@@ -40,16 +40,37 @@ TENO_HD inline double recip(double x) {
 
 // Linear weights of the reconstruction with selection `sel` (delta bits):
 // f^ = sum_k a[k] v_k over v = (f_{i-2}, ..., f_{i+2}), from the TENO weights
-// of eq. 2.15 and the candidate fluxes of eq. 2.4-2.6.
+// of eq. 2.15 and the candidate fluxes of eq. 2.4-2.6.  The eight selection
+// patterns' weights are a table built at compile time from these formulas
+// (selection 0, no stencil, cannot occur: all zeros).
+struct LinWeights {
+  double a[8][5];
+};
+constexpr LinWeights make_lin_weights() {
+  LinWeights t{};
+  for (unsigned sel = 1; sel < 8; ++sel) {
+    const double d0 = double(sel & 1u), d1 = double((sel >> 1) & 1u), d2 = double((sel >> 2) & 1u);
+    const double s = d0 * 0.1 + d1 * 0.6 + d2 * 0.3;
+    const double o0 = d0 * 0.1 / s, o1 = d1 * 0.6 / s, o2 = d2 * 0.3 / s;
+    t.a[sel][0] = o0 / 3.0;
+    t.a[sel][1] = -7.0 / 6.0 * o0 - 1.0 / 6.0 * o1;
+    t.a[sel][2] = 11.0 / 6.0 * o0 + 5.0 / 6.0 * o1 + 1.0 / 3.0 * o2;
+    t.a[sel][3] = 1.0 / 3.0 * o1 + 5.0 / 6.0 * o2;
+    t.a[sel][4] = -1.0 / 6.0 * o2;
+  }
+  return t;
+}
+#ifdef __CUDACC__
+__constant__ constexpr LinWeights c_lin_weights = make_lin_weights();
+#endif
+constexpr LinWeights h_lin_weights = make_lin_weights();
+
 TENO_HD inline void lin_weights(unsigned sel, double a[5]) {
-  const double d0 = double(sel & 1u), d1 = double((sel >> 1) & 1u), d2 = double((sel >> 2) & 1u);
-  const double s = d0 * 0.1 + d1 * 0.6 + d2 * 0.3;
-  const double o0 = d0 * 0.1 / s, o1 = d1 * 0.6 / s, o2 = d2 * 0.3 / s;
-  a[0] = o0 / 3.0;
-  a[1] = -7.0 / 6.0 * o0 - 1.0 / 6.0 * o1;
-  a[2] = 11.0 / 6.0 * o0 + 5.0 / 6.0 * o1 + 1.0 / 3.0 * o2;
-  a[3] = 1.0 / 3.0 * o1 + 5.0 / 6.0 * o2;
-  a[4] = -1.0 / 6.0 * o2;
+#ifdef __CUDA_ARCH__
+  for (int k = 0; k < 5; ++k) a[k] = c_lin_weights.a[sel & 7u][k];
+#else
+  for (int k = 0; k < 5; ++k) a[k] = h_lin_weights.a[sel & 7u][k];
+#endif
 }
 
 // With EXCL_P the flux term of the all-kept form, P_j A(U_j)^T Fbar
@@ -67,12 +88,13 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   const double gm1 = gamma - 1.0;
 
   // ---- forward --------------------------------------------------------------
-  double rho[6], u[6][NDIM], p[6], q[6], F[6][NV];
+  double rho[6], ir[6], u[6][NDIM], p[6], q[6], F[6][NV];
   for (int j = 0; j < 6; ++j) {
     rho[j] = Up[j][0];
+    ir[j] = recip(rho[j]);
     q[j] = 0.0;
     for (int k = 0; k < NDIM; ++k) {
-      u[j][k] = Up[j][1 + k] / rho[j];
+      u[j][k] = Up[j][1 + k] * ir[j];
       q[j] += u[j][k] * u[j][k];
     }
     p[j] = gm1 * (Up[j][E] - 0.5 * rho[j] * q[j]);
@@ -80,17 +102,18 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
     for (int k = 0; k < NDIM; ++k) F[j][1 + k] = Up[j][1 + k] * u[j][N] + (k == N ? p[j] : 0.0);
     F[j][E] = u[j][N] * (Up[j][E] + p[j]);
   }
-  const double sa = sqrt(rho[2]), sb = sqrt(rho[3]), S = sa + sb;
-  const double Ha = (Up[2][E] + p[2]) / rho[2], Hb = (Up[3][E] + p[3]) / rho[3];
+  const double sa = sqrt(rho[2]), sb = sqrt(rho[3]), S = sa + sb, iS = recip(S);
+  const double Ha = (Up[2][E] + p[2]) * ir[2], Hb = (Up[3][E] + p[3]) * ir[3];
   double ut[NDIM], q2 = 0.0;
   for (int k = 0; k < NDIM; ++k) {
-    ut[k] = (sa * u[2][k] + sb * u[3][k]) / S;
+    ut[k] = (sa * u[2][k] + sb * u[3][k]) * iS;
     q2 += ut[k] * ut[k];
   }
-  const double H = (sa * Ha + sb * Hb) / S;
+  const double H = (sa * Ha + sb * Hb) * iS;
   const double c2 = gm1 * (H - 0.5 * q2);
   const double c = sqrt(c2);
-  const double b1 = gm1 / c2;
+  const double ic = recip(c), ic2 = ic * ic;
+  const double b1 = gm1 * ic2;
   const double b2 = 0.5 * b1 * q2;
   const double un = ut[N];
 
@@ -100,8 +123,8 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   R[0][0] = 1.0;
   for (int k = 0; k < NDIM; ++k) R[1 + k][0] = ut[k] - (k == N ? c : 0.0);
   R[E][0] = H - un * c;
-  L[0][0] = 0.5 * (b2 + un / c);
-  for (int k = 0; k < NDIM; ++k) L[0][1 + k] = 0.5 * (-b1 * ut[k] - (k == N ? 1.0 / c : 0.0));
+  L[0][0] = 0.5 * (b2 + un * ic);
+  for (int k = 0; k < NDIM; ++k) L[0][1 + k] = 0.5 * (-b1 * ut[k] - (k == N ? ic : 0.0));
   L[0][E] = 0.5 * b1;
   R[0][1] = 1.0;
   for (int k = 0; k < NDIM; ++k) R[1 + k][1] = ut[k];
@@ -125,8 +148,8 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   R[0][E] = 1.0;
   for (int k = 0; k < NDIM; ++k) R[1 + k][E] = ut[k] + (k == N ? c : 0.0);
   R[E][E] = H + un * c;
-  L[E][0] = 0.5 * (b2 - un / c);
-  for (int k = 0; k < NDIM; ++k) L[E][1 + k] = 0.5 * (-b1 * ut[k] + (k == N ? 1.0 / c : 0.0));
+  L[E][0] = 0.5 * (b2 - un * ic);
+  for (int k = 0; k < NDIM; ++k) L[E][1 + k] = 0.5 * (-b1 * ut[k] + (k == N ? ic : 0.0));
   L[E][E] = 0.5 * b1;
 
   double w[6][NV], g[6][NV];
@@ -194,7 +217,6 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   double utb[NDIM];
   for (int k = 0; k < NDIM; ++k) utb[k] = 0.0;
   double Hbar = 0.0, cb = 0.0, b1b = 0.0, b2b = 0.0, q2b = 0.0;
-  const double ic = 1.0 / c, ic2 = ic * ic;
   // from L
   b2b += 0.5 * X[0][0] - X[1][0] + 0.5 * X[E][0];
   utb[N] += 0.5 * ic * (X[0][0] - X[E][0]);
@@ -218,21 +240,21 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
   // chain through b2, b1, c, c2, q2
   b1b += 0.5 * q2 * b2b;
   q2b += 0.5 * b1 * b2b;
-  double c2b = -(b1 / c2) * b1b + 0.5 * ic * cb;
+  double c2b = -(b1 * ic2) * b1b + 0.5 * ic * cb;
   Hbar += gm1 * c2b;
   q2b += -0.5 * gm1 * c2b;
   for (int k = 0; k < NDIM; ++k) utb[k] += 2.0 * ut[k] * q2b;
   // Roe averages
   double ub2[NDIM], ub3[NDIM], sab = 0.0, sbb = 0.0;
   for (int k = 0; k < NDIM; ++k) {
-    ub2[k] = sa / S * utb[k];
-    ub3[k] = sb / S * utb[k];
-    sab += (u[2][k] - ut[k]) / S * utb[k];
-    sbb += (u[3][k] - ut[k]) / S * utb[k];
+    ub2[k] = sa * iS * utb[k];
+    ub3[k] = sb * iS * utb[k];
+    sab += (u[2][k] - ut[k]) * iS * utb[k];
+    sbb += (u[3][k] - ut[k]) * iS * utb[k];
   }
-  const double Hab = sa / S * Hbar, Hbb = sb / S * Hbar;
-  sab += (Ha - H) / S * Hbar;
-  sbb += (Hb - H) / S * Hbar;
+  const double Hab = sa * iS * Hbar, Hbb = sb * iS * Hbar;
+  sab += (Ha - H) * iS * Hbar;
+  sbb += (Hb - H) * iS * Hbar;
 
   // per point: primitives -> conservative
   if (EXCL_P) {
@@ -248,10 +270,10 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
       const double sxb = (j == 2) ? sab : sbb;
       const double Hx = (j == 2) ? Ha : Hb;
       const double Hxb = (j == 2) ? Hab : Hbb;
-      rhob += 0.5 / sx * sxb;
-      Eb += Hxb / rho[j];
-      pb += Hxb / rho[j];
-      rhob += -Hx / rho[j] * Hxb;
+      rhob += 0.5 * sx * ir[j] * sxb;   // 1/(2 sqrt(rho)) = sqrt(rho) / (2 rho)
+      Eb += Hxb * ir[j];
+      pb += Hxb * ir[j];
+      rhob += -Hx * ir[j] * Hxb;
       for (int k = 0; k < NDIM; ++k) ub_[k] += (j == 2) ? ub2[k] : ub3[k];
     }
     // F = (rho u_n, m_k u_n + p delta_kn, u_n (E + p))
@@ -273,8 +295,8 @@ TENO_HD inline void interface_vjp(const double (&Up)[6][NDIM + 2], const double 
     for (int k = 0; k < NDIM; ++k) ub_[k] += -gm1 * rho[j] * u[j][k] * pb;
     // u = m / rho
     for (int k = 0; k < NDIM; ++k) {
-      mb[k] += ub_[k] / rho[j];
-      rhob += -u[j][k] / rho[j] * ub_[k];
+      mb[k] += ub_[k] * ir[j];
+      rhob += -u[j][k] * ir[j] * ub_[k];
     }
     Ub[j][0] += rhob;
     for (int k = 0; k < NDIM; ++k) Ub[j][1 + k] += mb[k];
