@@ -46,7 +46,7 @@ extern "C" {
 typedef enum {
   TENO_OK = 0,
   TENO_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or parameter   */
-  TENO_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  TENO_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement */
   TENO_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed        */
   TENO_ERR_NONPHYSICAL = 4,   /* device saw rho <= 0, p <= 0 or a non-finite */
   TENO_ERR_TIMEOUT = 5,       /* a bounded device wait ran out               */
