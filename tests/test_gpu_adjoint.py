@@ -190,3 +190,21 @@ def test_staged_step_adjoint_argument_checks(api):
     assert grid.lib.teno_rk3_step_adjoint_staged(c, p(U), p(U), p(U), float("nan"), p(B), p(B), ws, nb, None) == 1
     assert grid.lib.teno_rk3_step_adjoint_staged(c, p(U), None, p(U), 0.01, p(B), p(B), ws, nb, None) == 1
     assert grid.lib.teno_rk3_step_adjoint_staged(c, p(U), p(U), p(U), 0.01, p(B), p(B), ws, 16, None) == 6
+
+
+@pytest.mark.parametrize("name", ["2d-mixed", "3d-per"])
+def test_rhs_adjoint_every_interface_pending(api, oracle, name):
+    """A scheme without a keep-all magnitude (B_l = 1, B_u = 2, H = 1e16)
+    leaves every interface to the pending passes: the list holds all of
+    them, the partition splits it into the all-kept and the cut ones, and
+    the gradient still matches the oracle's."""
+    from oracle import grad
+    sch = dict(H=1e16, b_l=1, b_u=2)
+    _, U, n, dx, bc = next(c for c in _cases() if c[0] == name)
+    Rbar = np.random.default_rng(23).standard_normal(U.shape)
+    ref, _ = grad.rhs_vjp(U, n, dx, bc, Rbar, oracle.Params(**sch))
+    grid = api.EulerGrid(n, dx, bc, api.Scheme(**sch))
+    Ut = torch.from_numpy(np.ascontiguousarray(U)).cuda()
+    got = api.rhs_adjoint(grid, Ut, torch.from_numpy(Rbar).cuda()).cpu().numpy()
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= ADJ_RTOL, err
