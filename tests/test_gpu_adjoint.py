@@ -37,6 +37,7 @@ def _cases():
         ("3d-trans", inputs.random_discontinuous_state(3, (8, 6, 7), seed=5), (8, 6, 7), (0.1, 0.1, 0.1), (1, 1, 1)),
         ("turb16", inputs.solenoidal_turbulence(n=16).U0, (16, 16, 16), (2 * math.pi / 16,) * 3, (0, 0, 0)),
         # periodic lines shorter than the six-point stencil (the gather's slot-by-slot path)
+        ("1d-per-2", inputs.random_discontinuous_state(1, (2,), seed=13), (2,), (0.1,), (0,)),
         ("2d-short-per", inputs.random_discontinuous_state(2, (5, 4), seed=10), (5, 4), (0.1, 0.1), (0, 0)),
         ("3d-short-mixed", inputs.random_discontinuous_state(3, (7, 4, 5), seed=11), (7, 4, 5), (0.1, 0.1, 0.1),
          (0, 1, 0)),
