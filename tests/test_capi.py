@@ -49,6 +49,8 @@ def test_grid_validation(lib):
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.bc[0] = 7; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.b_u = g.b_l; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.n[2] = 3; bad.append(g)
+    g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.n[0] = 0; bad.append(g)     # empty grid
+    g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.n[1] = -4; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.gamma = 1.0; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.eps = -1.0; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.scheme = 4; bad.append(g)
@@ -117,3 +119,13 @@ def test_reflecting_walls_accepted_by_the_forward_path_only(lib):
     b = _lib.TenoBatch(2, 10, 2, 1.4, 10.0, 4, 10, 1e-6)
     off = (ctypes.c_int64 * 3)(0, 5, 10)
     assert lib.teno_batch_prepare(ctypes.byref(b), off, None, 0, None) == 2
+
+
+def test_empty_batch_rejected(lib):
+    """A batch of no problems, or of a problem with no cells, is an invalid
+    request (no work is launched for it)."""
+    from paper_2003_09145_gb300 import _lib
+    b = _lib.TenoBatch(0, 0, 1, 1.4, 10.0, 4, 10, 1e-6)
+    assert lib.teno_batch_workspace_bytes(ctypes.byref(b)) == 0
+    b = _lib.TenoBatch(2, 1, 1, 1.4, 10.0, 4, 10, 1e-6)     # fewer cells than problems
+    assert lib.teno_batch_workspace_bytes(ctypes.byref(b)) == 0
