@@ -21,9 +21,13 @@
 //     list passes      : the pending interfaces in one list, index order;
 //     adj_select_kernel: the listed interfaces' selections by the forward
 //                        pass's binary64 decisions;
-//     adj_general_kernel: the listed interfaces' general VJP with those
-//                        selections; the six cells' contributions go to
-//                        contrib_d;
+//     partition passes : the list reordered stably, the interfaces that keep
+//                        every stencil after all first;
+//     adj_general_kernel: the listed interfaces' VJP with those selections
+//                        (the closed form for the first kind); the six
+//                        cells' contributions go to contrib_d;
+// (teno_rk3_step_adjoint runs three of these after recomputing the stages
+// U1, U2; teno_rk3_step_adjoint_staged takes the stages from the caller.)
 //   adj_gather_kernel: one thread per cell sums, over every direction, the
 //                      contributions of every (interface, stencil slot) that
 //                      maps to it (boundary ghost copies included) and applies
