@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     const double* __restrict__ U, const double* __restrict__ aux,
     const unsigned long long* __restrict__ alpha_bits, const double* __restrict__ Rbar, double scale,
     double* __restrict__ kb, unsigned char* __restrict__ pending, double* __restrict__ apart,
-    int* __restrict__ status, Grid G, Scheme S) {
+    int* __restrict__ status, Grid G, Scheme S, const double* __restrict__ roe_in) {
   constexpr int NVAR = NDIM + 2;
   const IfcGeom<NDIM, DIR> I(G);
   double fa[NVAR], ha[NVAR], nfa[NVAR];
@@ -175,19 +175,33 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     int64_t id, base, cells[6];
     I.locate(q, G, id, base, cells);
     // The forward pass's Roe state (roe_interface on the cell pass's
-    // primitives) and its certified FP32 test: a pass keeps every stencil
-    // exactly where the forward's closed-form pass did.  U~ is accumulated
-    // over the same stencil loads.
+    // primitives; as the recomputed forward stage stored it, if it did) and
+    // its certified FP32 test: a pass keeps every stencil exactly where the
+    // forward's closed-form pass did.  U~ is accumulated over the same
+    // stencil loads.
     const double sr2 = aux[(NDIM + 1) * I.ncell + cells[2]], sr3 = aux[(NDIM + 1) * I.ncell + cells[3]];
     const double sh2 = aux[(NDIM + 2) * I.ncell + cells[2]], sh3 = aux[(NDIM + 2) * I.ncell + cells[3]];
-    double su2[NDIM], su3[NDIM];
-#pragma unroll
-    for (int k = 0; k < NDIM; ++k) {
-      su2[k] = aux[(NDIM + 3 + k) * I.ncell + cells[2]];
-      su3[k] = aux[(NDIM + 3 + k) * I.ncell + cells[3]];
-    }
     teno::RoeIfc<NDIM> Rf;
-    teno::roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, su2, su3, S, Rf, status);
+    if (roe_in) {
+#pragma unroll
+      for (int k = 0; k < NDIM; ++k) Rf.u[k] = roe_in[(int64_t)k * I.nifc + q];
+      Rf.q2 = roe_in[(int64_t)(NDIM + 0) * I.nifc + q];
+      Rf.H = roe_in[(int64_t)(NDIM + 1) * I.nifc + q];
+      Rf.cs = roe_in[(int64_t)(NDIM + 2) * I.nifc + q];
+      Rf.b1 = roe_in[(int64_t)(NDIM + 3) * I.nifc + q];
+      Rf.hb1 = roe_in[(int64_t)(NDIM + 4) * I.nifc + q];
+      Rf.hb2 = roe_in[(int64_t)(NDIM + 5) * I.nifc + q];
+      Rf.hic = roe_in[(int64_t)(NDIM + 6) * I.nifc + q];
+      Rf.hud = 0.5 * Rf.u[DIR];
+    } else {
+      double su2[NDIM], su3[NDIM];
+#pragma unroll
+      for (int k = 0; k < NDIM; ++k) {
+        su2[k] = aux[(NDIM + 3 + k) * I.ncell + cells[2]];
+        su3[k] = aux[(NDIM + 3 + k) * I.ncell + cells[3]];
+      }
+      teno::roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, su2, su3, S, Rf, status);
+    }
     teno::CertIfc<NDIM> C;
     teno::cert_begin<NDIM, DIR>(Rf, ha, C);
     double Ut[NVAR];
@@ -839,7 +853,8 @@ struct AdjLayout {
   size_t status = 0, dt = 8, alpha = 64, argidx = 512;
   size_t aux = 0, aux_bytes = 0, cand = 0, fh = 0, kb = 0, kb_bytes = 0, contrib = 0, contrib_bytes = 0,
          pending = 0, pending_bytes = 0, list = 0, sel = 0, lcount = 0, apart = 0, R = 0, U1 = 0, U2 = 0, B1 = 0,
-         B2 = 0, total = 0;
+         B2 = 0, roe = 0, roe_stage_bytes = 0, total = 0;
+  size_t roe_dir = 0;   // doubles between two directions' Roe states
 };
 
 AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
@@ -894,6 +909,11 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
     off += round_up(sizeof(double) * nvar * ncell);
     L.B2 = off;
     off += round_up(sizeof(double) * nvar * ncell);
+    // the recomputed stages' Roe states (stage slots 0, 1), [ndim][ndim + 7][maxifc]
+    L.roe_dir = size_t(g->ndim + 7) * size_t(maxifc);
+    L.roe_stage_bytes = round_up(sizeof(double) * g->ndim * L.roe_dir);
+    L.roe = off;
+    off += 2 * L.roe_stage_bytes;
   }
   L.total = off;
   return L;
@@ -935,9 +955,9 @@ template <int NDIM, int DIR>
 void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const double* aux,
                     const unsigned long long* alpha, const double* Rbar, double scale, double* kb,
                     double* contrib, unsigned char* pending, uint32_t* list, int* lcount, uint32_t* sel,
-                    double* apart, int* status, const Grid& G, const Scheme& S) {
+                    double* apart, int* status, const Grid& G, const Scheme& S, const double* roe_in) {
   adj_kept_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
-                                                          status, G, S);
+                                                          status, G, S, roe_in);
   int64_t nifc = 1;
   for (int k = 0; k < 3; ++k) nifc *= G.n[k] + (k == DIR ? 1 : 0);
   const int lblk = adj_list_blocks(nsm);
@@ -964,7 +984,7 @@ template <int NDIM>
 void launch_adj_all(int nblk, int nsm, cudaStream_t st, const double* U, const double* aux,
                     const unsigned long long* alpha, const unsigned long long* argidx, const double* Rbar,
                     double scale, const AdjLayout& L, char* ws, int* status, GatherArgs A, const Grid& G,
-                    const Scheme& S) {
+                    const Scheme& S, const double* roe_in) {
   auto* list = reinterpret_cast<uint32_t*>(ws + L.list);
   auto* lcount = reinterpret_cast<int*>(ws + L.lcount);
   auto* sel = reinterpret_cast<uint32_t*>(ws + L.sel);
@@ -974,11 +994,12 @@ void launch_adj_all(int nblk, int nsm, cudaStream_t st, const double* U, const d
     double* contrib = reinterpret_cast<double*>(ws + L.contrib + d * L.contrib_bytes);
     auto* pending = reinterpret_cast<unsigned char*>(ws + L.pending + d * L.pending_bytes);
     double* ap = apart + 6 * nblk * d;
-    if (d == 0) launch_adj_dir<NDIM, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S);
+    const double* rin = roe_in ? roe_in + d * L.roe_dir : nullptr;
+    if (d == 0) launch_adj_dir<NDIM, 0>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S, rin);
     if constexpr (NDIM > 1)
-      if (d == 1) launch_adj_dir<NDIM, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S);
+      if (d == 1) launch_adj_dir<NDIM, 1>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S, rin);
     if constexpr (NDIM > 2)
-      if (d == 2) launch_adj_dir<NDIM, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S);
+      if (d == 2) launch_adj_dir<NDIM, 2>(nblk, nsm, st, U, aux, alpha, Rbar, scale, kb, contrib, pending, list, lcount, sel, ap, status, G, S, rin);
     A.kb[d] = kb;
     A.contrib[d] = contrib;
     A.pending[d] = pending;
@@ -1021,9 +1042,14 @@ teno_status adjoint_sequence(const teno_grid* g, const AdjLayout& L, char* ws, i
   A.a = a;
   A.Y = Y;
   A.b = b;
-  if (g->ndim == 1) launch_adj_all<1>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S);
-  else if (g->ndim == 2) launch_adj_all<2>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S);
-  else launch_adj_all<3>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S);
+  // the recomputed forward stage's Roe states, where it stored them (stage
+  // slots 0 and 1; none without a keep-all magnitude, as nothing is kept)
+  const double* roe_in = (!cell && L.roe && stage < 2 && S.keep_idx >= 0)
+                             ? reinterpret_cast<const double*>(ws + L.roe + stage * L.roe_stage_bytes)
+                             : nullptr;
+  if (g->ndim == 1) launch_adj_all<1>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S, roe_in);
+  else if (g->ndim == 2) launch_adj_all<2>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S, roe_in);
+  else launch_adj_all<3>(nblk, nsm, st, U, aux, alpha, argidx, Rbar, scale, L, ws, status, A, G, S, roe_in);
   return cudaGetLastError() == cudaSuccess ? TENO_OK : TENO_ERR_CUDA;
 }
 
@@ -1104,14 +1130,16 @@ teno_status teno_rk3_step_adjoint(const teno_grid* g, const double* U_n, double 
   const int64_t ncell = int64_t(g->n[0]) * g->n[1] * g->n[2];
   set_value_kernel<<<1, 1, 0, st>>>(dtp, dt);
   if (cudaGetLastError() != cudaSuccess) return TENO_ERR_CUDA;
+  double* roe0 = reinterpret_cast<double*>(w + L.roe);
+  double* roe1 = reinterpret_cast<double*>(w + L.roe + L.roe_stage_bytes);
   teno_status s = teno::forward_stage(g, w, L.status, L.dt, L.alpha, L.aux, L.fh, L.contrib, L.list, U_n, R,
-                                      2, U_n, nullptr, U1, st, cand);
+                                      2, U_n, nullptr, U1, st, cand, roe0, L.roe_dir);
   if (s != TENO_OK) return s;
   if (teno::launch_argmax_finish(g->ndim, cand, ncell, nsm, reinterpret_cast<unsigned long long*>(w + L.argidx),
                                  st) != cudaSuccess)
     return TENO_ERR_CUDA;
   s = teno::forward_stage(g, w, L.status, L.dt, L.alpha + AdjLayout::kStage, L.aux + L.aux_bytes, L.fh, L.contrib,
-                          L.list, U1, R, 3, U_n, U1, U2, st, cand);
+                          L.list, U1, R, 3, U_n, U1, U2, st, cand, roe1, L.roe_dir);
   if (s != TENO_OK) return s;
   if (teno::launch_argmax_finish(g->ndim, cand, ncell, nsm,
                                  reinterpret_cast<unsigned long long*>(w + L.argidx + AdjLayout::kStage),

@@ -223,7 +223,9 @@ __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const d
 // stencil; otherwise `out` equals interface_flux's.
 // ---------------------------------------------------------------------------
 // (GH: the sweep direction has fixed-state ghost cells, read from gc; the
-// half fluxes of the ghost block are taken at direction DIR's block.)
+// half fluxes of the ghost block are taken at direction DIR's block.  With
+// `rout` the interface's Roe state is also returned, whatever the test
+// decides.)
 template <int NDIM, int DIR, bool GH = false>
 __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__ U,
                                                       const double* __restrict__ aux,
@@ -232,7 +234,8 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
                                                       const double (&alpha)[NDIM + 2],
                                                       const double (&nal)[NDIM + 2], const Scheme& S,
                                                       double (&out)[NDIM + 2], int* __restrict__ status,
-                                                      const GhostCells& gc = GhostCells()) {
+                                                      const GhostCells& gc = GhostCells(),
+                                                      RoeIfc<NDIM>* rout = nullptr) {
   constexpr int NVAR = NDIM + 2;
   if (S.keep_idx < 0) return false;
   const double* gfh = GH ? gc.fh + DIR * (NVAR - 1) * kGhostSlots : nullptr;
@@ -251,6 +254,7 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
                              ldc<GH>(aux, gc.aux, ncell, NDIM + 2, cells[2]),
                              ldc<GH>(aux, gc.aux, ncell, NDIM + 2, cells[3]), su2, su3, S, R, status);
   }
+  if (rout) *rout = R;
   CertIfc<NDIM> C;
   cert_begin<NDIM, DIR>(R, alpha, C);
   double Ft[NVAR], Ut[NVAR];

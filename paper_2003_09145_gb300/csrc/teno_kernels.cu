@@ -322,13 +322,16 @@ __device__ __forceinline__ void half_speeds(const unsigned long long* __restrict
 // WALL: 1 -- the sweep direction has a reflecting wall, so stencil points may
 // be mirrored; 2 -- fixed-state faces (ghost points read from the ghost
 // block); 0 -- neither: the mirror flags are the constant 0 and their sign
-// flips fold away.
-template <int NDIM, int DIR, int WALL>
+// flips fold away.  With ROE every interface's Roe state (the fields the
+// certificate and the adjoint's closed-form VJP read: u~, |u~|^2, H~, c~,
+// b1, b1/2, b2/2, 1/(2c~)) also goes to roe_out[ndim + 7][nifc], for the
+// adjoint of this stage.
+template <int NDIM, int DIR, int WALL, bool ROE = false>
 __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel(
     const double* __restrict__ U, const double* __restrict__ aux, const double* __restrict__ fh,
     const unsigned long long* __restrict__ alpha_bits, double* __restrict__ Fhat,
     uint32_t* __restrict__ list, unsigned* __restrict__ count, int* __restrict__ status, Grid G,
-    Scheme S) {
+    Scheme S, double* __restrict__ roe_out = nullptr) {
   constexpr int NVAR = NDIM + 2;
   const int64_t nifc = (G.n[0] + (DIR == 0)) * (G.n[1] + (DIR == 1)) * (G.n[2] + (DIR == 2));
   double alpha[NVAR], nal[NVAR];
@@ -340,9 +343,23 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
     unsigned flips;
     interface_cells<NDIM, DIR, WALL == 2>(q, G, cells, flips);
     double out[NVAR];
+    RoeIfc<NDIM> R;
     const bool done = interface_flux_closed<NDIM, DIR, WALL == 2>(
         U, aux, fh + (int64_t)DIR * (NVAR - 1) * G.ncell, G.ncell, cells, WALL == 1 ? flips : 0u, alpha, nal, S,
-        out, status, GhostCells{G.gU, G.gaux, G.gfh});
+        out, status, GhostCells{G.gU, G.gaux, G.gfh}, ROE ? &R : nullptr);
+    if constexpr (ROE) {
+      if (S.keep_idx >= 0) {
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) roe_out[(int64_t)k * nifc + q] = R.u[k];
+        roe_out[(int64_t)(NDIM + 0) * nifc + q] = R.q2;
+        roe_out[(int64_t)(NDIM + 1) * nifc + q] = R.H;
+        roe_out[(int64_t)(NDIM + 2) * nifc + q] = R.cs;
+        roe_out[(int64_t)(NDIM + 3) * nifc + q] = R.b1;
+        roe_out[(int64_t)(NDIM + 4) * nifc + q] = R.hb1;
+        roe_out[(int64_t)(NDIM + 5) * nifc + q] = R.hb2;
+        roe_out[(int64_t)(NDIM + 6) * nifc + q] = R.hic;
+      }
+    }
     if (done) {
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) Fhat[(int64_t)v * nifc + q] = out[v];
@@ -682,7 +699,7 @@ template <int NDIM, int DIR>
 static int flux_launch(int blocks, int threads, int pblocks, cudaStream_t st, const double* U,
                        const double* aux, const double* fh, const unsigned long long* alpha, double* Fhat,
                        uint8_t* flags, uint32_t* list, unsigned* count, int* status, const Grid& G,
-                       const Scheme& S) {
+                       const Scheme& S, double* roe_out) {
   const bool gh = G.bc[DIR] == TENO_BC_DIRICHLET;
   if (flags || !list) {
     if (flags && gh) flux_kernel<NDIM, DIR, true, true><<<blocks, threads, 0, st>>>(U, aux, alpha, Fhat, flags, status, G, S);
@@ -695,6 +712,9 @@ static int flux_launch(int blocks, int threads, int pblocks, cudaStream_t st, co
     flux_closed_kernel<NDIM, DIR, 1><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
   else if (gh)
     flux_closed_kernel<NDIM, DIR, 2><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
+  else if (roe_out)
+    flux_closed_kernel<NDIM, DIR, 0, true><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status,
+                                                                      G, S, roe_out);
   else
     flux_closed_kernel<NDIM, DIR, 0><<<blocks, threads, 0, st>>>(U, aux, fh, alpha, Fhat, list, count, status, G, S);
   if (gh)
@@ -708,7 +728,7 @@ cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, c
                         const unsigned long long* alpha, double* Fhat,
                         uint8_t* flags, uint32_t* list, unsigned* count, int* status,
                         const Grid& G, const Scheme& S, int nsm, cudaStream_t st,
-                        int* launches) {
+                        int* launches, double* roe_out) {
   int64_t nifc = 1;
   for (int k = 0; k < 3; ++k) nifc *= G.n[k] + (k == dir ? 1 : 0);
   if (nifc > int64_t(UINT32_MAX)) list = nullptr;   // list entries are 32-bit
@@ -717,14 +737,14 @@ cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, c
   const int blocks = blocks_for(nifc, threads, nsm * 64);
   const int pblocks = blocks_for(nifc, threads, nsm * 16);
   int n = 0;
-  if (ndim == 1) n = flux_launch<1, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
+  if (ndim == 1) n = flux_launch<1, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S, roe_out);
   else if (ndim == 2) {
-    if (dir == 0) n = flux_launch<2, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
-    else n = flux_launch<2, 1>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
+    if (dir == 0) n = flux_launch<2, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S, roe_out);
+    else n = flux_launch<2, 1>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S, roe_out);
   } else {
-    if (dir == 0) n = flux_launch<3, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
-    else if (dir == 1) n = flux_launch<3, 1>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
-    else n = flux_launch<3, 2>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S);
+    if (dir == 0) n = flux_launch<3, 0>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S, roe_out);
+    else if (dir == 1) n = flux_launch<3, 1>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S, roe_out);
+    else n = flux_launch<3, 2>(blocks, threads, pblocks, st, U, aux, fh, alpha, Fhat, flags, list, count, status, G, S, roe_out);
   }
   if (launches) *launches = n;
   return cudaGetLastError();
@@ -789,7 +809,8 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
                           size_t alpha_off, size_t aux_off, size_t fh_off, size_t fhat_off, size_t list_off,
                           const double* U, double* R, int mode, const double* Un, const double* Uk,
-                          double* Uout, cudaStream_t st, unsigned long long* cand) {
+                          double* Uout, cudaStream_t st, unsigned long long* cand, double* roe_out,
+                          size_t roe_stride) {
   Grid G;
   for (int k = 0; k < 3; ++k) {
     G.n[k] = g->n[k];
@@ -817,7 +838,7 @@ teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_
     return TENO_ERR_CUDA;
   for (int d = 0; d < g->ndim; ++d) {
     if (launch_flux(g->ndim, d, U, aux, fh, alpha, Fhat, nullptr, list, count + d, status, G, S, nsm, st,
-                    nullptr) != cudaSuccess)
+                    nullptr, roe_out ? roe_out + d * roe_stride : nullptr) != cudaSuccess)
       return TENO_ERR_CUDA;
     if (launch_diff(g->ndim, d, Fhat, R, Un, Uk, Uout, dt, G, mode, nsm, st, U) != cudaSuccess)
       return TENO_ERR_CUDA;

@@ -45,12 +45,14 @@ cudaError_t launch_argmax_finish(int ndim, const unsigned long long* cand, int64
 // `list` (room for one 32-bit entry per interface), its counter `count`
 // (zero on entry) and `fh`, the closed-form pass and the pass over the
 // interfaces it leaves pending.  `launches` (optional) receives the number
-// of kernels launched.
+// of kernels launched.  With `roe_out` (two-pass fluxes without reflecting or
+// fixed-state faces only) the closed-form pass also writes every
+// interface's Roe state, [ndim + 7][#interfaces] (flux_closed_kernel).
 cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, const double* fh,
                         const unsigned long long* alpha, double* Fhat,
                         uint8_t* flags, uint32_t* list, unsigned* count, int* status,
                         const Grid& G, const Scheme& S, int nsm, cudaStream_t st,
-                        int* launches);
+                        int* launches, double* roe_out = nullptr);
 
 // The workspace header holds the nine LF speeds (as bit patterns) and, right
 // after them, one pending-list counter per direction; one memset of
@@ -92,10 +94,12 @@ cudaError_t launch_dt(int ndim, const unsigned long long* alpha, const Grid& G,
 // the pending counters after them), the per-cell primitives, the half
 // fluxes, the interface-flux buffer and the pending list (fh_off or list_off
 // 0: one-pass fluxes); R holds the partial sums of the multi-dimensional
-// difference; `cand` (nullable) as for launch_cell.
+// difference; `cand` (nullable) as for launch_cell; with `roe_out`, direction
+// d's Roe states go to roe_out + d roe_stride (see launch_flux).
 teno_status forward_stage(const teno_grid* g, char* ws, size_t status_off, size_t dt_off,
                           size_t alpha_off, size_t aux_off, size_t fh_off, size_t fhat_off, size_t list_off,
                           const double* U, double* R, int mode, const double* Un, const double* Uk,
-                          double* Uout, cudaStream_t st, unsigned long long* cand = nullptr);
+                          double* Uout, cudaStream_t st, unsigned long long* cand = nullptr,
+                          double* roe_out = nullptr, size_t roe_stride = 0);
 
 }  // namespace teno
