@@ -382,10 +382,10 @@ TENO_HD inline void flux_vjp_acc(const double (&U)[NDIM + 2], const CellPrim<NDI
 }
 
 // Roe state of cells i (a) and i+1 (b) with the point quantities its
-// derivative needs.
+// derivative needs.  (The adjoint's kept pass fills only what
+// kept_roe_scaled reads: sa, sb, iS, duh, dH and the averaged state with
+// its halved coefficients.)
 template <int NDIM>
-// (roe_from_weighted sets only what interface_vjp_kept_roe reads: sa, sb,
-// iS, duh, dH and the averaged state.)
 struct RoeState {
   double sa, sb, iS, ira, irb, ua[NDIM], ub[NDIM], qa, qb, Ha, Hb;
   double duh[NDIM], dH;   // (u_a - u_b)/2, H_a - H_b
@@ -437,28 +437,6 @@ TENO_HD inline void roe_from_primitives(double sa, double sb, double sha, double
   R.H = (sha + shb) * R.iS;
   for (int k = 0; k < NDIM; ++k) R.duh[k] = 0.5 * (ua[k] - ub[k]);
   R.dH = R.Ha - R.Hb;
-  roe_average<NDIM>(gamma, R);
-}
-
-// The same from the cell pass's primitives: sqrt(rho), (E+p)/sqrt(rho), the
-// half velocities u/2 and the weighted velocities m/sqrt(rho) of both cells
-// (u~ = (w_a + w_b) / (s_a + s_b)); only the fields interface_vjp_kept_roe
-// reads are set.
-template <int NDIM>
-TENO_HD inline void roe_from_weighted(double sa, double sb, double sha, double shb, const double (&uha)[NDIM],
-                                      const double (&uhb)[NDIM], const double (&wa)[NDIM],
-                                      const double (&wb)[NDIM], double gamma, RoeState<NDIM>& R) {
-  R.sa = sa;
-  R.sb = sb;
-  R.dH = sha * recip(sa) - shb * recip(sb);
-  R.iS = recip(sa + sb);
-  R.q2 = 0.0;
-  for (int k = 0; k < NDIM; ++k) {
-    R.duh[k] = uha[k] - uhb[k];
-    R.ut[k] = (wa[k] + wb[k]) * R.iS;
-    R.q2 = fma(R.ut[k], R.ut[k], R.q2);
-  }
-  R.H = (sha + shb) * R.iS;
   roe_average<NDIM>(gamma, R);
 }
 
