@@ -152,7 +152,7 @@ __device__ __forceinline__ void add_alpha(const double (&ab)[NVAR], double (&asu
 #ifndef TENO_ADJ_KEPT_MINBLOCKS
 #define TENO_ADJ_KEPT_MINBLOCKS 3   // 168 registers: 12 warps per SM
 #endif
-template <int NDIM, int DIR>
+template <int NDIM, int DIR, bool STORED>
 __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept_kernel(
     const double* __restrict__ U, const double* __restrict__ aux,
     const unsigned long long* __restrict__ alpha_bits, const double* __restrict__ Rbar, double scale,
@@ -175,14 +175,49 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
     int64_t id, base, cells[6];
     I.locate(q, G, id, base, cells);
     // The forward pass's Roe state (roe_interface on the cell pass's
-    // primitives; as the recomputed forward stage stored it, if it did) and
-    // its certified FP32 test: a pass keeps every stencil exactly where the
-    // forward's closed-form pass did.  U~ is accumulated over the same
-    // stencil loads.
+    // primitives) and its certified FP32 test: a pass keeps every stencil
+    // exactly where the forward's closed-form pass did.  U~ is accumulated
+    // over the same stencil loads.  With STORED the recomputed forward
+    // stage's closed-form pass has stored both (roe_in), so neither is
+    // evaluated again.
     const double sr2 = aux[(NDIM + 1) * I.ncell + cells[2]], sr3 = aux[(NDIM + 1) * I.ncell + cells[3]];
     const double sh2 = aux[(NDIM + 2) * I.ncell + cells[2]], sh3 = aux[(NDIM + 2) * I.ncell + cells[3]];
     teno::RoeIfc<NDIM> Rf;
-    if (roe_in) {
+    double Ut[NVAR];
+    bool kept;
+    if constexpr (STORED) {
+      kept = roe_in[(int64_t)(NDIM + 7) * I.nifc + q] != 0.0;
+    } else {
+      double su2[NDIM], su3[NDIM];
+#pragma unroll
+      for (int k = 0; k < NDIM; ++k) {
+        su2[k] = aux[(NDIM + 3 + k) * I.ncell + cells[2]];
+        su3[k] = aux[(NDIM + 3 + k) * I.ncell + cells[3]];
+      }
+      teno::roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, su2, su3, S, Rf, status);
+      teno::CertIfc<NDIM> C;
+      teno::cert_begin<NDIM, DIR>(Rf, ha, C);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double Uj[NVAR];
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) {
+          Uj[v] = U[v * I.ncell + cells[j]];
+          Ut[v] = j == 0 ? Uj[v] : (j == 5 ? Ut[v] - Uj[v] : fma(Mi[j], Uj[v], Ut[v]));
+        }
+        teno::cert_point<NDIM, DIR>(j, Uj, aux[DIR * I.ncell + cells[j]], aux[NDIM * I.ncell + cells[j]], C);
+      }
+      kept = S.keep_idx >= 0 && teno::cert_keep<NDIM>(C, S);
+    }
+    pending[q] = kept ? 0 : 1;
+    if (!kept) {
+      // a pending interface's terms come from adj_general_kernel; zeros
+      // here let the gather add kb for every interface alike
+#pragma unroll
+      for (int v = 0; v < 3 * NVAR; ++v) kb[(int64_t)v * I.nifc + q] = 0.0;
+      continue;
+    }
+    if constexpr (STORED) {
 #pragma unroll
       for (int k = 0; k < NDIM; ++k) Rf.u[k] = roe_in[(int64_t)k * I.nifc + q];
       Rf.q2 = roe_in[(int64_t)(NDIM + 0) * I.nifc + q];
@@ -192,37 +227,13 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
       Rf.hb1 = roe_in[(int64_t)(NDIM + 4) * I.nifc + q];
       Rf.hb2 = roe_in[(int64_t)(NDIM + 5) * I.nifc + q];
       Rf.hic = roe_in[(int64_t)(NDIM + 6) * I.nifc + q];
-      Rf.hud = 0.5 * Rf.u[DIR];
-    } else {
-      double su2[NDIM], su3[NDIM];
 #pragma unroll
-      for (int k = 0; k < NDIM; ++k) {
-        su2[k] = aux[(NDIM + 3 + k) * I.ncell + cells[2]];
-        su3[k] = aux[(NDIM + 3 + k) * I.ncell + cells[3]];
-      }
-      teno::roe_interface<NDIM, DIR>(sr2, sr3, sh2, sh3, su2, su3, S, Rf, status);
-    }
-    teno::CertIfc<NDIM> C;
-    teno::cert_begin<NDIM, DIR>(Rf, ha, C);
-    double Ut[NVAR];
+      for (int j = 0; j < 6; ++j)
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      double Uj[NVAR];
-#pragma unroll
-      for (int v = 0; v < NVAR; ++v) {
-        Uj[v] = U[v * I.ncell + cells[j]];
-        Ut[v] = j == 0 ? Uj[v] : (j == 5 ? Ut[v] - Uj[v] : fma(Mi[j], Uj[v], Ut[v]));
-      }
-      teno::cert_point<NDIM, DIR>(j, Uj, aux[DIR * I.ncell + cells[j]], aux[NDIM * I.ncell + cells[j]], C);
-    }
-    const bool kept = S.keep_idx >= 0 && teno::cert_keep<NDIM>(C, S);
-    pending[q] = kept ? 0 : 1;
-    if (!kept) {
-      // a pending interface's terms come from adj_general_kernel; zeros
-      // here let the gather add kb for every interface alike
-#pragma unroll
-      for (int v = 0; v < 3 * NVAR; ++v) kb[(int64_t)v * I.nifc + q] = 0.0;
-      continue;
+        for (int v = 0; v < NVAR; ++v) {
+          const double u = U[v * I.ncell + cells[j]];
+          Ut[v] = j == 0 ? u : (j == 5 ? Ut[v] - u : fma(Mi[j], u, Ut[v]));
+        }
     }
     // the VJP's Roe state: the same average, and the cells' velocity and
     // enthalpy differences
@@ -909,8 +920,9 @@ AdjLayout adj_layout(const teno_grid* g, int op, int nsm) {
     off += round_up(sizeof(double) * nvar * ncell);
     L.B2 = off;
     off += round_up(sizeof(double) * nvar * ncell);
-    // the recomputed stages' Roe states (stage slots 0, 1), [ndim][ndim + 7][maxifc]
-    L.roe_dir = size_t(g->ndim + 7) * size_t(maxifc);
+    // the recomputed stages' Roe states and decisions (stage slots 0, 1),
+    // [ndim][ndim + 8][maxifc]
+    L.roe_dir = size_t(g->ndim + 8) * size_t(maxifc);
     L.roe_stage_bytes = round_up(sizeof(double) * g->ndim * L.roe_dir);
     L.roe = off;
     off += 2 * L.roe_stage_bytes;
@@ -956,8 +968,12 @@ void launch_adj_dir(int nblk, int nsm, cudaStream_t st, const double* U, const d
                     const unsigned long long* alpha, const double* Rbar, double scale, double* kb,
                     double* contrib, unsigned char* pending, uint32_t* list, int* lcount, uint32_t* sel,
                     double* apart, int* status, const Grid& G, const Scheme& S, const double* roe_in) {
-  adj_kept_kernel<NDIM, DIR><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
-                                                          status, G, S, roe_in);
+  if (roe_in)
+    adj_kept_kernel<NDIM, DIR, true><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
+                                                                  status, G, S, roe_in);
+  else
+    adj_kept_kernel<NDIM, DIR, false><<<nblk, kAdjThreads, 0, st>>>(U, aux, alpha, Rbar, scale, kb, pending, apart,
+                                                                   status, G, S, nullptr);
   int64_t nifc = 1;
   for (int k = 0; k < 3; ++k) nifc *= G.n[k] + (k == DIR ? 1 : 0);
   const int lblk = adj_list_blocks(nsm);

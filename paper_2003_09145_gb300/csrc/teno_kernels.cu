@@ -324,8 +324,9 @@ __device__ __forceinline__ void half_speeds(const unsigned long long* __restrict
 // block); 0 -- neither: the mirror flags are the constant 0 and their sign
 // flips fold away.  With ROE every interface's Roe state (the fields the
 // certificate and the adjoint's closed-form VJP read: u~, |u~|^2, H~, c~,
-// b1, b1/2, b2/2, 1/(2c~)) also goes to roe_out[ndim + 7][nifc], for the
-// adjoint of this stage.
+// b1, b1/2, b2/2, 1/(2c~)) and the certificate's decision (1 kept, 0
+// pending) also go to roe_out[ndim + 8][nifc], for the adjoint of this
+// stage.
 template <int NDIM, int DIR, int WALL, bool ROE = false>
 __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel(
     const double* __restrict__ U, const double* __restrict__ aux, const double* __restrict__ fh,
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(128, TENO_CLOSED_MINBLOCKS) flux_closed_kernel
         roe_out[(int64_t)(NDIM + 4) * nifc + q] = R.hb1;
         roe_out[(int64_t)(NDIM + 5) * nifc + q] = R.hb2;
         roe_out[(int64_t)(NDIM + 6) * nifc + q] = R.hic;
+        roe_out[(int64_t)(NDIM + 7) * nifc + q] = done ? 1.0 : 0.0;
       }
     }
     if (done) {

@@ -47,7 +47,8 @@ cudaError_t launch_argmax_finish(int ndim, const unsigned long long* cand, int64
 // interfaces it leaves pending.  `launches` (optional) receives the number
 // of kernels launched.  With `roe_out` (two-pass fluxes without reflecting or
 // fixed-state faces only) the closed-form pass also writes every
-// interface's Roe state, [ndim + 7][#interfaces] (flux_closed_kernel).
+// interface's Roe state and its certificate's decision, [ndim + 8][#interfaces]
+// (flux_closed_kernel).
 cudaError_t launch_flux(int ndim, int dir, const double* U, const double* aux, const double* fh,
                         const unsigned long long* alpha, double* Fhat,
                         uint8_t* flags, uint32_t* list, unsigned* count, int* status,
