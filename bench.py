@@ -672,6 +672,10 @@ def main() -> None:
     if not args.no_forms:
         forms["batched"] = bench_batched(api, device, max(args.steps, 4))
         forms["adjoint"] = bench_adjoint(api, device, grid, U0, 2)
+        # the reverse step in forward steps of the timed region
+        fwd_ms = ms / args.steps
+        forms["adjoint"]["x_forward_step"] = forms["adjoint"]["ms_per_step"] / fwd_ms
+        forms["adjoint"]["stages_kept"]["x_forward_step"] = forms["adjoint"]["stages_kept"]["ms_per_step"] / fwd_ms
         forms["riemann2d"] = bench_riemann2d(api, lib, device, max(args.steps, 5), args.warm_steps, peak)
         quad = inputs.riemann_2d(n=2048)
         qgrid = api.EulerGrid(quad.n, quad.dx, quad.bc)
