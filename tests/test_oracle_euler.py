@@ -204,7 +204,7 @@ def test_exact_riemann_jump_conditions_and_invariants(oracle):
 
 
 def test_sod_converges_to_exact_solution(oracle):
-    """Eq. 4.8 data (BASELINE layout: [0,1], jump at 0.5, t = 0.2): the L1 density
+    """Eq. 4.8 data (the standard Sod layout: [0,1], jump at 0.5, t = 0.2): the L1 density
     error against the exact solution decreases with N and is small at N = 200."""
     errs = []
     for n in (50, 100, 200):
