@@ -44,10 +44,15 @@ FP64_FLOP_PER_CLK_PER_SM = 4          # 2 FP64 FMA lanes per SM per clock
 #   output 24: 187.  (Forming F_d/2 costs 5 flops per cell and direction in
 #   the cell pass, plus E + p once; its mass component m_d/2 is not formed:
 #   the P-weighted sum takes m_d itself.)  The weighted sums are counted at
-#   one multiply-add per point and component; the kernel keeps them in
-#   integer weights and skips the products with weights +-1 (point 0 enters
-#   by assignment, point 5 by an add), so it executes 3 flops fewer per
-#   component and sum: 30 in 3D, reported as evaluated_flops_per_interface.
+#   one multiply-add per point and component.  The kernel keeps them in
+#   integer weights; it evaluates the five M-weighted sums and the mass
+#   component's P-weighted sum in 64-bit fixed point on the integer pipes
+#   (exact terms, one rounding: teno_fixsum.cuh) and the other four
+#   P-weighted sums as binary64 chains that skip the products with weights
+#   +-1 (9 of their 12 flops), so 187 - 6 x 12 - 4 x 3 = 103 flops per
+#   interface run on the FP64 pipe: fp64_flops_per_interface.  The roofline keeps the
+#   algorithmic count against the FP64 peak, the rate at which binary64
+#   could evaluate the same arithmetic.
 # * Otherwise the characteristic path: Roe 27, projection 6 x 20, split 6 x 28,
 #   sum 5, back-projection 21 (= 341), plus per scalar reconstruction 9 when
 #   its own FP32 pre-test keeps every stencil, else 38 for the binary64
@@ -68,7 +73,7 @@ def alg_counts(ndim: int):
 
 
 ALG_CLOSED_3D, ALG_FIXED_3D = alg_counts(3)
-EVAL_CLOSED_3D = ALG_CLOSED_3D - 3 * 2 * 5     # the closed form as the kernel evaluates it
+FP64_CLOSED_3D = ALG_CLOSED_3D - 6 * 12 - 4 * 3   # the closed form's flops on the FP64 pipe
 ALG_PER_RECON_KEEP = 9
 ALG_PER_RECON = 38
 ALG_CUTOFF = 21
@@ -164,7 +169,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-FLUX_KERNEL_SOURCES = ("teno_cert.cuh", "teno_device.cuh", "teno_flux.cuh", "teno_kernels.cu")
+FLUX_KERNEL_SOURCES = ("teno_cert.cuh", "teno_device.cuh", "teno_fixsum.cuh", "teno_flux.cuh", "teno_kernels.cu")
 
 
 def _source_hash() -> str:
@@ -641,7 +646,7 @@ def main() -> None:
                                f"{sm_max:.0f} MHz (max SM clock)",
                 "fp64_probe_tflops": probe,
                 "alg_flops_per_interface": alg_per_ifc,
-                "evaluated_flops_per_interface": alg_per_ifc - (ALG_CLOSED_3D - EVAL_CLOSED_3D) * closed_frac,
+                "fp64_flops_per_interface": alg_per_ifc - (ALG_CLOSED_3D - FP64_CLOSED_3D) * closed_frac,
                 "cutoff_evaluated_fraction": cut_frac,
                 "straightforward_count_tflops": STRAIGHTFORWARD_FLOPS_PER_IFACE_3D * nifc / flux_avg_s / 1e12}
 

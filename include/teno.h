@@ -85,7 +85,10 @@ typedef enum {
 } teno_scheme;
 
 /* Grid and scheme parameters (problem statement: eq. 2.1-2.2, eq. 4.7,
- * eq. 3.1-3.2).  Unused dimensions must have n = 1, dx = 1. */
+ * eq. 3.1-3.2).  Unused dimensions must have n = 1, dx = 1.  The interfaces
+ * along each direction are indexed with 32 bits: a grid with 2^32 or more
+ * interfaces along one direction (e.g. 2048 x 2048 x 1024 cells along x) is
+ * TENO_ERR_INVALID_ARG. */
 typedef struct {
   int ndim;          /* 1, 2 or 3                                            */
   int64_t n[3];      /* cells along x, y, z                                  */

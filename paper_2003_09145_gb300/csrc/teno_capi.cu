@@ -58,6 +58,12 @@ bool grid_ok(const teno_grid* g) {
   // total cell count must stay addressable with 64-bit indices
   const double cells = double(g->n[0]) * double(g->n[1]) * double(g->n[2]);
   if (cells * teno::aux_fields(g->ndim) > 9.0e18 / 8.0) return false;
+  // the pending lists hold 32-bit interface indices
+  for (int d = 0; d < g->ndim; ++d) {
+    double m = 1.0;
+    for (int k = 0; k < 3; ++k) m *= double(g->n[k] + (k == d ? 1 : 0));
+    if (m >= 4294967296.0) return false;
+  }
   return true;
 }
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "teno_device.cuh"
+#include "teno_fixsum.cuh"
 
 namespace teno {
 
@@ -27,6 +28,14 @@ __device__ __forceinline__ double ldc(const double* __restrict__ a, const double
                                       int64_t f, int64_t c) {
   if (GH && c >= ncell) return ga[f * kGhostSlots + (c - ncell)];
   return a[f * ncell + c];
+}
+
+// the high word of the same entry (sign, exponent, top of the significand)
+template <bool GH>
+__device__ __forceinline__ uint32_t ldc_hi(const double* __restrict__ a, const double* __restrict__ ga,
+                                           int64_t ncell, int64_t f, int64_t c) {
+  const double* p = (GH && c >= ncell) ? ga + f * kGhostSlots + (c - ncell) : a + f * ncell + c;
+  return reinterpret_cast<const uint32_t*>(p)[1];
 }
 
 // Characteristic projection of one vector X (conservative ordering) onto the
@@ -121,7 +130,8 @@ __device__ __forceinline__ bool cert_keep(const CertIfc<NDIM>& C, const Scheme& 
 // cell_flux_half gives F_d(U)/2 of one cell (eq. 4.7) from its half u_d and
 // half p -- the grid path stores it per cell and direction, the one-pass
 // path forms it per stencil point, with the same rounding; closed_point adds
-// point j to F~ and U~; closed_out forms F^.
+// point j to F~ and U~ as a binary64 chain (the one-pass form's sums; the
+// two-pass kernels use the fixed-point sums below); closed_out forms F^.
 //
 // The sums are kept in integer weights, 30 F~ = sum_j c_j F_j/2 with
 // c = (1,-8,37,37,-8,1) and 60 U~ = sum_j m_j U_j with m = (1,-5,10,-10,5,-1),
@@ -179,6 +189,102 @@ __device__ __forceinline__ void closed_point(int j, const double (&Uj)[NDIM + 2]
   }
 }
 
+// The same two sums in 64-bit fixed point (teno_fixsum.cuh): integer sums
+// on the grid 2^(E - 1078) of each component's largest stencil value,
+// rounded once to binary64 by closed_fix_out.  EU[v] and EF[v] are the
+// largest biased exponents of U[v] and of F/2[v] over the six points
+// (EF[0] = EU[1 + DIR]: the mass flux sums m_d); AU and AF accumulate the
+// integer terms.  Every U~ sum runs in fixed point; the F~ sums of the
+// components named by kFixFluxMask (1 mass, 2 momenta, 4 energy) do too, the
+// others stay binary64 chains (Ftd).  The mask balances the integer and FP64
+// pipes: it is a tuning choice, both forms being within their stated
+// rounding of the exact sum.  Measured on the 256^3 turbulence box (ms per
+// RK3 step): all ten sums in fixed point 38.3, U~ and the mass and energy
+// fluxes 37.5, U~ and the mass flux 37.4 (this default), every sum a
+// binary64 chain 40.4.
+#ifndef TENO_FIX_FLUX_MASK
+#define TENO_FIX_FLUX_MASK 1
+#endif
+constexpr unsigned kFixFluxMask = TENO_FIX_FLUX_MASK;
+
+template <int NDIM>
+struct ClosedFix {
+  uint32_t EU[NDIM + 2], EF[NDIM + 2];
+  int64_t AU[NDIM + 2], AF[NDIM + 2];
+  double Ftd[NDIM + 2];
+};
+
+template <int NVAR>
+__device__ __forceinline__ constexpr bool fix_flux(int v) {
+  return (kFixFluxMask & (v == 0 ? 1u : v == NVAR - 1 ? 4u : 2u)) != 0u;
+}
+
+// exponents from the running maxima of the magnitude keys (KF[v] is read
+// only for the fixed-point flux components); false when a component lies
+// outside the fixed point's range
+template <int NDIM, int DIR>
+__device__ __forceinline__ bool closed_fix_begin(const uint32_t (&KU)[NDIM + 2], const uint32_t (&KF)[NDIM + 2],
+                                                 ClosedFix<NDIM>& X) {
+  constexpr int NVAR = NDIM + 2;
+  bool ok = true;
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    X.AU[v] = X.AF[v] = 0;
+    X.Ftd[v] = 0.0;
+    X.EU[v] = teno_fix::exponent(KU[v]);
+    ok = ok && teno_fix::in_range(X.EU[v]);
+  }
+  X.EF[0] = X.EU[1 + DIR];
+#pragma unroll
+  for (int v = 1; v < NVAR; ++v) {
+    X.EF[v] = fix_flux<NVAR>(v) ? teno_fix::exponent(KF[v]) : 0u;
+    ok = ok && teno_fix::in_range(X.EF[v]);
+  }
+  return ok;
+}
+
+// the weights c_j and m_j for a point index that may be a loop variable
+__constant__ int c_fix_w[2][6] = {{1, -8, 37, 37, -8, 1}, {1, -5, 10, -10, 5, -1}};
+__constant__ double c_fix_cd[6] = {1.0, -8.0, 37.0, 37.0, -8.0, 1.0};
+
+// adds point j to the sums (all start at zero)
+template <int NDIM, int DIR>
+__device__ __forceinline__ void closed_fix_point(int j, const double (&Uj)[NDIM + 2], const double (&Fhj)[NDIM + 2],
+                                                 ClosedFix<NDIM>& X) {
+  constexpr int NVAR = NDIM + 2;
+  const int cw = c_fix_w[0][j], mw = c_fix_w[1][j];
+  const double cd = c_fix_cd[j];
+  // (a binary64 chain takes point 0 by assignment: j is uniform across the
+  // warp, so the branch does not diverge)
+  auto chain = [&](double& acc, double f) {
+    if (j == 0) acc = f;
+    else acc = fma(cd, f, acc);
+  };
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    teno_fix::add(X.AU[v], Uj[v], X.EU[v], mw);
+    if (v == 1 + DIR) {
+      if (fix_flux<NVAR>(0)) teno_fix::add(X.AF[0], Uj[v], X.EF[0], cw);
+      else chain(X.Ftd[0], Uj[v]);
+    }
+    if (v >= 1) {
+      if (fix_flux<NVAR>(v)) teno_fix::add(X.AF[v], Fhj[v], X.EF[v], cw);
+      else chain(X.Ftd[v], Fhj[v]);
+    }
+  }
+}
+
+template <int NDIM>
+__device__ __forceinline__ void closed_fix_out(const ClosedFix<NDIM>& X, double (&Ft)[NDIM + 2],
+                                               double (&Ut)[NDIM + 2]) {
+  constexpr int NVAR = NDIM + 2;
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) {
+    Ft[v] = fix_flux<NVAR>(v) ? teno_fix::round(X.AF[v], X.EF[v]) : X.Ftd[v];
+    Ut[v] = teno_fix::round(X.AU[v], X.EU[v]);
+  }
+}
+
 // The factor by which interface fluxes are stored (see above).
 constexpr double kFluxScale = 30.0;
 
@@ -215,12 +321,14 @@ __device__ __forceinline__ void closed_out(const double (&Ft)[NDIM + 2], const d
 }
 
 // ---------------------------------------------------------------------------
-// The certified closed form alone, one stencil point at a time (each
-// point's state is dead once it has entered F~, U~ and the FP32 test, which
-// keeps the register footprint small), with the per-cell F_DIR/2 of the cell
-// pass (`fh`, momentum and energy components only: [nvar - 1][ncell]).
-// Returns false, with `out` unwritten, when the test does not keep every
-// stencil; otherwise `out` equals interface_flux's.
+// The certified closed form alone, with the per-cell F_DIR/2 of the cell
+// pass (`fh`, momentum and energy components only: [nvar - 1][ncell]), in
+// two passes over the six stencil points: the FP32 test (and the exponents
+// of the sums), then the fixed-point sums, so that the test's state is dead
+// before the sums' state is live.  Returns false, with `out` unwritten, when
+// the test does not keep every stencil or the fixed point does not cover a
+// sum; otherwise `out` equals interface_flux's up to the rounding of the
+// sums (which that one-pass form evaluates as binary64 chains).
 // ---------------------------------------------------------------------------
 // (GH: the sweep direction has fixed-state ghost cells, read from gc; the
 // half fluxes of the ghost block are taken at direction DIR's block.  With
@@ -255,27 +363,67 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
                              ldc<GH>(aux, gc.aux, ncell, NDIM + 2, cells[3]), su2, su3, S, R, status);
   }
   if (rout) *rout = R;
-  CertIfc<NDIM> C;
-  cert_begin<NDIM, DIR>(R, alpha, C);
-  double Ft[NVAR], Ut[NVAR];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const int64_t c = cells[j];
-    // a mirrored wall point: U with the normal momentum reversed, so u_d and
-    // every component of F_d/2 but the normal-momentum one change sign
+  // stencil point j: U with the normal momentum reversed at a mirrored wall
+  // point, so u_d and every component of F_d/2 but the normal-momentum one
+  // change sign
+  auto load_point = [&](int j, int64_t c, double (&Uj)[NVAR], double (&Fhj)[NVAR]) {
     const bool fj = (flips >> j) & 1u;
-    double Uj[NVAR], Fhj[NVAR];
 #pragma unroll
     for (int v = 0; v < NVAR; ++v) Uj[v] = ldc<GH>(U, gc.U, ncell, v, c);
     Fhj[0] = 0.0;   // unused: the mass term comes from m_d
 #pragma unroll
     for (int v = 1; v < NVAR; ++v) Fhj[v] = flip_sign(ldc<GH>(fh, gfh, ncell, v - 1, c), fj && v != 1 + DIR);
     Uj[1 + DIR] = flip_sign(Uj[1 + DIR], fj);
-    const double unj = flip_sign(ldc<GH>(aux, gc.aux, ncell, DIR, c), fj), pnj = ldc<GH>(aux, gc.aux, ncell, NDIM, c);
-    closed_point<NDIM, DIR>(j, Uj, Fhj, Ft, Ut);
-    cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
+  };
+  // first pass: the certified test, and the magnitude keys of the summed
+  // components (high words only; a mirrored point changes signs only)
+  uint32_t KU[NVAR], KF[NVAR];
+#pragma unroll
+  for (int v = 0; v < NVAR; ++v) KF[v] = 0u;
+  {
+    CertIfc<NDIM> C;
+    cert_begin<NDIM, DIR>(R, alpha, C);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int64_t c = cells[j];
+      const bool fj = (flips >> j) & 1u;
+      double Uj[NVAR];
+#pragma unroll
+      for (int v = 0; v < NVAR; ++v) {
+        Uj[v] = ldc<GH>(U, gc.U, ncell, v, c);
+        const uint32_t k = teno_fix::key(teno_fix::hi_word(Uj[v]));
+        KU[v] = j == 0 ? k : max(KU[v], k);
+      }
+#pragma unroll
+      for (int v = 1; v < NVAR; ++v) {
+        if (!fix_flux<NVAR>(v)) continue;
+        const uint32_t k = teno_fix::key(ldc_hi<GH>(fh, gfh, ncell, v - 1, c));
+        KF[v] = j == 0 ? k : max(KF[v], k);
+      }
+      Uj[1 + DIR] = flip_sign(Uj[1 + DIR], fj);
+      const double unj = flip_sign(ldc<GH>(aux, gc.aux, ncell, DIR, c), fj);
+      const double pnj = ldc<GH>(aux, gc.aux, ncell, NDIM, c);
+      cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
+    }
+    if (!cert_keep<NDIM>(C, S)) return false;
   }
-  if (!cert_keep<NDIM>(C, S)) return false;
+  // second pass: the two sums per component in fixed point.  Where its
+  // exponent range does not cover a component (values below 2^-959 or above
+  // 2^1007, infinities, NaN) the interface goes to the pending list, whose
+  // characteristic path evaluates it in binary64.  The points are taken in
+  // two rounds of three (fully unrolled, the sums' temporaries of all six
+  // points would not fit in the registers beside the Roe state; the cell
+  // indices, read with a loop index, then sit in the stack frame).
+  ClosedFix<NDIM> X;
+  if (!closed_fix_begin<NDIM, DIR>(KU, KF, X)) return false;
+#pragma unroll 3
+  for (int j = 0; j < 6; ++j) {
+    double Uj[NVAR], Fhj[NVAR];
+    load_point(j, cells[j], Uj, Fhj);
+    closed_fix_point<NDIM, DIR>(j, Uj, Fhj, X);
+  }
+  double Ft[NVAR], Ut[NVAR];
+  closed_fix_out<NDIM>(X, Ft, Ut);
   closed_out<NDIM, DIR>(Ft, Ut, R, nal, out);
   return true;
 }
@@ -360,6 +508,8 @@ __device__ __forceinline__ void interface_flux(const double* __restrict__ U,
         return;
       }
       if (keep) {
+        // (the sums as binary64 chains: this one-pass form holds the whole
+        // stencil in registers already)
         double Ft[NVAR], Ut[NVAR];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {

@@ -269,7 +269,10 @@ __global__ void __launch_bounds__(128, TENO_FLUX_MINBLOCKS) flux_kernel(
 // stencils -- and appends the others to `list` (one atomic per warp);
 // flux_pending_kernel then takes the listed interfaces through the
 // characteristic path.  Each interface gets the arithmetic of the one-pass
-// kernel, so Fhat is identical; the closed-form pass stays small (registers,
+// kernel, except that the closed form's six-point sums are fixed-point sums
+// rounded once (teno_fixsum.cuh: terms on a grid of an eighth of the largest
+// value's ulp, added exactly) where the one-pass kernel chains binary64
+// operations; the closed-form pass stays small (registers,
 // instruction cache) and its warps do not diverge into the rare slow path.
 // ---------------------------------------------------------------------------
 #ifndef TENO_CLOSED_MINBLOCKS

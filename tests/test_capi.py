@@ -56,6 +56,10 @@ def test_grid_validation(lib):
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1); g.scheme = 4; bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1, scheme="teno5", ct_m=0); bad.append(g)
     g = _lib.make_grid((32, 16), (0.1, 0.1), 1, scheme="teno5", ct_m=16); bad.append(g)
+    # 2049 x 2048 x 1024 > 2^32 interfaces along x (32-bit interface indices)
+    bad.append(_lib.make_grid((2048, 2048, 1024), (0.1, 0.1, 0.1), 0))
+    assert lib.teno_workspace_bytes(ctypes.byref(_lib.make_grid((2048, 2047, 1023), (0.1, 0.1, 0.1), 0)),
+                                    _lib.OP_RHS) > 0
     for g in bad:
         assert lib.teno_workspace_bytes(ctypes.byref(g), _lib.OP_RHS) == 0
         st = lib.teno_rhs(ctypes.byref(g), None, None, None, None, 0, None)
