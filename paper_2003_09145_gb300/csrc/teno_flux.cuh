@@ -30,22 +30,6 @@ __device__ __forceinline__ double ldc(const double* __restrict__ a, const double
   return a[f * ncell + c];
 }
 
-// ldc with an L1 eviction priority: kept (evict_last) for values a later
-// pass reads again, streamed (evict_first) for values read once
-#ifndef TENO_L1_HINTS
-#define TENO_L1_HINTS 0
-#endif
-template <bool GH, bool KEEP>
-__device__ __forceinline__ double ldc_hint(const double* __restrict__ a, const double* __restrict__ ga,
-                                           int64_t ncell, int64_t f, int64_t c) {
-  if (!TENO_L1_HINTS || (GH && c >= ncell)) return ldc<GH>(a, ga, ncell, f, c);
-  const double* p = a + f * ncell + c;
-  double v;
-  if (KEEP) asm("ld.global.nc.L1::evict_last.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  else asm("ld.global.nc.L1::evict_first.f64 %0, [%1];" : "=d"(v) : "l"(p));
-  return v;
-}
-
 // the high word of the same entry (sign, exponent, top of the significand)
 template <bool GH>
 __device__ __forceinline__ uint32_t ldc_hi(const double* __restrict__ a, const double* __restrict__ ga,
@@ -388,7 +372,7 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
     for (int v = 0; v < NVAR; ++v) Uj[v] = ldc<GH>(U, gc.U, ncell, v, c);
     Fhj[0] = 0.0;   // unused: the mass term comes from m_d
 #pragma unroll
-    for (int v = 1; v < NVAR; ++v) Fhj[v] = flip_sign(ldc_hint<GH, false>(fh, gfh, ncell, v - 1, c), fj && v != 1 + DIR);
+    for (int v = 1; v < NVAR; ++v) Fhj[v] = flip_sign(ldc<GH>(fh, gfh, ncell, v - 1, c), fj && v != 1 + DIR);
     Uj[1 + DIR] = flip_sign(Uj[1 + DIR], fj);
   };
   // first pass: the certified test, and the magnitude keys of the summed
@@ -406,7 +390,7 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
       double Uj[NVAR];
 #pragma unroll
       for (int v = 0; v < NVAR; ++v) {
-        Uj[v] = ldc_hint<GH, true>(U, gc.U, ncell, v, c);
+        Uj[v] = ldc<GH>(U, gc.U, ncell, v, c);
         const uint32_t k = teno_fix::key(teno_fix::hi_word(Uj[v]));
         KU[v] = j == 0 ? k : max(KU[v], k);
       }
@@ -417,8 +401,8 @@ __device__ __forceinline__ bool interface_flux_closed(const double* __restrict__
         KF[v] = j == 0 ? k : max(KF[v], k);
       }
       Uj[1 + DIR] = flip_sign(Uj[1 + DIR], fj);
-      const double unj = flip_sign(ldc_hint<GH, false>(aux, gc.aux, ncell, DIR, c), fj);
-      const double pnj = ldc_hint<GH, false>(aux, gc.aux, ncell, NDIM, c);
+      const double unj = flip_sign(ldc<GH>(aux, gc.aux, ncell, DIR, c), fj);
+      const double pnj = ldc<GH>(aux, gc.aux, ncell, NDIM, c);
       cert_point<NDIM, DIR>(j, Uj, unj, pnj, C);
     }
     if (!cert_keep<NDIM>(C, S)) return false;
