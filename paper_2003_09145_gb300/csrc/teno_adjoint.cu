@@ -56,6 +56,23 @@ using teno::Scheme;
 
 constexpr int kAdjThreads = 128;
 
+// The adjoint's six-point sums with integer weights in 64-bit fixed point
+// (teno_fixsum.cuh, as in the forward's closed form): bit 1 the stencil on
+// Rbar (weights 1, -9, 45 on the differences), bit 2 the M-weighted U~bar of
+// the slots, bit 4 the kept pass's 60 U~ (from stored Roe states).  A
+// component the fixed point does not cover takes the binary64 form.  A
+// tuning choice between the FP64 and integer pipes; measured on the 256^3
+// reverse RK3 step (ms): none 102.4, bit 1 100.9-101.1 (this default), bit
+// 4 101.5, bits 1 and 4 100.0, bits 1 and 2 114.7 (the M sums' seven loads
+// per component spill and the integer chains then bound the gather).  Bit 4
+// is left off: the kept pass without stored states (the staged reverse
+// step's) sums U~ as a binary64 chain, and the two reverse steps agree bit
+// for bit only if both do.
+#ifndef TENO_ADJ_FIX_MASK
+#define TENO_ADJ_FIX_MASK 1
+#endif
+constexpr unsigned kAdjFixMask = TENO_ADJ_FIX_MASK;
+
 // Geometry of interface q of direction DIR: its index id along DIR, the
 // linear index of its line's cell 0 and the six stencil cells (ghosts mapped).
 template <int NDIM, int DIR>
@@ -228,12 +245,18 @@ __global__ void __launch_bounds__(kAdjThreads, TENO_ADJ_KEPT_MINBLOCKS) adj_kept
       Rf.hb2 = roe_in[(int64_t)(NDIM + 5) * I.nifc + q];
       Rf.hic = roe_in[(int64_t)(NDIM + 6) * I.nifc + q];
 #pragma unroll
-      for (int j = 0; j < 6; ++j)
+      for (int v = 0; v < NVAR; ++v) {
+        double us[6];
 #pragma unroll
-        for (int v = 0; v < NVAR; ++v) {
-          const double u = U[v * I.ncell + cells[j]];
-          Ut[v] = j == 0 ? u : (j == 5 ? Ut[v] - u : fma(Mi[j], u, Ut[v]));
+        for (int j = 0; j < 6; ++j) us[j] = U[v * I.ncell + cells[j]];
+        const int mw[6] = {1, -5, 10, -10, 5, -1};
+        if (!(kAdjFixMask & 4u) || !teno_fix::sum<6>(us, mw, Ut[v])) {
+          Ut[v] = us[0];
+#pragma unroll
+          for (int j = 1; j < 5; ++j) Ut[v] = fma(Mi[j], us[j], Ut[v]);
+          Ut[v] -= us[5];
         }
+      }
     }
     // the VJP's Roe state: the same average, and the cells' velocity and
     // enthalpy differences
@@ -544,6 +567,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_general_kernel(
 // for U~ = sum_j M_j U_j (indexed by a warp-uniform slot number).
 __constant__ double c_adjP[6] = {1.0 / 60.0, -8.0 / 60.0, 37.0 / 60.0, 37.0 / 60.0, -8.0 / 60.0, 1.0 / 60.0};
 __constant__ double c_adjM[6] = {1.0 / 60.0, -5.0 / 60.0, 10.0 / 60.0, -10.0 / 60.0, 5.0 / 60.0, -1.0 / 60.0};
+__constant__ int c_adjMi[6] = {1, -5, 10, -10, 5, -1};
+
 
 // What the gather reads per direction, and its output.
 struct GatherArgs {
@@ -561,6 +586,24 @@ struct GatherArgs {
 // acc and its Roe-parameter adjoints (j = 2: cell i, j = 3: cell i+1) into
 // rp (both zero for a pending interface), and for a pending one its own
 // contribution into acc.
+// (slot_rest: the same without the M_j U~bar term, which the stencil path
+// sums in fixed point.)
+template <int NVAR>
+__device__ __forceinline__ void slot_rest(int j, int64_t q, const double* __restrict__ kb,
+                                          const double* __restrict__ contrib,
+                                          const unsigned char* __restrict__ pending, int64_t nifc,
+                                          double (&acc)[NVAR], double (&rp)[NVAR]) {
+  if (j == 2)
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(NVAR + v) * nifc + q];
+  if (j == 3)
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) rp[v] += kb[(int64_t)(2 * NVAR + v) * nifc + q];
+  if (pending[q])
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) acc[v] += contrib[(int64_t)(j * NVAR + v) * nifc + q];
+}
+
 template <int NVAR>
 __device__ __forceinline__ void slot_terms(int j, int64_t q, const double* __restrict__ kb,
                                            const double* __restrict__ contrib,
@@ -671,16 +714,49 @@ __device__ __forceinline__ void gather_dir(const Grid& G, int64_t c, int64_t i0,
     const int64_t o2p = wrapped(idl + 2) * cstride, o2m = wrapped(idl - 2) * cstride;
     const int64_t o3p = wrapped(idl + 3) * cstride, o3m = wrapped(idl - 3) * cstride;
     const double w1 = fs * (1.0 / 60.0), w9 = fs * (-9.0 / 60.0), w45 = fs * (45.0 / 60.0);
-#pragma unroll
-    for (int v = 0; v < NVAR; ++v) {
-      const double* r = Rbar + v * ncell + line;
-      Fsum[v] = fma(w45, r[o1p] - r[o1m], fma(w9, r[o2p] - r[o2m], w1 * (r[o3p] - r[o3m])));
-    }
+    // slot j's interface; on a periodic line the slot whose interface is 0
+    // also takes face nd (jd), whose U~bar enters the M sum as a seventh term
+    // (interface indices fit in 32 bits: the C-ABI's grid limit)
+    uint32_t qs[6];
+    int jd = -1;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       const int x = wrapped(idl + 3 - j);
-      slot_terms<NVAR>(j, q0 + (int64_t)x * sd, kb, contrib, pending, nifc, acc, rp);
-      if (x == 0 && bc == 0) slot_terms<NVAR>(j, q0 + (int64_t)ndl * sd, kb, contrib, pending, nifc, acc, rp);
+      qs[j] = static_cast<uint32_t>(q0 + (int64_t)x * sd);
+      if (x == 0 && bc == 0) jd = j;
+    }
+    const uint32_t qd = static_cast<uint32_t>(q0 + (int64_t)ndl * sd);
+#pragma unroll
+    for (int v = 0; v < NVAR; ++v) {
+      const double* r = Rbar + v * ncell + line;
+      const double r1p = r[o1p], r1m = r[o1m], r2p = r[o2p], r2m = r[o2m], r3p = r[o3p], r3m = r[o3m];
+      double S;
+      const double rs[6] = {r3p, r3m, r2p, r2m, r1p, r1m};
+      const int rw[6] = {1, -1, -9, 9, 45, -45};
+      if ((kAdjFixMask & 1u) && teno_fix::sum<6>(rs, rw, S)) Fsum[v] = w1 * S;
+      else Fsum[v] = fma(w45, r1p - r1m, fma(w9, r2p - r2m, w1 * (r3p - r3m)));
+      if (kAdjFixMask & 2u) {
+        const double* k = kb + (int64_t)v * nifc;
+        const double ks[7] = {k[qs[0]], k[qs[1]], k[qs[2]], k[qs[3]], k[qs[4]], k[qs[5]], jd >= 0 ? k[qd] : 0.0};
+        const int kw[7] = {1, -5, 10, -10, 5, -1, jd >= 0 ? c_adjMi[jd] : 0};
+        double T;
+        if (teno_fix::sum<7>(ks, kw, T)) {
+          acc[v] = fma(1.0 / 60.0, T, acc[v]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 7; ++j) acc[v] = fma(kw[j] * (1.0 / 60.0), ks[j], acc[v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (kAdjFixMask & 2u) {
+        slot_rest<NVAR>(j, qs[j], kb, contrib, pending, nifc, acc, rp);
+        if (j == jd) slot_rest<NVAR>(j, qd, kb, contrib, pending, nifc, acc, rp);
+      } else {
+        slot_terms<NVAR>(j, qs[j], kb, contrib, pending, nifc, acc, rp);
+        if (j == jd) slot_terms<NVAR>(j, qd, kb, contrib, pending, nifc, acc, rp);
+      }
     }
   } else {
 #pragma unroll

@@ -1,5 +1,6 @@
-// teno_fixsum.cuh -- the closed form's six-point sums with integer weights,
-// evaluated in 64-bit fixed point on the integer pipes, for host and device.
+// teno_fixsum.cuh -- the closed form's six-point sums with integer weights
+// (and the adjoint's sums of the same kind), evaluated in 64-bit fixed point
+// on the integer pipes, for host and device.
 //
 // Where every stencil is kept, the interface flux needs per component two
 // sums S = sum_j w_j x_j over the six stencil points, with the integer
@@ -132,6 +133,26 @@ TENO_FIX_HD double round(int64_t A, uint32_t E) {
   // leading bit (and a carry to 2^53) adds to the exponent field
   const uint64_t b = static_cast<uint64_t>(E) + 11u - kGuard - static_cast<uint64_t>(lz);
   return from_bits(((b - 1u) << 52) + m + (s << 63));
+}
+
+// sum_k w_k x_k of n values in fixed point, for weights with sum_k |w_k| < 128
+// (so |A| < 2^63): false, with `out` untouched, where the fixed point does not
+// cover the values
+template <int N>
+TENO_FIX_HD bool sum(const double (&x)[N], const int (&w)[N], double& out) {
+  uint32_t kmax = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t kk = key(hi_word(x[k]));
+    kmax = kk > kmax ? kk : kmax;
+  }
+  const uint32_t E = exponent(kmax);
+  if (!in_range(E)) return false;
+  int64_t A = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) add(A, x[k], E, w[k]);
+  out = round(A, E);
+  return true;
 }
 
 }  // namespace teno_fix

@@ -27,4 +27,17 @@ void fix_sum6_batch(int64_t n, const double* x, const int* w, double* out, int* 
   }
 }
 
+// the same through teno_fix::sum (n values of 7, weights of any sign with
+// sum |w| < 128); ok[i] = 0 where it declines
+void fix_sum7_batch(int64_t n, const double* x, const int* w, double* out, int* ok) {
+  int wa[7];
+  for (int j = 0; j < 7; ++j) wa[j] = w[j];
+  for (int64_t i = 0; i < n; ++i) {
+    double xi[7];
+    for (int j = 0; j < 7; ++j) xi[j] = x[7 * i + j];
+    out[i] = 0.0;
+    ok[i] = teno_fix::sum<7>(xi, wa, out[i]) ? 1 : 0;
+  }
+}
+
 }  // extern "C"

@@ -34,6 +34,8 @@ def lib():
     L.fix_sum6_batch.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_void_p]
     L.fix_sum6_batch.restype = None
+    L.fix_sum7_batch.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.fix_sum7_batch.restype = None
     return L
 
 
@@ -188,3 +190,34 @@ def test_matches_binary64_chain_on_flux_like_data(lib):
     chain = chain + x[:, 5]
     mx = np.max(np.abs(x), axis=1)
     assert np.all(np.abs(out - chain) <= 256 * np.spacing(mx))
+
+
+# the adjoint gather's sums: the antisymmetric stencil on Rbar (weights
+# 1, -1, -9, 9, 45, -45: sum |w| = 110) and the M-weighted slot sum with the
+# periodic face's second copy as a seventh term
+@pytest.mark.parametrize("w", [(1, -1, -9, 9, 45, -45, 0), (1, -5, 10, -10, 5, -1, 10), (1, -5, 10, -10, 5, -1, 0)])
+def test_seven_term_sums_against_exact(lib, w):
+    rng = np.random.default_rng(16)
+    n = 2000
+    x = rng.standard_normal((n, 7)) * np.exp2(rng.integers(-200, 200, (n, 1)).astype(np.float64))
+    x *= np.exp2(rng.integers(-30, 31, (n, 7)).astype(np.float64))
+    x[rng.random((n, 7)) < 0.05] = 0.0
+    out = np.zeros(n)
+    ok = np.zeros(n, dtype=np.int32)
+    wa = np.ascontiguousarray(w, dtype=np.int32)
+    lib.fix_sum7_batch(n, np.ascontiguousarray(x).ctypes.data, wa.ctypes.data, out.ctypes.data, ok.ctypes.data)
+    assert ok.all()
+    for i in range(n):
+        want, _ = _spec(x[i], w)
+        assert out[i] == want, (x[i], out[i], want)
+        exact = sum(Fraction(wj) * Fraction(float(v)) for wj, v in zip(w, x[i]))
+        mx = float(np.max(np.abs(x[i])))
+        bound = Fraction(sum(abs(wj) for wj in w), 8) * Fraction(_ulp(mx)) + Fraction(_ulp(out[i])) / 2
+        assert abs(Fraction(float(out[i])) - exact) <= bound
+    # declines on NaN and on values out of range
+    bad = np.zeros((2, 7))
+    bad[0, 3] = np.nan
+    bad[1, 0] = 2.0 ** 1010
+    lib.fix_sum7_batch(2, np.ascontiguousarray(bad).ctypes.data, wa.ctypes.data, out.ctypes.data, ok.ctypes.data)
+    assert not ok[:2].any()
+
