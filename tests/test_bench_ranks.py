@@ -70,3 +70,20 @@ def test_single_process_defaults():
         os.environ.update(env)
     assert bench.max_over_ranks(None, 12.5, "cpu") == 12.5
     assert bench.whole_job_rate(1, 100, 2, 1000.0) == pytest.approx(2e-7)
+
+
+def test_flop_accounting():
+    """The roofline's per-interface counts, term by term as bench.py lists
+    them: the closed form 187 (3D) / 153 (2D), the characteristic path 341 /
+    290; of the closed form's 187, the FP64 pipe runs 103 (six of the ten
+    six-point sums in fixed point: 72 FLOPs; the other four skip their
+    products with weights +-1: 12)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.alg_counts(3) == (187, 341)
+    assert bench.alg_counts(2) == (153, 290)
+    assert bench.ALG_CLOSED_3D - bench.FP64_CLOSED_3D == 6 * 12 + 4 * 3
+    assert bench.FP64_CLOSED_3D == 103
+    # the six-point sums are 12 algorithmic FLOPs each (one multiply-add per
+    # point), ten per interface: 120 of the closed form's 187
+    assert 10 * 12 == 6 * 4 * 5
