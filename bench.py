@@ -648,9 +648,10 @@ def main() -> None:
                 "alg_flops_per_interface": alg_per_ifc,
                 "fp64_flops_per_interface": alg_per_ifc - (ALG_CLOSED_3D - FP64_CLOSED_3D) * closed_frac,
                 "fixed_point_sums": "closed form: the five M-weighted sums (60 U~) and the mass flux's "
-                                    "P-weighted sum in exact 64-bit fixed point on the integer pipes, "
-                                    "rounded once to binary64; the momentum and energy P-sums as binary64 "
-                                    "chains",
+                                    "P-weighted sum in 64-bit fixed point on the integer pipes (terms "
+                                    "truncated 3 bits below the largest value's ulp, summed exactly, "
+                                    "rounded once to binary64); the momentum and energy P-sums as "
+                                    "binary64 chains",
                 "cutoff_evaluated_fraction": cut_frac,
                 "straightforward_count_tflops": STRAIGHTFORWARD_FLOPS_PER_IFACE_3D * nifc / flux_avg_s / 1e12}
 
